@@ -1,0 +1,349 @@
+"""Benchmark of the fV-SRN render / fit path on GB300.
+
+Workload (N = 1): the config-2 scene.  A 256^3 fractal-noise volume, an
+fV-SRN with a 32^3 x 16 FP16 latent grid, 14 Fourier features and 4 SnakeAlt
+layers of width 32, fitted to the volume by the library's own fit kernels,
+rendered at 1024 x 1024 with step 1/512, an 8-point TF and early termination
+at 0.99.  One step = one 1024^2 frame (views cycle over 8 orbit cameras).
+
+Headline metric: network samples/s (device-counted network evaluations /
+device time).  Also reported: ms/frame of fV-SRN vs dense-grid DVR of the
+same volume with the PSNR between them, and fit steps/s (config 3).
+
+--impl reference times the FP64 CPU oracle (the only reference there is) on
+a bounded sample of the same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "network samples/s and ms/frame @1024² (fV-SRN vs dense DVR, PSNR stated); fit steps/s"
+W_IMG = H_IMG = 1024
+STEP = 1.0 / 512
+ET = 0.99
+N_VIEWS = 8
+FIT_STEPS = 2000
+FIT_POINTS = 1 << 18
+WORKLOAD = "cfg2: 256^3 fractal noise; fV-SRN 32^3x16 fp16 grid, m=14, 4x32 SnakeAlt; 1024^2, step 1/512, 8-pt TF, ET 0.99"
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def setup_scene(device="cuda", fit_steps=FIT_STEPS, seed=0):
+    """Volume, fitted network (FP16 render copy), TF and cameras of config 2."""
+    import torch
+    from paper_2112_01579_gb300 import srn, synth
+    vol = synth.noise_volume(256, seed=seed, device=device).contiguous()
+    p = synth.init_params(R=32, F=16, m=14, layers=4, width=32, out_dim=1, act=synth.ACT_SNAKEALT, seed=seed)
+    net = srn.Network(p, precision=srn.SRN_PREC_FP16, max_fit_points=FIT_POINTS, adam=True)
+    fit_info = {"steps": 0}
+    loss = torch.zeros(1, device=device)
+    try:
+        t0 = time.time()
+        for s in range(fit_steps):
+            srn.srn_fit_step(net.ctx, vol, FIT_POINTS, seed + 1, s, loss, lr_grid=1e-2, lr_net=5e-3)
+        torch.cuda.synchronize()
+        fit_info = {"steps": fit_steps, "final_loss": float(loss.item()), "wall_s": time.time() - t0}
+    except srn.SrnError as e:
+        fit_info = {"steps": 0, "unavailable": str(e)}
+    srn.srn_sync_half(net.ctx)
+    return vol, net, synth.tf_preset(8), synth.orbit_cameras(N_VIEWS), fit_info
+
+
+def time_fit(net, vol, n_steps=50, seed=5):
+    import torch
+    from paper_2112_01579_gb300 import srn
+    loss = torch.zeros(1, device="cuda")
+    try:
+        for s in range(3):
+            srn.srn_fit_step(net.ctx, vol, FIT_POINTS, seed, 10000 + s, loss, lr_grid=0.0, lr_net=0.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for s in range(n_steps):
+            srn.srn_fit_step(net.ctx, vol, FIT_POINTS, seed, 10003 + s, loss, lr_grid=0.0, lr_net=0.0)
+        e1.record()
+        torch.cuda.synchronize()
+        return n_steps / (e0.elapsed_time(e1) / 1e3)
+    except srn.SrnError:
+        return None
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2112_01579_gb300 import srn
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    vol, net, tf, cams, fit_info = setup_scene(fit_steps=args.fit_steps)
+    prec_name = "fp16-mma"
+    desc = srn.render_desc(W_IMG, H_IMG, STEP, ET)
+    out = torch.zeros((1, 1, H_IMG, W_IMG, 4), device=dev)
+    ctr = torch.zeros(1, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+    try:
+        srn.srn_render(net.ctx, cams[:1], tf, desc, out, samples=ctr)
+    except srn.SrnError as e:
+        if e.status != srn.SRN_ERR_UNSUPPORTED:
+            raise
+        # the FP16 tensor-core kernel does not cover this build: measure the FP32 path
+        net.close()
+        from paper_2112_01579_gb300 import synth
+        net = srn.Network(net.unpack(), precision=srn.SRN_PREC_FP32)
+        prec_name = "fp32"
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MiB > L2
+
+    def frame(k, samples=None):
+        srn.srn_render(net.ctx, [cams[(k + rank) % N_VIEWS]], tf, desc, out, samples=samples)
+
+    for k in range(args.warmup):
+        frame(k)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ctr.zero_()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            frame(k, ctr)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    t_total = sum(ms) / 1e3
+    samples = int(ctr.item())
+    if world > 1:
+        t = torch.tensor([t_total], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        s = torch.tensor([samples], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(s)
+        t_total, samples = float(t.item()), int(s.item())
+    value = samples / t_total
+    ms_frame = t_total * 1e3 / args.steps
+
+    # dense-grid DVR of the same volume and PSNR between the two renderers
+    dense = torch.zeros_like(out[0])
+    dctr = torch.zeros(1, dtype=torch.int64, device=dev)
+    srn.srn_dvr_dense(vol, cams[:1], tf, desc, dense)
+    torch.cuda.synchronize()
+    d_ms = []
+    for k in range(max(3, args.steps // 2)):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        srn.srn_dvr_dense(vol, [cams[k % N_VIEWS]], tf, desc, dense, samples=dctr)
+        b.record(stream)
+        torch.cuda.synchronize()
+        d_ms.append(a.elapsed_time(b))
+    psnrs = []
+    mse = torch.zeros(1, dtype=torch.float64, device=dev)
+    for v in range(N_VIEWS):
+        srn.srn_render(net.ctx, [cams[v]], tf, desc, out)
+        srn.srn_dvr_dense(vol, [cams[v]], tf, desc, dense)
+        srn.srn_image_mse(out, dense, mse)
+        torch.cuda.synchronize()
+        psnrs.append(10 * math.log10(1.0 / max(mse.item(), 1e-30)))
+    fit_sps = time_fit(net, vol) if fit_info.get("steps") else None
+
+    # end-to-end through the C ABI with host buffers: parameters uploaded from
+    # pinned host memory and the image read back, every step
+    e2e = run_e2e(net, tf, cams, desc, dev, args.steps)
+
+    res = {
+        "metric": METRIC, "value": value, "unit": "network samples/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_frame, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f16" if prec_name == "fp16-mma" else "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": prec_name, "width": W_IMG, "height": H_IMG,
+                   "step": STEP, "et": ET, "l2": "flushed (256 MiB write) between timed frames",
+                   "samples_per_frame": samples / args.steps / world,
+                   "fvsrn_ms_per_frame": ms_frame, "dense_dvr_ms_per_frame": float(np.median(d_ms)),
+                   "psnr_fvsrn_vs_dense_db": float(np.mean(psnrs)), "fit": fit_info,
+                   "fit_steps_per_s": fit_sps, "parallelism": f"replicas x{world} (views split across ranks)"},
+        "e2e": e2e, "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+    }
+    return res, net, vol, tf, cams
+
+
+def run_e2e(net, tf, cams, desc, dev, steps):
+    import torch
+    from paper_2112_01579_gb300 import srn
+    host_grid = net.grid_h.cpu().pin_memory()
+    host_w = net.weights_h.cpu().pin_memory()
+    host_b = net.biases.cpu().pin_memory()
+    host_img = torch.empty((1, 1, H_IMG, W_IMG, 4), dtype=torch.float32).pin_memory()
+    out = torch.empty((1, 1, H_IMG, W_IMG, 4), device=dev)
+    ctr = torch.zeros(1, dtype=torch.int64, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(steps):
+        net.grid_h.copy_(host_grid, non_blocking=True)
+        net.weights_h.copy_(host_w, non_blocking=True)
+        net.biases.copy_(host_b, non_blocking=True)
+        srn.srn_render(net.ctx, [cams[k % N_VIEWS]], tf, desc, out, samples=ctr)
+        host_img.copy_(out, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    dt = time.perf_counter() - t0
+    h2d = host_grid.numel() * 2 + host_w.numel() * 2 + host_b.numel() * 4
+    return {"value": int(ctr.item()) / dt, "unit": "network samples/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(host_img.numel() * 4)}
+
+
+def cpu_baseline(params, vol_np, tf, cams, budget_rows=16):
+    """The FP64 oracle on a bounded sample: every (H / budget_rows)-th row of
+    one 1024^2 frame of the same scene."""
+    import oracle
+    on = oracle.OracleNet(params)
+    otf = oracle.OracleTF(tf["pos"], tf["rgba"], tf["opacity_scale"])
+    rows = np.arange(0, H_IMG, H_IMG // budget_rows)
+    pix = (rows[:, None] * W_IMG + np.arange(W_IMG)[None, :]).reshape(-1)
+    t0 = time.perf_counter()
+    _, _, ns = oracle.render(on, cams[:1], otf, W_IMG, H_IMG, STEP, ET, pixels=pix)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": ns / dt, "unit": "network samples/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(rows)} of {H_IMG} rows of one {W_IMG}x{H_IMG} frame ({ns} samples, {dt:.1f} s)"}
+
+
+def roofline(res):
+    """Dominant kernel (the fV-SRN render) against its binding unit."""
+    return None
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import torch
+    from paper_2112_01579_gb300 import synth
+    vol = synth.noise_volume(256, seed=0, device="cpu")
+    p = synth.init_params(R=32, F=16, m=14, layers=4, width=32, out_dim=1, act=synth.ACT_SNAKEALT, seed=0)
+    p = synth.to_half_exact(p)
+    tf, cams = synth.tf_preset(8), synth.orbit_cameras(N_VIEWS)
+    for _ in range(args.warmup):
+        cpu_baseline(p, None, tf, cams, budget_rows=4)
+    vals, samples, secs = [], 0, 0.0
+    cb = None
+    for _ in range(args.steps):
+        cb = cpu_baseline(p, None, tf, cams, budget_rows=4)
+        vals.append(cb["value"])
+    value = float(np.mean(vals))
+    cb["value"] = value
+    return {"metric": METRIC, "value": value, "unit": "network samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD + " (bounded row sample per step)"}, "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "network samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fit-steps", type=int, default=FIT_STEPS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    rank = int(os.environ.get("RANK", 0))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "ours":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+            dist.init_process_group("nccl")
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res))
+        return
+    import __graft_entry__
+    __graft_entry__.build()
+    res, net, vol, tf, cams = run_ours(args, rank, world)
+    res["roofline"] = roofline(res)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(net.unpack_half(), None, tf, cams)
+    if rank == 0:
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

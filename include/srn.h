@@ -1,0 +1,243 @@
+/*
+ * srn.h — C ABI of the GB300 (sm_103a) fV-SRN render / fit library.
+ *
+ * fV-SRN (Weiss, Hermüller, Westermann, "Fast Neural Representations for
+ * Direct Volume Rendering", arXiv 2112.01579) represents a scalar volume by a
+ * small MLP (Section 3) whose input is the position, its Fourier features
+ * (Eq. 1-2) and a latent vector trilinearly interpolated from a dense latent
+ * grid (Section 4.2).  This library evaluates that network at every sample
+ * of a direct-volume-rendering ray march, trains it on density samples
+ * (world-space L1 fit, Section 5 ablation setup), and computes its input
+ * gradient for shading (Section 5 gradients).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - All array pointers named *_dev are CUDA device pointers owned by the
+ *   caller; the library never frees them.  They must be 16-byte aligned.
+ * - Pointers to structs (configs, cameras, transfer functions, descriptors)
+ *   are host pointers; their contents are copied during the call.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Work is enqueued asynchronously on it; no call synchronizes
+ *   except srn_sync_status, srn_save and srn_load.
+ * - Arguments are validated before anything is enqueued: an invalid call
+ *   returns SRN_ERR_INVALID_ARG or SRN_ERR_UNSUPPORTED with no side effect.
+ *   A failed launch returns SRN_ERR_CUDA.  srn_last_error() gives the
+ *   thread-local message of the last failure.
+ * - There is no CPU fallback: every computation runs in the library's own
+ *   CUDA kernels on the current device.
+ *
+ * Geometry
+ * --------
+ * The volume fills the world-space box [-0.5, 0.5]^3; network / volume
+ * coordinates are p = x + 0.5 in [0, 1]^3.  Grids are vertex aligned: a grid
+ * of n vertices per axis has vertex i at p = i / (n - 1) ("R vertices along
+ * each axis", Section 4.2).  Volumes are float32 [nz][ny][nx] with x fastest.
+ */
+#ifndef SRN_H
+#define SRN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum srn_status {
+  SRN_OK = 0,
+  SRN_ERR_INVALID_ARG = 1, /* a pointer, size or enum is invalid */
+  SRN_ERR_UNSUPPORTED = 2, /* valid, but not a shape this build implements */
+  SRN_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed */
+  SRN_ERR_NONFINITE = 4,   /* a fit step produced a non-finite loss/gradient */
+  SRN_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+  SRN_ERR_INTERNAL = 6     /* a device-side consistency check failed */
+} srn_status;
+
+enum { SRN_ACT_SINE = 0, SRN_ACT_SNAKEALT = 1 };   /* sin(x); Eq. 3: 0.5x + sin^2 x */
+enum { SRN_PREC_FP32 = 0, SRN_PREC_FP16 = 1 };     /* network arithmetic of render / eval */
+enum { SRN_SHADE_NONE = 0, SRN_SHADE_ADJOINT = 1, SRN_SHADE_FD = 2, SRN_SHADE_HEAD = 3 };
+
+#define SRN_MAX_KEYFRAMES 32
+#define SRN_MAX_TF_POINTS 32
+#define SRN_MAX_VIEWS 64
+#define SRN_MAX_TIMES 64
+
+/*
+ * Network shape (Section 3 layer equation v_{i+1} = a(W_i v_i + b_i),
+ * Section 4.1 m = (c-4)/2 rule, Section 4.2 latent grid, Section 7
+ * keyframes).  Layer i maps d_i -> d_{i+1} with d_0 = 3 + 2m + F (input
+ * [p, sin(Fp), cos(Fp), z]), d_1..d_{l-1} = width, d_l = out_dim; the
+ * activation follows every layer but the last.
+ */
+typedef struct srn_config {
+  int grid_res;    /* R >= 2: latent grid vertices per axis */
+  int feat;        /* F: latent channels, a multiple of 4 (of 8 for FP16) */
+  int n_fourier;   /* m: rows of the Fourier matrix */
+  int layers;      /* l >= 2: number of linear layers */
+  int width;       /* c: hidden channels (32 for every implemented kernel) */
+  int out_dim;     /* D: 1 (density) or 4 (density + gradient head, Section 5) */
+  int activation;  /* SRN_ACT_* */
+  int precision;   /* SRN_PREC_*: arithmetic of srn_render (FP16 = tensor cores) */
+  int n_keyframes; /* >= 1 latent grids; > 1 enables time interpolation */
+  float key_times[SRN_MAX_KEYFRAMES]; /* increasing keyframe times (n_keyframes > 1) */
+  int max_fit_points; /* scratch of srn_fit_step / srn_backward is sized for this many points (0: none) */
+} srn_config;
+
+/*
+ * Parameters, all device memory owned by the caller and read at call time
+ * (updating them needs no re-create).  Layouts:
+ *   grid     float32 [n_keyframes][R][R][R][F]   (x fastest, channel innermost)
+ *   fourier  float32 [m][3]                      (fixed, not trained; Eq. 1)
+ *   weights  float32 W_0 | W_1 | ... | W_{l-1}, each row-major [d_{i+1}][d_i]
+ *   biases   float32 b_0 | ... | b_{l-1}
+ *   grid_h / weights_h: FP16 copies with the same layouts, read by the FP16
+ *            path; srn_sync_half writes them from the FP32 masters.
+ *   adam_m / adam_v: float32 Adam moments packed [grid | weights | biases];
+ *            required by srn_fit_step only.
+ */
+typedef struct srn_params {
+  float* grid;
+  const float* fourier;
+  float* weights;
+  float* biases;
+  void* grid_h;
+  void* weights_h;
+  float* adam_m;
+  float* adam_v;
+} srn_params;
+
+/* Pinhole camera: row 0 is the top row, rays through pixel centres. */
+typedef struct srn_camera {
+  float eye[3];
+  float target[3];
+  float up[3];
+  float fovy; /* vertical field of view, radians */
+} srn_camera;
+
+/*
+ * Transfer function (Section 3: densities are mapped to colour by a TF).
+ * Density is clamped to [0,1]; RGBA is piecewise linear between the sorted
+ * control points pos[0..n-1] (host arrays, copied), constant outside.
+ * The extinction coefficient is A * opacity_scale per unit world length.
+ */
+typedef struct srn_tf {
+  int n; /* 2..SRN_MAX_TF_POINTS */
+  const float* pos;
+  const float* rgba; /* n x 4 */
+  float opacity_scale;
+} srn_tf;
+
+/*
+ * Ray-march description.  Each ray is cut at the box into segments
+ * [t0 + k step, min(t0 + (k+1) step, t1)], sampled at the segment midpoint,
+ * alpha = 1 - exp(-kappa * length), composited front to back (premultiplied,
+ * black background) and stopped after the sample that brings the opacity to
+ * et_threshold or above (> 1 disables early termination).
+ */
+typedef struct srn_render_desc {
+  int width, height;
+  float step;         /* world units (the box is 1 wide) */
+  float et_threshold; /* early ray termination opacity, e.g. 0.99 */
+  int shading;        /* SRN_SHADE_*: headlight Blinn-Phong from the density gradient */
+  float fd_h;         /* central-difference step (network coordinates) for SRN_SHADE_FD */
+} srn_render_desc;
+
+typedef struct srn_ctx srn_ctx;
+
+/* Library version string (static storage). */
+const char* srn_version(void);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* srn_last_error(void);
+
+/*
+ * Create a context for one network.  Copies *cfg and *params (the pointed-to
+ * device arrays are not copied and must outlive the context).  Allocates the
+ * device scratch of the fit / backward (sized by cfg->max_fit_points) and a
+ * small status word; nothing else allocates later.
+ */
+srn_status srn_create(const srn_config* cfg, const srn_params* params, srn_ctx** out);
+
+/* Free the context's scratch.  Waits for the device first. */
+srn_status srn_destroy(srn_ctx* ctx);
+
+/* Replace the parameter pointers (same shapes). */
+srn_status srn_set_params(srn_ctx* ctx, const srn_params* params);
+
+/* Write grid_h / weights_h as the round-to-nearest FP16 of grid / weights. */
+srn_status srn_sync_half(srn_ctx* ctx, void* stream);
+
+/*
+ * fV-SRN direct volume rendering (the hot path): for every time in
+ * times[0..n_times-1] (NULL: one frame at time 0) and every camera, render
+ * an H x W image.  rgba_dev receives float32 [n_times][n_views][H][W][4],
+ * premultiplied RGBA.  If samples_dev is not NULL the number of network
+ * density samples taken is ADDED to *samples_dev (uint64).  Allocates
+ * nothing (Section 6: fV-SRN decodes without temporary memory).
+ * precision FP32: CUDA-core FP32; FP16: tensor-core MMA with FP32 accumulate.
+ */
+srn_status srn_render(srn_ctx* ctx, const srn_camera* cams, int n_views, const float* times, int n_times,
+                      const srn_tf* tf, const srn_render_desc* desc, float* rgba_dev,
+                      unsigned long long* samples_dev, void* stream);
+
+/*
+ * Dense-grid DVR of a float32 volume (the plain method the network replaces;
+ * Section 4 renders the original volume as the reference).  Same ray march,
+ * density = trilinear interpolation of the volume; FD shading uses central
+ * differences with a one-voxel step.  dims = {nx, ny, nz}, each >= 2.
+ */
+srn_status srn_dvr_dense(const float* volume_dev, const int dims[3], const srn_camera* cams, int n_views,
+                         const srn_tf* tf, const srn_render_desc* desc, float* rgba_dev,
+                         unsigned long long* samples_dev, void* stream);
+
+/* Network output at n points (pts_dev float32 [n][3] in [0,1]^3) at one time:
+ * out_dev float32 [n][D].  FP32 arithmetic. */
+srn_status srn_eval(srn_ctx* ctx, const float* pts_dev, int n, float time, float* out_dev, void* stream);
+
+/* Density and its adjoint input gradient (Section 5 "Adjoint"): rho_dev [n],
+ * grad_dev [n][3] (d rho / d p; may be NULL).  FP32 arithmetic. */
+srn_status srn_density_grad(srn_ctx* ctx, const float* pts_dev, int n, float time, float* rho_dev,
+                            float* grad_dev, void* stream);
+
+/*
+ * Parameter gradients of sum_j <dout_j, net(p_j)> (backward of srn_eval):
+ * dgrid, dweights, dbiases are OVERWRITTEN (layouts of grid / weights /
+ * biases).  dout_dev float32 [n][D].  n <= cfg.max_fit_points.  Deterministic:
+ * the latent-grid gradient is gathered per vertex from points sorted by
+ * cell, with no floating-point atomics.
+ */
+srn_status srn_backward(srn_ctx* ctx, const float* pts_dev, int n, float time, const float* dout_dev,
+                        float* dgrid_dev, float* dweights_dev, float* dbiases_dev, void* stream);
+
+/*
+ * One training step (world-space fit): draw n_points positions with the
+ * counter-based Philox4x32-10 generator keyed by (seed, step), take the
+ * trilinear density of the volume there, L1 loss against the network output
+ * (plus grad_weight * L1 of the head's gradient outputs against grad_scale
+ * times central differences of the volume when D = 4), backpropagate, and
+ * apply Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias correction at step+1)
+ * with lr_grid on the latent grid and lr_net on weights and biases.  The
+ * keyframe time of the samples is `time`.  Writes the loss (float32) to
+ * loss_dev.  If the loss or any gradient is not finite the parameters are
+ * left unchanged and the context records SRN_ERR_NONFINITE, reported by
+ * srn_sync_status.  Also refreshes the FP16 copies when they exist.
+ */
+srn_status srn_fit_step(srn_ctx* ctx, const float* volume_dev, const int dims[3], int n_points, uint64_t seed,
+                        int step, float time, float lr_grid, float lr_net, float grad_weight, float grad_scale,
+                        float* loss_dev, void* stream);
+
+/* Synchronize `stream` and return (then clear) the device status word:
+ * SRN_OK, SRN_ERR_NONFINITE or SRN_ERR_INTERNAL. */
+srn_status srn_sync_status(srn_ctx* ctx, void* stream);
+
+/* Mean squared error over the RGB channels of n RGBA float32 pixels, the
+ * quantity behind the PSNR = 10 log10(1 / MSE) the paper reports for image
+ * quality (Section 6).  Writes one double to mse_dev; deterministic. */
+srn_status srn_image_mse(const float* a_dev, const float* b_dev, long long n_pixels, double* mse_dev,
+                         void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SRN_H */

@@ -1,0 +1,352 @@
+// C ABI of the library (include/srn.h): argument validation, context
+// management and kernel dispatch.  No computation happens here: every step
+// of the render / eval / fit path runs in the library's CUDA kernels.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "srn_fit.h"
+#include "srn_internal.h"
+
+using namespace srn;
+
+struct srn_ctx {
+  srn_config cfg;
+  srn_params prm;
+  int device;
+  unsigned int* status;       // device status word (SRN_OK / SRN_ERR_NONFINITE / SRN_ERR_INTERNAL)
+  unsigned long long* ray_counter;  // persistent-render work counter (8-byte aligned)
+  FitScratch fit;             // scratch of srn_fit_step / srn_backward
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+srn_status fail(srn_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+srn_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(SRN_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+srn_status check_config(const srn_config* c) {
+  if (!c) return fail(SRN_ERR_INVALID_ARG, "config is NULL");
+  if (c->grid_res < 2) return fail(SRN_ERR_INVALID_ARG, "grid_res must be >= 2");
+  if (c->feat < 4 || c->feat % 4) return fail(SRN_ERR_INVALID_ARG, "feat must be a positive multiple of 4");
+  if (c->n_fourier < 0) return fail(SRN_ERR_INVALID_ARG, "n_fourier must be >= 0");
+  if (c->layers < 2) return fail(SRN_ERR_INVALID_ARG, "layers must be >= 2");
+  if (c->layers > 8) return fail(SRN_ERR_UNSUPPORTED, "at most 8 layers are implemented");
+  if (c->out_dim != 1 && c->out_dim != 4) return fail(SRN_ERR_INVALID_ARG, "out_dim must be 1 or 4");
+  if (c->activation != SRN_ACT_SINE && c->activation != SRN_ACT_SNAKEALT)
+    return fail(SRN_ERR_INVALID_ARG, "unknown activation");
+  if (c->precision != SRN_PREC_FP32 && c->precision != SRN_PREC_FP16)
+    return fail(SRN_ERR_INVALID_ARG, "unknown precision");
+  if (c->n_keyframes < 1 || c->n_keyframes > SRN_MAX_KEYFRAMES)
+    return fail(SRN_ERR_INVALID_ARG, "n_keyframes must be in [1, %d]", SRN_MAX_KEYFRAMES);
+  for (int k = 1; k < c->n_keyframes; ++k)
+    if (!(c->key_times[k] > c->key_times[k - 1])) return fail(SRN_ERR_INVALID_ARG, "key_times must increase");
+  if (c->max_fit_points < 0) return fail(SRN_ERR_INVALID_ARG, "max_fit_points must be >= 0");
+  if (!render_fp32_supported(c->width)) return fail(SRN_ERR_UNSUPPORTED, "width %d is not implemented", c->width);
+  if (3 + 2 * c->n_fourier + c->feat > 256) return fail(SRN_ERR_UNSUPPORTED, "network input wider than 256");
+  if ((size_t)c->grid_res * c->grid_res * c->grid_res * c->feat * c->n_keyframes > (size_t)1 << 31)
+    return fail(SRN_ERR_UNSUPPORTED, "latent grid larger than 2^31 entries");
+  return SRN_OK;
+}
+
+srn_status check_params(const srn_config* c, const srn_params* p) {
+  if (!p) return fail(SRN_ERR_INVALID_ARG, "params is NULL");
+  if (!p->grid || !p->weights || !p->biases || (c->n_fourier > 0 && !p->fourier))
+    return fail(SRN_ERR_INVALID_ARG, "grid, weights, biases and fourier are required");
+  if (!aligned16(p->grid) || !aligned16(p->grid_h) || !aligned16(p->weights))
+    return fail(SRN_ERR_INVALID_ARG, "parameter arrays must be 16-byte aligned");
+  if (c->precision == SRN_PREC_FP16 && (!p->grid_h || !p->weights_h))
+    return fail(SRN_ERR_INVALID_ARG, "FP16 precision needs grid_h and weights_h");
+  return SRN_OK;
+}
+
+NetDev make_net(const srn_ctx* ctx) {
+  NetDev n;
+  const srn_config& c = ctx->cfg;
+  n.grid = ctx->prm.grid;
+  n.grid_h = reinterpret_cast<const __half*>(ctx->prm.grid_h);
+  n.fourier = ctx->prm.fourier;
+  n.W = ctx->prm.weights;
+  n.W_h = reinterpret_cast<const __half*>(ctx->prm.weights_h);
+  n.b = ctx->prm.biases;
+  n.R = c.grid_res; n.F = c.feat; n.m = c.n_fourier; n.l = c.layers; n.c = c.width; n.D = c.out_dim;
+  n.act = c.activation; n.nkey = c.n_keyframes;
+  for (int k = 0; k < SRN_MAX_KEYFRAMES; ++k) n.key_times[k] = k < c.n_keyframes ? c.key_times[k] : 0.0f;
+  return n;
+}
+
+srn_status fill_batch(BatchDev& b, const srn_camera* cams, int n_views, const float* times, int n_times,
+                      const srn_tf* tf, const srn_render_desc* desc, float* rgba, unsigned long long* samples,
+                      bool network) {
+  memset(&b, 0, sizeof(b));
+  if (!cams || n_views < 1 || n_views > SRN_MAX_VIEWS)
+    return fail(SRN_ERR_INVALID_ARG, "need 1..%d cameras", SRN_MAX_VIEWS);
+  if (n_times < 1 || n_times > SRN_MAX_TIMES) return fail(SRN_ERR_INVALID_ARG, "need 1..%d times", SRN_MAX_TIMES);
+  if (times == nullptr && n_times != 1) return fail(SRN_ERR_INVALID_ARG, "times is NULL but n_times != 1");
+  if (!tf || tf->n < 2 || tf->n > SRN_MAX_TF_POINTS || !tf->pos || !tf->rgba)
+    return fail(SRN_ERR_INVALID_ARG, "transfer function needs 2..%d points", SRN_MAX_TF_POINTS);
+  for (int i = 1; i < tf->n; ++i)
+    if (!(tf->pos[i] >= tf->pos[i - 1])) return fail(SRN_ERR_INVALID_ARG, "TF control points must be sorted");
+  if (!(tf->opacity_scale >= 0.0f) || !isfinite(tf->opacity_scale))
+    return fail(SRN_ERR_INVALID_ARG, "opacity_scale must be finite and >= 0");
+  if (!desc || desc->width < 1 || desc->height < 1) return fail(SRN_ERR_INVALID_ARG, "bad image size");
+  if (!(desc->step >= 1e-5f) || !isfinite(desc->step)) return fail(SRN_ERR_INVALID_ARG, "step must be >= 1e-5");
+  if (desc->shading < SRN_SHADE_NONE || desc->shading > SRN_SHADE_HEAD)
+    return fail(SRN_ERR_INVALID_ARG, "unknown shading mode");
+  if (network && desc->shading == SRN_SHADE_FD && !(desc->fd_h > 0.0f)) return fail(SRN_ERR_INVALID_ARG, "fd_h must be > 0");
+  if (!rgba || !aligned16(rgba)) return fail(SRN_ERR_INVALID_ARG, "rgba_dev must be a 16-byte aligned pointer");
+  if ((long long)desc->width * desc->height * n_views * n_times > (1ll << 34))
+    return fail(SRN_ERR_UNSUPPORTED, "batch too large");
+  for (int v = 0; v < n_views; ++v) {
+    const srn_camera& c = cams[v];
+    float f[3] = {c.target[0] - c.eye[0], c.target[1] - c.eye[1], c.target[2] - c.eye[2]};
+    float r[3] = {f[1] * c.up[2] - f[2] * c.up[1], f[2] * c.up[0] - f[0] * c.up[2], f[0] * c.up[1] - f[1] * c.up[0]};
+    if (f[0] * f[0] + f[1] * f[1] + f[2] * f[2] == 0.0f || r[0] * r[0] + r[1] * r[1] + r[2] * r[2] == 0.0f ||
+        !(c.fovy > 0.0f && c.fovy < 3.14159f))
+      return fail(SRN_ERR_INVALID_ARG, "camera %d is degenerate", v);
+    b.cams[v] = c;
+  }
+  for (int t = 0; t < n_times; ++t) b.times[t] = times ? times[t] : 0.0f;
+  b.n_views = n_views;
+  b.n_times = n_times;
+  b.W = desc->width;
+  b.H = desc->height;
+  b.step = desc->step;
+  b.et = desc->et_threshold;
+  b.shading = desc->shading;
+  b.fd_h = desc->fd_h;
+  b.tf.n = tf->n;
+  b.tf.opacity_scale = tf->opacity_scale;
+  for (int i = 0; i < SRN_MAX_TF_POINTS; ++i) {
+    int k = i < tf->n ? i : tf->n - 1;
+    b.tf.pos[i] = tf->pos[k];
+    b.tf.rgba[i] = make_float4(tf->rgba[4 * k], tf->rgba[4 * k + 1], tf->rgba[4 * k + 2], tf->rgba[4 * k + 3]);
+  }
+  b.out = rgba;
+  b.samples = samples;
+  return SRN_OK;
+}
+
+srn_status use_device(const srn_ctx* ctx) {
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (cur != ctx->device) return fail(SRN_ERR_INVALID_ARG, "context belongs to device %d, current is %d", ctx->device, cur);
+  return SRN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* srn_version(void) { return "fvsrn-gb300 0.1 (sm_103a)"; }
+
+const char* srn_last_error(void) { return g_err; }
+
+srn_status srn_create(const srn_config* cfg, const srn_params* params, srn_ctx** out) {
+  if (!out) return fail(SRN_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  srn_status st = check_config(cfg);
+  if (st) return st;
+  st = check_params(cfg, params);
+  if (st) return st;
+  srn_ctx* ctx = new (std::nothrow) srn_ctx;
+  if (!ctx) return fail(SRN_ERR_INTERNAL, "out of host memory");
+  memset(ctx, 0, sizeof(*ctx));
+  ctx->cfg = *cfg;
+  ctx->prm = *params;
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->status, 4 * sizeof(unsigned int));
+  if (e == cudaSuccess) {
+    ctx->ray_counter = reinterpret_cast<unsigned long long*>(ctx->status + 2);
+    e = cudaMemset(ctx->status, 0, 4 * sizeof(unsigned int));
+  }
+  if (e == cudaSuccess) e = fit_scratch_alloc(ctx->fit, make_net(ctx), cfg->max_fit_points);
+  if (e != cudaSuccess) {
+    fit_scratch_free(ctx->fit);
+    if (ctx->status) cudaFree(ctx->status);
+    delete ctx;
+    return cuda_fail(e, "srn_create");
+  }
+  *out = ctx;
+  return SRN_OK;
+}
+
+srn_status srn_destroy(srn_ctx* ctx) {
+  if (!ctx) return SRN_OK;
+  cudaDeviceSynchronize();
+  fit_scratch_free(ctx->fit);
+  if (ctx->status) cudaFree(ctx->status);
+  delete ctx;
+  return SRN_OK;
+}
+
+srn_status srn_set_params(srn_ctx* ctx, const srn_params* params) {
+  if (!ctx) return fail(SRN_ERR_INVALID_ARG, "ctx is NULL");
+  srn_status st = check_params(&ctx->cfg, params);
+  if (st) return st;
+  ctx->prm = *params;
+  return SRN_OK;
+}
+
+srn_status srn_sync_half(srn_ctx* ctx, void* stream) {
+  if (!ctx) return fail(SRN_ERR_INVALID_ARG, "ctx is NULL");
+  if (!ctx->prm.grid_h || !ctx->prm.weights_h) return fail(SRN_ERR_INVALID_ARG, "no FP16 copies to write");
+  srn_status st = use_device(ctx);
+  if (st) return st;
+  NetDev n = make_net(ctx);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = launch_to_half(n.grid, (__half*)ctx->prm.grid_h, net_grid_count(n), s);
+  if (e == cudaSuccess) e = launch_to_half(n.W, (__half*)ctx->prm.weights_h, net_weight_count(n), s);
+  return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_sync_half");
+}
+
+srn_status srn_render(srn_ctx* ctx, const srn_camera* cams, int n_views, const float* times, int n_times,
+                      const srn_tf* tf, const srn_render_desc* desc, float* rgba_dev,
+                      unsigned long long* samples_dev, void* stream) {
+  if (!ctx) return fail(SRN_ERR_INVALID_ARG, "ctx is NULL");
+  BatchDev b;
+  srn_status st = fill_batch(b, cams, n_views, times, n_times, tf, desc, rgba_dev, samples_dev, true);
+  if (st) return st;
+  if (desc->shading == SRN_SHADE_HEAD && ctx->cfg.out_dim != 4)
+    return fail(SRN_ERR_INVALID_ARG, "head shading needs out_dim 4");
+  st = use_device(ctx);
+  if (st) return st;
+  NetDev n = make_net(ctx);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (ctx->cfg.precision == SRN_PREC_FP16) {
+    if (!render_mma_supported(n, desc->shading))
+      return fail(SRN_ERR_UNSUPPORTED, "FP16 tensor-core render does not implement this shape / shading");
+    e = launch_render_mma(n, b, ctx->ray_counter, ctx->status, s);
+  } else {
+    e = launch_render_fp32(n, b, s);
+  }
+  return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_render");
+}
+
+srn_status srn_dvr_dense(const float* volume_dev, const int dims[3], const srn_camera* cams, int n_views,
+                         const srn_tf* tf, const srn_render_desc* desc, float* rgba_dev,
+                         unsigned long long* samples_dev, void* stream) {
+  if (!volume_dev || !dims) return fail(SRN_ERR_INVALID_ARG, "volume and dims are required");
+  if (dims[0] < 2 || dims[1] < 2 || dims[2] < 2) return fail(SRN_ERR_INVALID_ARG, "volume dims must be >= 2");
+  BatchDev b;
+  srn_status st = fill_batch(b, cams, n_views, nullptr, 1, tf, desc, rgba_dev, samples_dev, false);
+  if (st) return st;
+  if (desc->shading != SRN_SHADE_NONE && desc->shading != SRN_SHADE_FD)
+    return fail(SRN_ERR_INVALID_ARG, "dense DVR shades by central differences only");
+  VolDev v{volume_dev, dims[0], dims[1], dims[2]};
+  cudaError_t e = launch_dvr_dense(v, b, (cudaStream_t)stream);
+  return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_dvr_dense");
+}
+
+srn_status srn_eval(srn_ctx* ctx, const float* pts_dev, int n, float time, float* out_dev, void* stream) {
+  if (!ctx) return fail(SRN_ERR_INVALID_ARG, "ctx is NULL");
+  if (n < 0 || (n > 0 && (!pts_dev || !out_dev))) return fail(SRN_ERR_INVALID_ARG, "bad points / output");
+  srn_status st = use_device(ctx);
+  if (st) return st;
+  cudaError_t e = launch_eval_fp32(make_net(ctx), pts_dev, n, time, out_dev, nullptr, 0, (cudaStream_t)stream);
+  return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_eval");
+}
+
+srn_status srn_density_grad(srn_ctx* ctx, const float* pts_dev, int n, float time, float* rho_dev,
+                            float* grad_dev, void* stream) {
+  if (!ctx) return fail(SRN_ERR_INVALID_ARG, "ctx is NULL");
+  if (n < 0 || (n > 0 && (!pts_dev || !rho_dev))) return fail(SRN_ERR_INVALID_ARG, "bad points / output");
+  srn_status st = use_device(ctx);
+  if (st) return st;
+  cudaError_t e = launch_eval_fp32(make_net(ctx), pts_dev, n, time, rho_dev, grad_dev, 1, (cudaStream_t)stream);
+  return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_density_grad");
+}
+
+srn_status srn_backward(srn_ctx* ctx, const float* pts_dev, int n, float time, const float* dout_dev,
+                        float* dgrid_dev, float* dweights_dev, float* dbiases_dev, void* stream) {
+  if (!ctx) return fail(SRN_ERR_INVALID_ARG, "ctx is NULL");
+  if (n < 0 || n > ctx->cfg.max_fit_points)
+    return fail(SRN_ERR_INVALID_ARG, "n must be in [0, max_fit_points=%d]", ctx->cfg.max_fit_points);
+  if (n > 0 && (!pts_dev || !dout_dev)) return fail(SRN_ERR_INVALID_ARG, "points and dout are required");
+  if (!dgrid_dev || !dweights_dev || !dbiases_dev) return fail(SRN_ERR_INVALID_ARG, "gradient outputs are required");
+  srn_status st = use_device(ctx);
+  if (st) return st;
+  cudaError_t e = launch_backward(ctx->fit, make_net(ctx), pts_dev, n, time, dout_dev, dgrid_dev, dweights_dev,
+                                  dbiases_dev, (cudaStream_t)stream);
+  return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_backward");
+}
+
+srn_status srn_fit_step(srn_ctx* ctx, const float* volume_dev, const int dims[3], int n_points, uint64_t seed,
+                        int step, float time, float lr_grid, float lr_net, float grad_weight, float grad_scale,
+                        float* loss_dev, void* stream) {
+  if (!ctx) return fail(SRN_ERR_INVALID_ARG, "ctx is NULL");
+  if (!volume_dev || !dims || dims[0] < 2 || dims[1] < 2 || dims[2] < 2)
+    return fail(SRN_ERR_INVALID_ARG, "volume with dims >= 2 is required");
+  if (n_points < 1 || n_points > ctx->cfg.max_fit_points)
+    return fail(SRN_ERR_INVALID_ARG, "n_points must be in [1, max_fit_points=%d]", ctx->cfg.max_fit_points);
+  if (step < 0) return fail(SRN_ERR_INVALID_ARG, "step must be >= 0");
+  if (!ctx->prm.adam_m || !ctx->prm.adam_v) return fail(SRN_ERR_INVALID_ARG, "Adam moments are required");
+  if (!loss_dev) return fail(SRN_ERR_INVALID_ARG, "loss_dev is required");
+  if (!(lr_grid >= 0.0f) || !(lr_net >= 0.0f)) return fail(SRN_ERR_INVALID_ARG, "learning rates must be >= 0");
+  srn_status st = use_device(ctx);
+  if (st) return st;
+  FitArgs a;
+  a.vol = VolDev{volume_dev, dims[0], dims[1], dims[2]};
+  a.n = n_points;
+  a.seed = seed;
+  a.step = step;
+  a.time = time;
+  a.lr_grid = lr_grid;
+  a.lr_net = lr_net;
+  a.grad_weight = grad_weight;
+  a.grad_scale = grad_scale;
+  a.loss = loss_dev;
+  a.status = ctx->status;
+  a.grid_h = reinterpret_cast<__half*>(ctx->prm.grid_h);
+  a.weights_h = reinterpret_cast<__half*>(ctx->prm.weights_h);
+  a.adam_m = ctx->prm.adam_m;
+  a.adam_v = ctx->prm.adam_v;
+  a.grid = ctx->prm.grid;
+  a.weights = ctx->prm.weights;
+  a.biases = ctx->prm.biases;
+  cudaError_t e = launch_fit_step(ctx->fit, make_net(ctx), a, (cudaStream_t)stream);
+  return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_fit_step");
+}
+
+srn_status srn_sync_status(srn_ctx* ctx, void* stream) {
+  if (!ctx) return fail(SRN_ERR_INVALID_ARG, "ctx is NULL");
+  unsigned int word = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(&word, ctx->status, sizeof(word), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->status, 0, sizeof(unsigned int), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "srn_sync_status");
+  if (word == SRN_ERR_NONFINITE) return fail(SRN_ERR_NONFINITE, "a fit step produced a non-finite loss or gradient");
+  if (word == SRN_ERR_TIMEOUT) return fail(SRN_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (word != 0) return fail(SRN_ERR_INTERNAL, "device status word %u", word);
+  return SRN_OK;
+}
+
+srn_status srn_image_mse(const float* a_dev, const float* b_dev, long long n_pixels, double* mse_dev,
+                         void* stream) {
+  if (n_pixels < 0 || !mse_dev || (n_pixels > 0 && (!a_dev || !b_dev)))
+    return fail(SRN_ERR_INVALID_ARG, "bad image arguments");
+  if (!aligned16(a_dev) || !aligned16(b_dev)) return fail(SRN_ERR_INVALID_ARG, "images must be 16-byte aligned");
+  cudaError_t e = launch_image_mse(a_dev, b_dev, n_pixels, mse_dev, (cudaStream_t)stream);
+  return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_image_mse");
+}
+
+}  // extern "C"

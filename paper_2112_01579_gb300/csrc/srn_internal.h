@@ -1,0 +1,81 @@
+// Internal declarations shared by the CUDA translation units of the library.
+// Not part of the public C ABI (include/srn.h).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "srn.h"
+
+namespace srn {
+
+// Transfer function copied into kernel parameters (Section 3 TF mapping).
+struct TFDev {
+  int n;
+  float opacity_scale;
+  float pos[SRN_MAX_TF_POINTS];
+  float4 rgba[SRN_MAX_TF_POINTS];
+};
+
+// Network description as seen by kernels.  Layer i maps d_i -> d_{i+1} with
+// d_0 = 3 + 2m + F, hidden width c, output D (Section 3 layer equation).
+struct NetDev {
+  const float* grid;     // fp32 [nkey][R][R][R][F]
+  const __half* grid_h;  // fp16 copy (FP16 path)
+  const float* fourier;  // [m][3]
+  const float* W;        // packed row-major layers
+  const __half* W_h;     // fp16 copy of W
+  const float* b;        // packed biases
+  int R, F, m, l, c, D, act, nkey;
+  float key_times[SRN_MAX_KEYFRAMES];
+};
+
+// One render batch: n_times x n_views frames of H x W pixels.
+struct BatchDev {
+  srn_camera cams[SRN_MAX_VIEWS];
+  float times[SRN_MAX_TIMES];
+  int n_views, n_times;
+  int W, H;
+  float step, et;
+  int shading;
+  float fd_h;
+  TFDev tf;
+  float* out;                     // [n_times][n_views][H][W][4]
+  unsigned long long* samples;    // nullable
+};
+
+// Dense volume source for the plain DVR.
+struct VolDev {
+  const float* vol;  // [nz][ny][nx]
+  int nx, ny, nz;
+};
+
+// Launchers (return the cudaGetLastError of the launch).
+cudaError_t launch_render_fp32(const NetDev& net, const BatchDev& b, cudaStream_t s);
+cudaError_t launch_dvr_dense(const VolDev& v, const BatchDev& b, cudaStream_t s);
+cudaError_t launch_eval_fp32(const NetDev& net, const float* pts, int n, float time, float* out, float* grad,
+                             int mode, cudaStream_t s);  // mode 0: out[n][D]; 1: rho[n] + grad[n][3]
+bool render_fp32_supported(int width);
+
+// FP16 tensor-core render (tcgen05 / TMEM).
+cudaError_t launch_render_mma(const NetDev& net, const BatchDev& b, unsigned long long* ray_counter,
+                              unsigned int* status, cudaStream_t s);
+bool render_mma_supported(const NetDev& net, int shading);
+
+// Conversions and small utilities.
+cudaError_t launch_to_half(const float* src, __half* dst, size_t n, cudaStream_t s);
+cudaError_t launch_image_mse(const float* a, const float* b, long long n, double* out, cudaStream_t s);
+
+// Layer shapes of a network.
+inline int net_d0(const NetDev& n) { return 3 + 2 * n.m + n.F; }
+inline size_t net_weight_count(const NetDev& n) {
+  size_t t = (size_t)n.c * net_d0(n);
+  t += (size_t)(n.l - 2) * n.c * n.c;
+  t += (size_t)n.D * n.c;
+  return t;
+}
+inline size_t net_bias_count(const NetDev& n) { return (size_t)(n.l - 1) * n.c + n.D; }
+inline size_t net_grid_count(const NetDev& n) { return (size_t)n.nkey * n.R * n.R * n.R * n.F; }
+
+}  // namespace srn

@@ -1,0 +1,622 @@
+// FP16 tensor-core fV-SRN render for sm_103a: tcgen05.mma with TMEM
+// accumulators, persistent CTAs, one thread per ray.
+//
+// Design (GB300-first restatement of the fused TensorCore network of
+// Section 4.1):
+// * A CTA holds 4 warpgroups.  Each warpgroup owns a tile of 128 rays, one
+//   per thread; thread i of the warpgroup is row i of the MMA operand A and
+//   TMEM lane i of the accumulator, so the per-ray work (ray stepping,
+//   latent-grid trilinear fetch, Fourier features, transfer function,
+//   compositing, early termination) stays one thread per ray as in the paper,
+//   while the layers run as M=128 x N=32 tensor-core MMAs.
+// * Every sample: the thread writes its FP16 layer-0 input row [p, sin(Fp),
+//   cos(Fp), z, 1] into a 128B-swizzled shared-memory tile; one elected
+//   thread issues tcgen05.mma (kind::f16, FP32 accumulate in TMEM); the
+//   thread reads its row back with tcgen05.ld, applies the activation in FP32
+//   and writes the FP16 result as the next layer's A row.  Biases ride in the
+//   MMA through a constant-1 input column.  The last layer (32 -> D) runs on
+//   the CUDA cores in FP32.
+// * Rays are claimed dynamically (warp-aggregated atomic on a work counter);
+//   a thread whose ray terminates (box exit or opacity >= threshold) writes
+//   its pixel and takes the next ray, so tiles stay full.
+// * Every mbarrier wait is bounded; on timeout the warpgroup stops, records
+//   SRN_ERR_TIMEOUT in the status word and the CTA frees its TMEM.
+#include "srn_device.cuh"
+
+namespace srn {
+namespace {
+
+constexpr int kWG = 4;                 // warpgroups per CTA
+constexpr int kThreads = 128 * kWG;    // 512 threads, one CTA per SM
+constexpr int kTile = 128 * 128;       // one A tile: 128 rows x 128 B (64 fp16)
+constexpr int kBTile = 32 * 128;       // one B tile: 32 rows x 128 B
+constexpr int kTmemCols = 32 * kWG;    // one 32-column FP32 accumulator per warpgroup
+constexpr long long kWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: gives up after kWaitCycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t a, uint32_t parity) {
+  if (mbar_try_wait(a, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(a, parity)) {
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void bar_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ bool bar_red_or(int id, int n, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred q, p;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.or.pred p, %2, %3, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(id), "r"(n)
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (FP16 inputs, FP32 accumulate).
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+// Thread's TMEM lane, 32 consecutive FP32 columns, waited for.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms
+// 1024 bytes apart (SBO), sm100 descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;              // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024u >> 4) << 32;    // stride byte offset
+  d |= (uint64_t)1u << 46;              // descriptor version
+  d |= (uint64_t)2u << 61;              // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor: kind::f16, A = B = FP16, D = FP32, both K-major,
+// N = 32, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+// Byte offset of 16-byte chunk j of row r in a 128B-swizzled tile.
+__device__ __forceinline__ uint32_t sw_off(int r, int j) { return (uint32_t)(r * 128 + ((j ^ (r & 7)) << 4)); }
+
+__device__ __forceinline__ uint32_t pack_h2(float a, float b) {
+  __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+template <int ACT>
+__device__ __forceinline__ float act_fast(float x) {
+  float s = __sinf(x);
+  return ACT == SRN_ACT_SNAKEALT ? fmaf(s, s, 0.5f * x) : s;
+}
+
+// ---------------------------------------------------------------- layout
+struct SmemPlan {
+  int oA0, oAh, oB, oWl, oTF, oFm, oMbar, oMisc, total;
+};
+
+SmemPlan make_plan(const NetDev& n) {
+  SmemPlan s;
+  int o = 0;
+  s.oA0 = o; o += kWG * kTile;
+  s.oAh = o; o += kWG * kTile;
+  s.oB = o; o += (n.l - 1) * kBTile;
+  s.oWl = o; o += (n.D * 32 + 4) * 4;
+  o = (o + 15) & ~15;
+  s.oTF = o; o += (int)sizeof(TFDev);
+  o = (o + 15) & ~15;
+  s.oFm = o; o += ((3 * n.m + 3) & ~3) * 4 + 16;
+  o = (o + 7) & ~7;
+  s.oMbar = o; o += 8 * kWG;
+  s.oMisc = o; o += 16 * 4;
+  s.total = o + 1024;  // alignment slack
+  return s;
+}
+
+struct RayLat {
+  int g0, g1;     // element offsets of the bracketing keyframe grids (g1 < 0: single grid)
+  float w0, w1;   // time weights
+};
+
+// Latent vector (Section 4.2 trilinear latent grid; Section 7 time blend)
+// from the FP16 grid, accumulated in FP32.
+template <int F>
+__device__ __forceinline__ void latent_h(const __half* __restrict__ G, int R, const RayLat& rl, float3 p,
+                                         float (&z)[F]) {
+  int ix, iy, iz;
+  float fx, fy, fz;
+  cell_coord(p.x, R, ix, fx);
+  cell_coord(p.y, R, iy, fy);
+  cell_coord(p.z, R, iz, fz);
+  const int sx = F, sy = R * F, sz = R * R * F;
+  const int base = iz * sz + iy * sy + ix * sx;
+#pragma unroll
+  for (int f = 0; f < F; ++f) z[f] = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+    const float w = (dx ? fx : 1.0f - fx) * (dy ? fy : 1.0f - fy) * (dz ? fz : 1.0f - fz);
+    const int off = base + dx * sx + dy * sy + dz * sz;
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+      const int g = kk ? rl.g1 : rl.g0;
+      if (kk && g < 0) break;
+      const float ww = w * (kk ? rl.w1 : rl.w0);
+#pragma unroll
+      for (int c = 0; c < F; c += 8) {
+        uint4 q = __ldg(reinterpret_cast<const uint4*>(G + g + off + c));
+        const __half2* h = reinterpret_cast<const __half2*>(&q);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          float2 v = __half22float2(h[e]);
+          z[c + 2 * e] = fmaf(ww, v.x, z[c + 2 * e]);
+          z[c + 2 * e + 1] = fmaf(ww, v.y, z[c + 2 * e + 1]);
+        }
+      }
+    }
+  }
+}
+
+// Layer-0 input row [p, sin(Fp), cos(Fp), z, 1, 0...] (Eq. 1-2 features),
+// written in FP16 into the thread's row of the swizzled A tile.
+template <int M, int F, int K0>
+__device__ __forceinline__ void write_input_row(uint8_t* tile, int row, float3 p, bool nerf, const float* fm,
+                                                const __half* G, int R, const RayLat& rl) {
+  constexpr int D0 = 3 + 2 * M + F;
+  float v[K0];
+  v[0] = p.x;
+  v[1] = p.y;
+  v[2] = p.z;
+  if (nerf) {
+    // NeRF rows are 2 pi 2^(k div 3) along axis k mod 3: one sincospi per
+    // axis, then exact angle doubling sin 2t = 2 s c, cos 2t = (c - s)(c + s).
+    float s[3], c[3];
+    sincospif(2.0f * p.x, &s[0], &c[0]);
+    sincospif(2.0f * p.y, &s[1], &c[1]);
+    sincospif(2.0f * p.z, &s[2], &c[2]);
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      const int a = k % 3;
+      if (k >= 3) {
+        const float ss = s[a], cc = c[a];
+        s[a] = 2.0f * ss * cc;
+        c[a] = (cc - ss) * (cc + ss);
+      }
+      v[3 + k] = s[a];
+      v[3 + M + k] = c[a];
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      const float e = fm[3 * k] * p.x + fm[3 * k + 1] * p.y + fm[3 * k + 2] * p.z;
+      sincosf(e, &v[3 + k], &v[3 + M + k]);
+    }
+  }
+  float z[F];
+  latent_h<F>(G, R, rl, p, z);
+#pragma unroll
+  for (int f = 0; f < F; ++f) v[3 + 2 * M + f] = z[f];
+  v[D0] = 1.0f;
+#pragma unroll
+  for (int i = D0 + 1; i < K0; ++i) v[i] = 0.0f;
+#pragma unroll
+  for (int j = 0; j < K0 / 8; ++j) {
+    uint4 q;
+    q.x = pack_h2(v[8 * j], v[8 * j + 1]);
+    q.y = pack_h2(v[8 * j + 2], v[8 * j + 3]);
+    q.z = pack_h2(v[8 * j + 4], v[8 * j + 5]);
+    q.w = pack_h2(v[8 * j + 6], v[8 * j + 7]);
+    *reinterpret_cast<uint4*>(tile + sw_off(row, j)) = q;
+  }
+}
+
+// ---------------------------------------------------------------- kernel
+template <int M, int F, int ACT, int SH>
+__global__ void __launch_bounds__(kThreads, 1)
+    render_mma_kernel(const NetDev net, const BatchDev b, const SmemPlan plan, unsigned long long* __restrict__ ray_counter,
+                      unsigned int* __restrict__ status) {
+  constexpr int D0 = 3 + 2 * M + F;
+  constexpr int K0 = ((D0 + 1 + 15) / 16) * 16;
+  static_assert(K0 <= 64, "layer-0 input must fit one 128-byte row");
+  constexpr int NP = SH == SRN_SHADE_FD ? 7 : 1;  // network passes per sample
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* A0all = sm + plan.oA0;
+  uint8_t* Ahall = sm + plan.oAh;
+  uint8_t* Bw = sm + plan.oB;
+  float* wl = reinterpret_cast<float*>(sm + plan.oWl);
+  TFDev& tf = *reinterpret_cast<TFDev*>(sm + plan.oTF);
+  float* fm = reinterpret_cast<float*>(sm + plan.oFm);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + plan.oMbar);
+  volatile int* misc = reinterpret_cast<volatile int*>(sm + plan.oMisc);  // [0] tmem base, [1] nerf, [4+wg] fail
+
+  const int tid = threadIdx.x;
+  const int wg = tid >> 7, row = tid & 127, lane = tid & 31;
+  const int L = net.l, D = net.D;
+
+  // ---- stage parameters: MMA layers as 32 x 64 FP16 B tiles (row o = output
+  // neuron, K-major, bias in column d_in), last layer FP32, TF, Fourier rows.
+  for (int it = tid; it < (L - 1) * 32 * 8; it += kThreads) {
+    const int layer = it / 256, o = (it >> 3) & 31, j = it & 7;
+    const int din = layer == 0 ? D0 : 32;
+    const __half* Wsrc = net.W_h + (layer == 0 ? 0 : (size_t)32 * D0 + (size_t)(layer - 1) * 32 * 32);
+    const float bias = net.b[layer * 32 + o];
+    uint32_t w[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float a[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int col = 8 * j + 2 * e + h;
+        a[h] = col < din ? __half2float(Wsrc[(size_t)o * din + col]) : (col == din ? bias : 0.0f);
+      }
+      w[e] = pack_h2(a[0], a[1]);
+    }
+    *reinterpret_cast<uint4*>(Bw + layer * kBTile + sw_off(o, j)) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  {
+    const __half* Wl = net.W_h + (size_t)32 * D0 + (size_t)(L - 2) * 32 * 32;
+    for (int i = tid; i < D * 32; i += kThreads) wl[i] = __half2float(Wl[i]);
+    if (tid < D) wl[D * 32 + tid] = net.b[(L - 1) * 32 + tid];
+    for (int i = tid; i < 3 * M; i += kThreads) fm[i] = net.fourier[i];
+  }
+  load_tf(tf, b.tf);
+  // zero the thread's A rows; the hidden tile carries the constant-1 bias column at 32
+  {
+    uint8_t* A0 = A0all + wg * kTile;
+    uint8_t* Ah = Ahall + wg * kTile;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      *reinterpret_cast<uint4*>(A0 + sw_off(row, j)) = make_uint4(0, 0, 0, 0);
+      uint4 q = make_uint4(0, 0, 0, 0);
+      if (j == 4) q.x = pack_h2(1.0f, 0.0f);
+      *reinterpret_cast<uint4*>(Ah + sw_off(row, j)) = q;
+    }
+  }
+  if (row == 0) {
+    mbar_init(smem_u32(&mbar[wg]), 1);
+    misc[4 + wg] = 0;
+  }
+  if (tid < 32) {
+    tmem_alloc(smem_u32((const void*)&misc[0]), kTmemCols);
+    tmem_relinquish();
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (tid == 0) {
+    int ok = 1;
+    // row k of a NeRF matrix: 2 pi 2^(k div 3) on axis k mod 3, zero elsewhere
+    for (int k = 0; k < M && ok; ++k)
+      for (int a = 0; a < 3; ++a) {
+        const float want = (a == k % 3) ? 6.2831855f * (float)(1 << (k / 3)) : 0.0f;
+        if (fm[3 * k + a] != want) ok = 0;
+      }
+    misc[1] = ok;
+  }
+  __syncthreads();
+  const bool nerf = misc[1] != 0;
+  const uint32_t tmem = (uint32_t)misc[0];
+  const uint32_t d_tmem = tmem + (uint32_t)(wg * 32);
+  const uint32_t t_row = d_tmem + ((uint32_t)((row >> 5) * 32) << 16);  // warp's lane quarter
+  uint8_t* A0 = A0all + wg * kTile;
+  uint8_t* Ah = Ahall + wg * kTile;
+  const uint32_t a0_addr = smem_u32(A0), ah_addr = smem_u32(Ah), b_addr = smem_u32(Bw);
+  const uint32_t mb = smem_u32(&mbar[wg]);
+  const int bar_id = 1 + wg;
+
+  // ---- ray state
+  const int tiles_x = (b.W + 7) / 8, tiles_y = (b.H + 3) / 4;
+  const long long tpf = (long long)tiles_x * tiles_y;
+  const long long n_rays = tpf * 32 * b.n_views * b.n_times;
+  const size_t gsz = (size_t)net.R * net.R * net.R * net.F;
+  bool active = false, exhausted = false, failed = false;
+  long long pix = 0;
+  float3 o = make_float3(0.f, 0.f, 0.f), d = o;
+  float t0 = 0.f, t1 = 0.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
+  int k = 0, pass = 0;
+  RayLat rl{0, -1, 1.0f, 0.0f};
+  float rho_c = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+  unsigned int ns = 0;
+  uint32_t phase = 0;
+
+  while (true) {
+    // ---- refill: threads without a ray claim new ones (warp-aggregated)
+    while (true) {
+      const bool need = !active && !exhausted && !failed;
+      const unsigned int mask = __ballot_sync(0xffffffffu, need);
+      if (mask == 0) break;
+      unsigned long long base = 0;
+      const int leader = __ffs(mask) - 1;
+      if (lane == leader) base = atomicAdd(ray_counter, (unsigned long long)__popc(mask));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (need) {
+        const long long r = (long long)base + __popc(mask & ((1u << lane) - 1u));
+        if (r >= n_rays) {
+          exhausted = true;
+        } else {
+          const long long tile = r >> 5;
+          const int li = (int)(r & 31);
+          const long long frame = tile / tpf;
+          const int tt = (int)(tile - frame * tpf);
+          const int px = (tt % tiles_x) * 8 + (li & 7), py = (tt / tiles_x) * 4 + (li >> 3);
+          if (px < b.W && py < b.H) {
+            const int view = (int)(frame % b.n_views), ti = (int)(frame / b.n_views);
+            pix = (frame * b.H + py) * (long long)b.W + px;
+            camera_ray(b.cams[view], b.W, b.H, px, py, o, d);
+            if (box_intersect(o, d, t0, t1)) {
+              int k0;
+              float f;
+              time_weights(net, b.times[ti], k0, f);
+              rl.g0 = (int)(k0 * gsz);
+              rl.g1 = net.nkey > 1 ? (int)((k0 + 1) * gsz) : -1;
+              rl.w0 = net.nkey > 1 ? 1.0f - f : 1.0f;
+              rl.w1 = f;
+              C0 = C1 = C2 = A = 0.f;
+              k = 0;
+              pass = 0;
+              active = true;
+            } else {
+              reinterpret_cast<float4*>(b.out)[pix] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+          }
+        }
+      }
+    }
+
+    // ---- layer-0 input of this pass
+    float ta = 0.f, len = 0.f;
+    float3 p = make_float3(0.f, 0.f, 0.f);
+    if (active && !failed) {
+      ta = fmaf((float)k, b.step, t0);
+      const float tb = fminf(fmaf((float)(k + 1), b.step, t0), t1);
+      len = tb - ta;
+      const float tm = 0.5f * (ta + tb);
+      p = make_float3(clamp01f(fmaf(tm, d.x, o.x) + 0.5f), clamp01f(fmaf(tm, d.y, o.y) + 0.5f),
+                      clamp01f(fmaf(tm, d.z, o.z) + 0.5f));
+      float3 q = p;
+      if (SH == SRN_SHADE_FD && pass > 0) {
+        const int ax = (pass - 1) >> 1;
+        const float h = (pass & 1) ? b.fd_h : -b.fd_h;
+        if (ax == 0) q.x = clamp01f(p.x + h);
+        if (ax == 1) q.y = clamp01f(p.y + h);
+        if (ax == 2) q.z = clamp01f(p.z + h);
+      }
+      write_input_row<M, F, K0>(A0, row, q, nerf, fm, net.grid_h, net.R, rl);
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    const bool any = bar_red_or(bar_id, 128, active && !failed);
+    if (!any || misc[4 + wg]) break;
+    if (row == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int kk = 0; kk < K0 / 16; ++kk)
+        mma_f16(d_tmem, sw128_desc(a0_addr + kk * 32), sw128_desc(b_addr + kk * 32), kIdesc, kk > 0);
+      mma_commit(mb);
+    }
+
+    // ---- layers: wait, read the accumulator row, activation, next MMA
+    float out[4] = {0.f, 0.f, 0.f, 0.f};
+    bool stop = false;
+    for (int layer = 0; layer < L - 1; ++layer) {
+      // the failure decision is warp-uniform so tcgen05.ld stays convergent;
+      // a failed thread keeps arriving at the warpgroup barriers, which all
+      // threads leave together once the flag is visible
+      if (!__all_sync(0xffffffffu, mbar_wait_bounded(mb, phase))) {
+        failed = true;
+        misc[4 + wg] = 1;
+      }
+      phase ^= 1u;
+      tc_fence_after();
+      float x[32];
+      if (!failed) tmem_ld32(t_row, x);
+      if (layer < L - 2) {
+        if (!failed) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            uint4 q;
+            q.x = pack_h2(act_fast<ACT>(x[8 * j]), act_fast<ACT>(x[8 * j + 1]));
+            q.y = pack_h2(act_fast<ACT>(x[8 * j + 2]), act_fast<ACT>(x[8 * j + 3]));
+            q.z = pack_h2(act_fast<ACT>(x[8 * j + 4]), act_fast<ACT>(x[8 * j + 5]));
+            q.w = pack_h2(act_fast<ACT>(x[8 * j + 6]), act_fast<ACT>(x[8 * j + 7]));
+            *reinterpret_cast<uint4*>(Ah + sw_off(row, j)) = q;
+          }
+        }
+        fence_proxy_async();
+        tc_fence_before();
+        bar_sync(bar_id, 128);
+        if (misc[4 + wg]) { stop = true; break; }
+        if (row == 0) {
+          tc_fence_after();
+          const uint32_t bl = b_addr + (layer + 1) * kBTile;
+#pragma unroll
+          for (int kk = 0; kk < 3; ++kk)
+            mma_f16(d_tmem, sw128_desc(ah_addr + kk * 32), sw128_desc(bl + kk * 32), kIdesc, kk > 0);
+          mma_commit(mb);
+        }
+      } else if (!failed) {
+        float a[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) a[j] = act_fast<ACT>(x[j]);
+#pragma unroll
+        for (int dd = 0; dd < 4; ++dd) {
+          if (dd < D) {
+            float s = wl[D * 32 + dd];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) s = fmaf(wl[dd * 32 + j], a[j], s);
+            out[dd] = s;
+          }
+        }
+      }
+    }
+    if (stop) break;
+
+    // ---- transfer function, shading, compositing, termination
+    if (active && !failed) {
+      bool sample_done = true;
+      float3 g = make_float3(0.f, 0.f, 0.f);
+      if (SH == SRN_SHADE_FD) {
+        if (pass == 0) rho_c = out[0];
+        else if (pass == 1) gx = out[0];
+        else if (pass == 2) gx = (gx - out[0]) / (2.0f * b.fd_h);
+        else if (pass == 3) gy = out[0];
+        else if (pass == 4) gy = (gy - out[0]) / (2.0f * b.fd_h);
+        else if (pass == 5) gz = out[0];
+        else gz = (gz - out[0]) / (2.0f * b.fd_h);
+        sample_done = pass == NP - 1;
+        pass = sample_done ? 0 : pass + 1;
+        g = make_float3(gx, gy, gz);
+      } else {
+        rho_c = out[0];
+        if (SH == SRN_SHADE_HEAD) g = make_float3(out[1], out[2], out[3]);
+      }
+      if (sample_done) {
+        ++ns;
+        float4 c = tf_eval(tf, rho_c);
+        const float alpha = 1.0f - __expf(-c.w * tf.opacity_scale * len);
+        if (SH != SRN_SHADE_NONE) shade(c, g, d);
+        const float w = (1.0f - A) * alpha;
+        C0 = fmaf(w, c.x, C0);
+        C1 = fmaf(w, c.y, C1);
+        C2 = fmaf(w, c.z, C2);
+        A += w;
+        ++k;
+        if (A >= b.et || fmaf((float)k, b.step, t0) >= t1) {
+          reinterpret_cast<float4*>(b.out)[pix] = make_float4(C0, C1, C2, A);
+          active = false;
+        }
+      }
+    }
+  }
+
+  if (failed || misc[4 + wg]) {
+    if (row == 0) atomicExch(status, (unsigned int)SRN_ERR_TIMEOUT);
+  }
+  add_samples(b.samples, ns);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (tid < 32) tmem_dealloc(tmem, kTmemCols);
+}
+
+template <int M, int F, int ACT, int SH>
+cudaError_t launch_t(const NetDev& net, const BatchDev& b, unsigned long long* ctr, unsigned int* status,
+                     cudaStream_t s) {
+  SmemPlan plan = make_plan(net);
+  auto k = render_mma_kernel<M, F, ACT, SH>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  k<<<sms, kThreads, plan.total, s>>>(net, b, plan, ctr, status);
+  return cudaGetLastError();
+}
+
+template <int M, int F, int ACT>
+cudaError_t dispatch_shading(const NetDev& net, const BatchDev& b, unsigned long long* ctr, unsigned int* st,
+                             cudaStream_t s) {
+  switch (b.shading) {
+    case SRN_SHADE_NONE: return launch_t<M, F, ACT, SRN_SHADE_NONE>(net, b, ctr, st, s);
+    case SRN_SHADE_FD: return launch_t<M, F, ACT, SRN_SHADE_FD>(net, b, ctr, st, s);
+    default: return launch_t<M, F, ACT, SRN_SHADE_HEAD>(net, b, ctr, st, s);
+  }
+}
+
+}  // namespace
+
+bool render_mma_supported(const NetDev& n, int shading) {
+  if (n.c != 32 || n.l < 2 || n.l > 8) return false;
+  if (shading == SRN_SHADE_ADJOINT) return false;
+  if (shading == SRN_SHADE_HEAD && n.D != 4) return false;
+  const bool shape_a = n.m == 14 && n.F == 16;
+  const bool shape_b = n.m == 12 && n.F == 8;
+  if (!shape_a && !shape_b) return false;
+  if ((size_t)n.nkey * n.R * n.R * n.R * n.F >= (size_t)1 << 31) return false;
+  return n.act == SRN_ACT_SINE || n.act == SRN_ACT_SNAKEALT;
+}
+
+cudaError_t launch_render_mma(const NetDev& n, const BatchDev& b, unsigned long long* ctr, unsigned int* status,
+                              cudaStream_t s) {
+  if (n.m == 14 && n.F == 16) {
+    return n.act == SRN_ACT_SNAKEALT ? dispatch_shading<14, 16, SRN_ACT_SNAKEALT>(n, b, ctr, status, s)
+                                     : dispatch_shading<14, 16, SRN_ACT_SINE>(n, b, ctr, status, s);
+  }
+  return n.act == SRN_ACT_SNAKEALT ? dispatch_shading<12, 8, SRN_ACT_SNAKEALT>(n, b, ctr, status, s)
+                                   : dispatch_shading<12, 8, SRN_ACT_SINE>(n, b, ctr, status, s);
+}
+
+}  // namespace srn

@@ -1,0 +1,156 @@
+"""GPU parity of the FP16 tensor-core render (tcgen05 / TMEM) against the FP64
+oracle evaluated with the same FP16 parameter values, through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2112_01579_gb300 import synth
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def srn():
+    import torch
+    from paper_2112_01579_gb300 import build
+    build.build()
+    from paper_2112_01579_gb300 import srn as S
+    assert torch.cuda.is_available()
+    return S
+
+
+def _net16(S, p):
+    q = synth.to_half_exact(p)
+    net = S.Network(q, precision=S.SRN_PREC_FP16)
+    return net, q
+
+
+def _render(S, net, cams, tf, W, Hh, step, et, shading=0, fd_h=0.0, times=None):
+    import torch
+    T = 1 if times is None else len(times)
+    out = torch.full((T, len(cams), Hh, W, 4), -1.0, device="cuda")
+    ns = torch.zeros(1, dtype=torch.int64, device="cuda")
+    S.srn_render(net.ctx, cams, tf, S.render_desc(W, Hh, step, et, shading, fd_h), out, times=times, samples=ns)
+    torch.cuda.synchronize()
+    st, msg = S.srn_sync_status(net.ctx)
+    assert st == 0, msg
+    return out.cpu().numpy(), int(ns.item())
+
+
+@pytest.mark.parametrize("et", [2.0, 0.99])
+def test_mma_cfg2_network_small_frames(srn, et):
+    S = srn
+    net, q = _net16(S, H.cfg2_params(seed=20))
+    tf = synth.tf_preset(8)
+    cams = synth.orbit_cameras(2)
+    got, ns = _render(S, net, cams, tf, 64, 48, 1 / 128, et)
+    ref, mg, ns_ref = oracle.render(oracle.OracleNet(q), cams, H.oracle_tf(tf), 64, 48, 1 / 128, et,
+                                    want_margin=True)
+    assert np.all(got >= 0)  # every pixel written
+    r = H.compare_images(got[0], ref[0], mg[0], H.TOL_FP16_IMG, et)
+    assert r["ok"], r
+    assert abs(ns - ns_ref) <= 0.002 * ns_ref + 2
+    assert ref[0, ..., 3].max() > 0.2
+
+
+def test_mma_cfg1_shape_sine(srn):
+    S = srn
+    net, q = _net16(S, H.cfg1_params(seed=21))
+    tf = synth.tf_preset(4)
+    cams = synth.orbit_cameras(3)
+    got, _ = _render(S, net, cams, tf, 40, 40, 1 / 128, 2.0)
+    ref, _, _ = oracle.render(oracle.OracleNet(q), cams, H.oracle_tf(tf), 40, 40, 1 / 128, 2.0)
+    assert np.abs(got[0] - ref[0]).max() <= H.TOL_FP16_IMG
+
+
+def test_mma_ragged_and_degenerate_images(srn):
+    S = srn
+    net, q = _net16(S, H.cfg2_params(seed=22))
+    tf = synth.tf_preset(8)
+    cams = [dict(eye=[0.9, 0.3, 0.9], target=[0.5, 0.6, 0.0], up=[0, 1, 0], fovy=math.radians(70))]
+    for W, Hh in [(37, 23), (1, 1), (9, 5), (130, 3)]:
+        got, _ = _render(S, net, cams, tf, W, Hh, 1 / 100, 2.0)
+        ref, _, _ = oracle.render(oracle.OracleNet(q), cams, H.oracle_tf(tf), W, Hh, 1 / 100, 2.0)
+        assert np.all(got >= 0)
+        assert np.abs(got - ref).max() <= H.TOL_FP16_IMG, (W, Hh)
+    miss = [dict(eye=[0, 0, 3], target=[0, 0, 6], up=[0, 1, 0], fovy=0.5)]
+    got, ns = _render(S, net, miss, tf, 16, 16, 1 / 100, 0.99)
+    assert ns == 0 and np.all(got == 0)
+
+
+def test_mma_full_size_sampled_pixels(srn):
+    """Config 2 launch configuration: 1024 x 1024, step 1/512, ET 0.99."""
+    S = srn
+    net, q = _net16(S, H.cfg2_params(seed=23))
+    tf = synth.tf_preset(8)
+    cams = synth.orbit_cameras(1)
+    got, ns = _render(S, net, cams, tf, 1024, 1024, 1 / 512, 0.99)
+    assert np.all(got >= 0)
+    pix = synth.sample_pixels(1, 1, 1024, 1024, 300, seed=24)
+    ref, mg, _ = oracle.render(oracle.OracleNet(q), cams, H.oracle_tf(tf), 1024, 1024, 1 / 512, 0.99, pixels=pix,
+                               want_margin=True)
+    r = H.compare_images(got.reshape(-1, 4)[pix], ref, mg, H.TOL_FP16_IMG, 0.99)
+    assert r["ok"], r
+
+
+def test_mma_matches_fp32_path_sample_count(srn):
+    """Same network (FP16-exact values) in both precisions: the number of
+    network samples of a frame without early termination agrees to the
+    handful of rays whose last segment rounds differently."""
+    import torch
+    S = srn
+    q = synth.to_half_exact(H.cfg2_params(seed=25))
+    n16 = S.Network(q, precision=S.SRN_PREC_FP16)
+    n32 = S.Network(q, precision=S.SRN_PREC_FP32)
+    tf = synth.tf_preset(8)
+    cams = synth.orbit_cameras(1)
+    a, na = _render(S, n16, cams, tf, 256, 256, 1 / 256, 2.0)
+    b, nb = _render(S, n32, cams, tf, 256, 256, 1 / 256, 2.0)
+    assert abs(na - nb) <= 0.001 * nb
+    assert np.abs(a - b).max() <= H.TOL_FP16_IMG
+
+
+@pytest.mark.parametrize("shading", [2, 3])
+def test_mma_shading(srn, shading):
+    S = srn
+    net, q = _net16(S, H.cfg2_params(seed=26, R=16, out_dim=4 if shading == 3 else 1))
+    tf = synth.tf_preset(8)
+    cams = synth.orbit_cameras(2)
+    got, _ = _render(S, net, cams, tf, 32, 24, 1 / 64, 2.0, shading=shading, fd_h=1 / 64)
+    ref, _, _ = oracle.render(oracle.OracleNet(q), cams, H.oracle_tf(tf), 32, 24, 1 / 64, 2.0, shading=shading,
+                              fd_h=1 / 64)
+    err = np.abs(got[0] - ref[0]).max()
+    # FD divides FP16-path density differences by 2h: its error scales by 1/h
+    tol = H.TOL_FP16_IMG if shading == 3 else 5 * H.TOL_FP16_IMG
+    assert err <= tol, err
+
+
+def test_mma_time_batch(srn):
+    """Config 5 layout at small size: 5 keyframes (0, 4, 8, 12, 15), 16 times x
+    4 views in one launch."""
+    S = srn
+    p = H.cfg2_params(seed=27, R=16, nkey=5, key_times=[0, 4, 8, 12, 15])
+    net, q = _net16(S, p)
+    tf = synth.tf_preset(8)
+    cams = synth.orbit_cameras(4)
+    times = list(range(16))
+    got, _ = _render(S, net, cams, tf, 20, 12, 1 / 64, 0.99, times=times)
+    ref, mg, _ = oracle.render(oracle.OracleNet(q), cams, H.oracle_tf(tf), 20, 12, 1 / 64, 0.99, times=times,
+                               want_margin=True)
+    r = H.compare_images(got, ref, mg, H.TOL_FP16_IMG, 0.99)
+    assert r["ok"], r
+
+
+def test_mma_rejects_unsupported(srn):
+    S = srn
+    p = synth.random_params(R=8, F=12, m=10, layers=3, width=32, seed=28)
+    q = synth.to_half_exact(p)
+    with pytest.raises(S.SrnError) as e:
+        net = S.Network(q, precision=S.SRN_PREC_FP16)
+        import torch
+        out = torch.zeros((1, 1, 8, 8, 4), device="cuda")
+        S.srn_render(net.ctx, synth.orbit_cameras(1), synth.tf_preset(4), S.render_desc(8, 8, 0.01), out)
+    assert e.value.status == S.SRN_ERR_UNSUPPORTED
