@@ -279,7 +279,9 @@ srn_status srn_backward(srn_ctx* ctx, const float* pts_dev, int n, float time, c
   if (!ctx) return fail(SRN_ERR_INVALID_ARG, "ctx is NULL");
   if (n < 0 || n > ctx->cfg.max_fit_points)
     return fail(SRN_ERR_INVALID_ARG, "n must be in [0, max_fit_points=%d]", ctx->cfg.max_fit_points);
+  if (ctx->cfg.max_fit_points < 1) return fail(SRN_ERR_INVALID_ARG, "context was created without fit scratch");
   if (n > 0 && (!pts_dev || !dout_dev)) return fail(SRN_ERR_INVALID_ARG, "points and dout are required");
+  if (!fit_supported(make_net(ctx))) return fail(SRN_ERR_UNSUPPORTED, "backward does not implement this shape");
   if (!dgrid_dev || !dweights_dev || !dbiases_dev) return fail(SRN_ERR_INVALID_ARG, "gradient outputs are required");
   srn_status st = use_device(ctx);
   if (st) return st;
@@ -299,6 +301,9 @@ srn_status srn_fit_step(srn_ctx* ctx, const float* volume_dev, const int dims[3]
   if (step < 0) return fail(SRN_ERR_INVALID_ARG, "step must be >= 0");
   if (!ctx->prm.adam_m || !ctx->prm.adam_v) return fail(SRN_ERR_INVALID_ARG, "Adam moments are required");
   if (!loss_dev) return fail(SRN_ERR_INVALID_ARG, "loss_dev is required");
+  if (!fit_supported(make_net(ctx))) return fail(SRN_ERR_UNSUPPORTED, "fit does not implement this shape");
+  if (ctx->cfg.out_dim == 4 && !(grad_scale == grad_scale && grad_weight >= 0.0f))
+    return fail(SRN_ERR_INVALID_ARG, "grad_weight must be >= 0");
   if (!(lr_grid >= 0.0f) || !(lr_net >= 0.0f)) return fail(SRN_ERR_INVALID_ARG, "learning rates must be >= 0");
   srn_status st = use_device(ctx);
   if (st) return st;

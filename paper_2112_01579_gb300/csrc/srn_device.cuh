@@ -129,4 +129,20 @@ __device__ __forceinline__ void load_tf(TFDev& dst, const TFDev& src) {
   }
 }
 
+// Trilinear interpolation of a dense float32 volume [nz][ny][nx].
+__device__ __forceinline__ float vol_sample(const VolDev& v, float3 p) {
+  int ix, iy, iz;
+  float fx, fy, fz;
+  cell_coord(p.x, v.nx, ix, fx);
+  cell_coord(p.y, v.ny, iy, fy);
+  cell_coord(p.z, v.nz, iz, fz);
+  const size_t sy = (size_t)v.nx, sz = (size_t)v.nx * v.ny;
+  const float* b = v.vol + iz * sz + iy * sy + ix;
+  float c000 = __ldg(b), c100 = __ldg(b + 1), c010 = __ldg(b + sy), c110 = __ldg(b + sy + 1);
+  float c001 = __ldg(b + sz), c101 = __ldg(b + sz + 1), c011 = __ldg(b + sz + sy), c111 = __ldg(b + sz + sy + 1);
+  float gx = 1.0f - fx, gy = 1.0f - fy, gz = 1.0f - fz;
+  return gx * gy * gz * c000 + fx * gy * gz * c100 + gx * fy * gz * c010 + fx * fy * gz * c110 +
+         gx * gy * fz * c001 + fx * gy * fz * c101 + gx * fy * fz * c011 + fx * fy * fz * c111;
+}
+
 }  // namespace srn

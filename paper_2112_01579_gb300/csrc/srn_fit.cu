@@ -1,16 +1,636 @@
-// World-space fit and parameter backward (temporary: not yet implemented).
+// World-space fit (Section 5 training setup: uniformly drawn positions, L1
+// loss against the trilinear density of the volume, Adam) and the parameter
+// backward of the network, FP32 throughout.
+//
+// Pipeline of one step (all on the caller's stream, no host sync):
+//   1. point kernel: Philox4x32-10 sample (counter = point, step), ground
+//      truth, forward with stashed pre-activations, loss, backward through
+//      the layers.  Weight gradients: each CTA stages delta_i and v_i of its
+//      128 points in shared memory and accumulates dW_i = sum_p delta v^T for
+//      the entries it owns (fixed order); one partial row per CTA.  Latent
+//      adjoints dz and the cell of every point go to scratch.
+//   2. stable LSD radix sort of (cell, point) pairs, 8-bit digits: per-block
+//      per-warp digit counts, one exclusive scan, stable scatter.
+//   3. cell offsets, then one warp per grid vertex gathers w_corner(p) * dz
+//      over the points of its (up to 8) cells in sorted order and reduces
+//      across lanes with a fixed butterfly: no floating-point atomics, the
+//      latent-grid gradient is bit-reproducible.
+//   4. fixed-order reduction of the CTA partials (weights, biases, loss).
+//   5. Adam over grid, weights and biases (skipped if anything is not
+//      finite), refreshing the FP16 copies.
+#include <algorithm>
+#include <utility>
+
 #include "srn_fit.h"
+#include "srn_net32.cuh"
 
 namespace srn {
-cudaError_t fit_scratch_alloc(FitScratch& s, const NetDev&, int max_points) {
+namespace {
+
+using namespace net32;
+
+constexpr int kFitThreads = 128;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 2048;  // keys per sort block: 8 warps x 8 rounds x 32
+
+// ---------------------------------------------------------------- RNG
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011): ten rounds of the
+// Philox S-box with multipliers 0xD2511F53 / 0xCD9E8D57 and Weyl key
+// increments 0x9E3779B9 / 0xBB67AE85.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned int lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const unsigned int lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Training point j of a step: counter (j, step, 0x5352, 0), key (seed
+// low, seed high); each coordinate is (word >> 8) * 2^-24.
+__device__ __forceinline__ float3 sample_point(unsigned long long seed, int step, int j) {
+  uint4 o = philox4x32_10(make_uint4((unsigned)j, (unsigned)step, 0x5352u, 0u),
+                          make_uint2((unsigned)(seed & 0xffffffffull), (unsigned)(seed >> 32)));
+  const float s = 1.0f / 16777216.0f;
+  return make_float3((float)(o.x >> 8) * s, (float)(o.y >> 8) * s, (float)(o.z >> 8) * s);
+}
+
+__device__ __forceinline__ float sgnf(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
+
+struct PointArgs {
+  int n;
+  int mode;  // 0: fit (sample, loss); 1: backward of given points / adjoints
+  const float* pts_in;
+  const float* dout_in;
+  unsigned long long seed;
+  int step;
+  float time;
+  VolDev vol;
+  float gw, gs;
+  float* pts;   // scratch out
+  float* dz;
+  unsigned int* key;
+  unsigned int* idx;
+  float* part;
+  int n_entries;
+  int dstride;  // stride of the staged input rows
+};
+
+// Adds the contribution of the CTA's points to the gradient entries of one
+// layer: W block (dout x din at woff) and bias block (dout at boff).
+__device__ __forceinline__ void accumulate_layer(float* sacc, const float* sdelta, int dstr_d, const float* svin,
+                                                 int dstr_v, int dout, int din, int woff, int boff) {
+  const int tid = threadIdx.x;
+  for (int e = tid; e < dout * din; e += kFitThreads) {
+    const int o = e / din, j = e - o * din;
+    float s = 0.f;
+#pragma unroll 8
+    for (int p = 0; p < kFitThreads; ++p) s = fmaf(sdelta[p * dstr_d + o], svin[p * dstr_v + j], s);
+    sacc[woff + e] += s;
+  }
+  for (int e = tid; e < dout; e += kFitThreads) {
+    float s = 0.f;
+#pragma unroll 8
+    for (int p = 0; p < kFitThreads; ++p) s += sdelta[p * dstr_d + e];
+    sacc[boff + e] += s;
+  }
+}
+
+template <int C>
+__global__ void __launch_bounds__(kFitThreads) fit_point_kernel(const NetDev net, const PointArgs a, const Layout L) {
+  extern __shared__ float4 smem4[];
+  float* sm = reinterpret_cast<float*>(smem4);
+  const int dstr_d = C + 1, dstr_v = a.dstride;
+  float* sdelta = sm + L.total;
+  float* svin = sdelta + kFitThreads * dstr_d;
+  float* sacc = svin + kFitThreads * dstr_v;
+  float* sred = sacc + ((a.n_entries + 3) & ~3);
+  load_net<C>(sm, L, net);
+  const int tid = threadIdx.x;
+  for (int e = tid; e < a.n_entries; e += kFitThreads) sacc[e] = 0.f;
+
+  // packed offsets of each layer's weights / biases in [W | b]
+  const int d0 = L.d0, l = L.l, D = L.D;
+  const int nW = C * d0 + (l - 2) * C * C + D * C;
+  const Latent lat = make_latent(net, a.time);
+  const float inv_n = 1.0f / (float)a.n;
+  float loss_acc = 0.f;
+  const int nchunks = (a.n + kFitThreads - 1) / kFitThreads;
+
+  for (int chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+    const int j = chunk * kFitThreads + tid;
+    const bool valid = j < a.n;
+    float3 p = make_float3(0.5f, 0.5f, 0.5f);
+    float out[4] = {0.f, 0.f, 0.f, 0.f}, dout[4] = {0.f, 0.f, 0.f, 0.f};
+    float hs[kMaxL][C];
+    if (valid) {
+      if (a.mode == 0) p = sample_point(a.seed, a.step, j);
+      else p = clamp_p(make_float3(a.pts_in[3 * j], a.pts_in[3 * j + 1], a.pts_in[3 * j + 2]));
+      forward<C, true>(sm, L, net.act, lat, p, out, hs);
+      if (a.mode == 0) {
+        const float r = out[0] - vol_sample(a.vol, p);
+        loss_acc += fabsf(r);
+        dout[0] = sgnf(r) * inv_n;
+        if (D == 4) {
+          const float hh[3] = {1.0f / (float)(a.vol.nx - 1), 1.0f / (float)(a.vol.ny - 1),
+                               1.0f / (float)(a.vol.nz - 1)};
+#pragma unroll
+          for (int ax = 0; ax < 3; ++ax) {
+            float3 pp = p, pm = p;
+            if (ax == 0) { pp.x = clamp01f(p.x + hh[0]); pm.x = clamp01f(p.x - hh[0]); }
+            if (ax == 1) { pp.y = clamp01f(p.y + hh[1]); pm.y = clamp01f(p.y - hh[1]); }
+            if (ax == 2) { pp.z = clamp01f(p.z + hh[2]); pm.z = clamp01f(p.z - hh[2]); }
+            const float g = (vol_sample(a.vol, pp) - vol_sample(a.vol, pm)) / (2.0f * hh[ax]);
+            const float ra = out[1 + ax] - a.gs * g;
+            loss_acc += a.gw * fabsf(ra);
+            dout[1 + ax] = a.gw * sgnf(ra) * inv_n;
+          }
+        }
+      } else {
+        for (int dd = 0; dd < D; ++dd) dout[dd] = a.dout_in[(size_t)j * D + dd];
+      }
+    }
+    // ---- last layer (C -> D): delta = dout, input = act(h_{l-2})
+    float act_in[C];
+#pragma unroll
+    for (int o = 0; o < C; ++o) act_in[o] = valid ? act_f(net.act, hs[l - 2][o]) : 0.f;
+#pragma unroll
+    for (int dd = 0; dd < 4; ++dd)
+      if (dd < D) sdelta[tid * dstr_d + dd] = dout[dd];
+#pragma unroll
+    for (int o = 0; o < C; ++o) svin[tid * dstr_v + o] = act_in[o];
+    __syncthreads();
+    accumulate_layer(sacc, sdelta, dstr_d, svin, dstr_v, D, C, nW - D * C, nW + (l - 1) * C);
+    __syncthreads();
+    float delta[C];
+#pragma unroll
+    for (int jj = 0; jj < C; ++jj) {
+      float g = 0.f;
+      for (int dd = 0; dd < D; ++dd) g = fmaf(sm[L.oWl + dd * C + jj], dout[dd], g);
+      delta[jj] = valid ? g * act_df(net.act, hs[l - 2][jj]) : 0.f;
+    }
+    // ---- hidden layers i = l-2 .. 1 (C -> C)
+    for (int i = l - 2; i >= 1; --i) {
+#pragma unroll
+      for (int o = 0; o < C; ++o) {
+        sdelta[tid * dstr_d + o] = delta[o];
+        svin[tid * dstr_v + o] = valid ? act_f(net.act, hs[i - 1][o]) : 0.f;
+      }
+      __syncthreads();
+      accumulate_layer(sacc, sdelta, dstr_d, svin, dstr_v, C, C, C * d0 + (i - 1) * C * C, nW + i * C);
+      __syncthreads();
+      const float* Wrm = sm + L.oHid + (i - 1) * L.hidStride + C * C + C;
+      float g[C];
+#pragma unroll
+      for (int jj = 0; jj < C; ++jj) g[jj] = 0.f;
+#pragma unroll
+      for (int o = 0; o < C; ++o) axpy<C>(g, Wrm + o * C, delta[o]);
+#pragma unroll
+      for (int jj = 0; jj < C; ++jj) delta[jj] = valid ? g[jj] * act_df(net.act, hs[i - 1][jj]) : 0.f;
+    }
+    // ---- layer 0 (d0 -> C): input [p, sin(Fp), cos(Fp), z]
+#pragma unroll
+    for (int o = 0; o < C; ++o) sdelta[tid * dstr_d + o] = delta[o];
+    {
+      float* v = svin + tid * dstr_v;
+      v[0] = p.x; v[1] = p.y; v[2] = p.z;
+      const float* Fm = sm + L.oF;
+      for (int k = 0; k < L.m; ++k) {
+        const float e = Fm[3 * k] * p.x + Fm[3 * k + 1] * p.y + Fm[3 * k + 2] * p.z;
+        float s, c;
+        sincosf(e, &s, &c);
+        v[3 + k] = s;
+        v[3 + L.m + k] = c;
+      }
+      const Cell cell = make_cell(lat, p);
+      for (int f = 0; f < L.F; f += 4) {
+        const float4 z = latent4(lat, cell, f);
+        v[3 + 2 * L.m + f] = z.x;
+        v[3 + 2 * L.m + f + 1] = z.y;
+        v[3 + 2 * L.m + f + 2] = z.z;
+        v[3 + 2 * L.m + f + 3] = z.w;
+      }
+      if (!valid)
+        for (int q = 0; q < d0; ++q) v[q] = 0.f;
+    }
+    __syncthreads();
+    accumulate_layer(sacc, sdelta, dstr_d, svin, dstr_v, C, d0, 0, nW);
+    __syncthreads();
+    if (valid) {
+      const float* W0T = sm + L.oW0T;
+      for (int f = 0; f < L.F; ++f) a.dz[(size_t)j * L.F + f] = dotrow<C>(W0T + (3 + 2 * L.m + f) * C, delta);
+      a.pts[3 * j] = p.x;
+      a.pts[3 * j + 1] = p.y;
+      a.pts[3 * j + 2] = p.z;
+      int ix, iy, iz;
+      float fx, fy, fz;
+      cell_coord(p.x, lat.R, ix, fx);
+      cell_coord(p.y, lat.R, iy, fy);
+      cell_coord(p.z, lat.R, iz, fz);
+      a.key[j] = (unsigned)((iz * (lat.R - 1) + iy) * (lat.R - 1) + ix);
+      a.idx[j] = (unsigned)j;
+    }
+  }
+  // ---- per-CTA partials: gradient entries, then the loss sum (fixed tree)
+  float* row = a.part + (size_t)blockIdx.x * (a.n_entries + 1);
+  for (int e = tid; e < a.n_entries; e += kFitThreads) row[e] = sacc[e];
+  sred[tid] = loss_acc;
+  __syncthreads();
+  for (int w = kFitThreads / 2; w > 0; w >>= 1) {
+    if (tid < w) sred[tid] += sred[tid + w];
+    __syncthreads();
+  }
+  if (tid == 0) row[a.n_entries] = sred[0];
+}
+
+// ---------------------------------------------------------------- radix sort
+__device__ __forceinline__ void warp_digit_counts(const unsigned int* __restrict__ keys, int n, int shift,
+                                                  unsigned int (*cnt)[256]) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int base = blockIdx.x * kSortItems + w * 256;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int i = base + r * 32 + lane;
+    const bool valid = i < n;
+    const unsigned int d = valid ? (keys[i] >> shift) & 255u : 0xFFFFFFFFu;
+    const unsigned int peers = __match_any_sync(0xffffffffu, d);
+    if (valid && lane == __ffs(peers) - 1) cnt[w][d] += __popc(peers);
+    __syncwarp();
+  }
+}
+
+__global__ void __launch_bounds__(kSortThreads) sort_hist_kernel(const unsigned int* __restrict__ keys, int n,
+                                                                 int shift, unsigned int* __restrict__ hist,
+                                                                 int nblocks) {
+  __shared__ unsigned int cnt[8][256];
+  for (int i = threadIdx.x; i < 8 * 256; i += kSortThreads) (&cnt[0][0])[i] = 0;
+  __syncthreads();
+  warp_digit_counts(keys, n, shift, cnt);
+  __syncthreads();
+  const int d = threadIdx.x;
+  unsigned int t = 0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) t += cnt[w][d];
+  hist[(size_t)d * nblocks + blockIdx.x] = t;
+}
+
+// Exclusive scan of m counts in place (one block, fixed segmentation).
+__global__ void __launch_bounds__(1024) scan_kernel(unsigned int* __restrict__ a, int m) {
+  __shared__ unsigned int part[1024];
+  const int tid = threadIdx.x;
+  const int seg = (m + 1023) / 1024;
+  const int b0 = min(tid * seg, m), b1 = min(b0 + seg, m);
+  unsigned int s = 0;
+  for (int i = b0; i < b1; ++i) s += a[i];
+  part[tid] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const unsigned int v = tid >= off ? part[tid - off] : 0u;
+    __syncthreads();
+    part[tid] += v;
+    __syncthreads();
+  }
+  unsigned int run = part[tid] - s;
+  for (int i = b0; i < b1; ++i) {
+    const unsigned int v = a[i];
+    a[i] = run;
+    run += v;
+  }
+}
+
+__global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(const unsigned int* __restrict__ kin,
+                                                                    const unsigned int* __restrict__ vin,
+                                                                    unsigned int* __restrict__ kout,
+                                                                    unsigned int* __restrict__ vout, int n, int shift,
+                                                                    const unsigned int* __restrict__ scanned,
+                                                                    int nblocks) {
+  __shared__ unsigned int cnt[8][256];
+  for (int i = threadIdx.x; i < 8 * 256; i += kSortThreads) (&cnt[0][0])[i] = 0;
+  __syncthreads();
+  warp_digit_counts(kin, n, shift, cnt);
+  __syncthreads();
+  {
+    const int d = threadIdx.x;
+    unsigned int base = scanned[(size_t)d * nblocks + blockIdx.x];
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      const unsigned int c = cnt[w][d];
+      cnt[w][d] = base;
+      base += c;
+    }
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int base = blockIdx.x * kSortItems + w * 256;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int i = base + r * 32 + lane;
+    const bool valid = i < n;
+    const unsigned int k = valid ? kin[i] : 0u;
+    const unsigned int d = valid ? (k >> shift) & 255u : 0xFFFFFFFFu;
+    const unsigned int peers = __match_any_sync(0xffffffffu, d);
+    const unsigned int rank = __popc(peers & ((1u << lane) - 1u));
+    if (valid) {
+      const unsigned int pos = cnt[w][d] + rank;
+      kout[pos] = k;
+      vout[pos] = vin[i];
+    }
+    __syncwarp();
+    if (valid && lane == __ffs(peers) - 1) cnt[w][d] += __popc(peers);
+    __syncwarp();
+  }
+}
+
+// cell_start[c] = first sorted position with key >= c, for c in [0, n_cells].
+__global__ void cell_start_kernel(const unsigned int* __restrict__ skeys, int n, unsigned int* __restrict__ start,
+                                  int n_cells) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s > n) return;
+  const int cur = s < n ? (int)skeys[s] : n_cells;
+  const int prev = s > 0 ? (int)skeys[s - 1] : -1;
+  for (int c = prev + 1; c <= cur; ++c) start[c] = (unsigned int)s;
+}
+
+// One warp per grid vertex: gather w_corner(p_j) * dz_j over the points of the
+// vertex's adjacent cells (fixed cell order, sorted point order, lane-strided)
+// and reduce across lanes with a fixed butterfly.
+template <int F>
+__global__ void grid_grad_kernel(const float* __restrict__ pts, const float* __restrict__ dz,
+                                 const unsigned int* __restrict__ sidx, const unsigned int* __restrict__ start, int R,
+                                 float w0, float w1, float* __restrict__ g0, float* __restrict__ g1,
+                                 unsigned int* __restrict__ flag) {
+  const long long v = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (v >= (long long)R * R * R) return;
+  const int vx = (int)(v % R), vy = (int)((v / R) % R), vz = (int)(v / ((long long)R * R));
+  float acc[F];
+#pragma unroll
+  for (int f = 0; f < F; ++f) acc[f] = 0.f;
+  for (int c = 0; c < 8; ++c) {
+    const int dx = c & 1, dy = (c >> 1) & 1, dzz = c >> 2;
+    const int cx = vx - dx, cy = vy - dy, cz = vz - dzz;
+    if (cx < 0 || cy < 0 || cz < 0 || cx > R - 2 || cy > R - 2 || cz > R - 2) continue;
+    const int cell = (cz * (R - 1) + cy) * (R - 1) + cx;
+    const int s0 = (int)start[cell], s1 = (int)start[cell + 1];
+    for (int s = s0 + lane; s < s1; s += 32) {
+      const int j = (int)sidx[s];
+      int ix, iy, iz;
+      float fx, fy, fz;
+      cell_coord(pts[3 * j], R, ix, fx);
+      cell_coord(pts[3 * j + 1], R, iy, fy);
+      cell_coord(pts[3 * j + 2], R, iz, fz);
+      const float w = (dx ? fx : 1.0f - fx) * (dy ? fy : 1.0f - fy) * (dzz ? fz : 1.0f - fz);
+      const float4* zz = reinterpret_cast<const float4*>(dz + (size_t)j * F);
+#pragma unroll
+      for (int f = 0; f < F; f += 4) {
+        const float4 q = zz[f / 4];
+        acc[f] = fmaf(w, q.x, acc[f]);
+        acc[f + 1] = fmaf(w, q.y, acc[f + 1]);
+        acc[f + 2] = fmaf(w, q.z, acc[f + 2]);
+        acc[f + 3] = fmaf(w, q.w, acc[f + 3]);
+      }
+    }
+  }
+#pragma unroll
+  for (int f = 0; f < F; ++f)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc[f] += __shfl_xor_sync(0xffffffffu, acc[f], off);
+  if (lane == 0) {
+    bool bad = false;
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+      g0[(size_t)v * F + f] = w0 * acc[f];
+      if (g1) g1[(size_t)v * F + f] = w1 * acc[f];
+      bad |= !isfinite(acc[f]);
+    }
+    if (bad) atomicOr(flag, 1u);
+  }
+}
+
+// Fixed-order sum of the CTA partials: weights, biases and the loss.
+__global__ void reduce_parts_kernel(const float* __restrict__ part, int n_cta, int nW, int nb,
+                                    float* __restrict__ outW, float* __restrict__ outb, float* __restrict__ loss,
+                                    float inv_n, unsigned int* __restrict__ flag) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ne = nW + nb;
+  if (e > ne) return;
+  float s = 0.f;
+  for (int c = 0; c < n_cta; ++c) s += part[(size_t)c * (ne + 1) + e];
+  if (e < nW) outW[e] = s;
+  else if (e < ne) outb[e - nW] = s;
+  else if (loss) {
+    s *= inv_n;
+    *loss = s;
+  }
+  if (!isfinite(s) && (e < ne || loss)) atomicOr(flag, 1u);
+}
+
+// Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias correction at step + 1) over
+// [grid | weights | biases]; refreshes the FP16 copies.  Skipped entirely
+// when the step produced a non-finite loss or gradient.
+__global__ void adam_kernel(float* __restrict__ grid, float* __restrict__ W, float* __restrict__ b,
+                            const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v, size_t ng,
+                            size_t nW, size_t nb, float lr_grid, float lr_net, int step,
+                            const unsigned int* __restrict__ flag, unsigned int* __restrict__ status,
+                            __half* __restrict__ grid_h, __half* __restrict__ W_h) {
+  if (*flag) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(status, (unsigned int)SRN_ERR_NONFINITE);
+    return;
+  }
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const float bc1 = 1.0f - powf(b1, (float)(step + 1)), bc2 = 1.0f - powf(b2, (float)(step + 1));
+  const size_t n = ng + nW + nb;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float upd = (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    if (i < ng) {
+      const float t = grid[i] - lr_grid * upd;
+      grid[i] = t;
+      if (grid_h) grid_h[i] = __float2half_rn(t);
+    } else if (i < ng + nW) {
+      const float t = W[i - ng] - lr_net * upd;
+      W[i - ng] = t;
+      if (W_h) W_h[i - ng] = __float2half_rn(t);
+    } else {
+      b[i - ng - nW] -= lr_net * upd;
+    }
+  }
+}
+
+int sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+// Steps 1-4 shared by the fit and the backward.  Writes the grid gradient
+// (all keyframes) to dgrid, weights / biases to dW / db, the loss (fit) to
+// loss.
+cudaError_t run_backward(FitScratch& s, const NetDev& net, PointArgs pa, float* dgrid, float* dW, float* db,
+                         float* loss, cudaStream_t st) {
+  const int n = pa.n;
+  const int nW = (int)(net_weight_count(net)), nb = (int)net_bias_count(net);
+  Layout L = make_layout(net, true);
+  const int dstride = (net_d0(net) > net.c ? net_d0(net) : net.c) + 1;
+  pa.dstride = dstride;
+  pa.n_entries = nW + nb;
+  pa.pts = s.pts;
+  pa.dz = s.dz;
+  pa.key = s.key;
+  pa.idx = s.idx;
+  pa.part = s.part;
+  const int n_cta = std::min(s.max_cta, (n + kFitThreads - 1) / kFitThreads);
+  size_t smem = sizeof(float) * ((size_t)L.total + kFitThreads * (net.c + 1) + (size_t)kFitThreads * dstride +
+                                 ((pa.n_entries + 3) & ~3) + kFitThreads);
+  cudaError_t e = cudaMemsetAsync(s.flag, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) return e;
+  if (n_cta > 0) {
+    auto k = fit_point_kernel<32>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<n_cta, kFitThreads, smem, st>>>(net, pa, L);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  // sort (cell, point) by cell
+  unsigned int *k_in = s.key, *v_in = s.idx, *k_out = s.key_alt, *v_out = s.idx_alt;
+  int bits = 1;
+  while (((size_t)1 << bits) < s.n_cells) ++bits;
+  const int nblocks = (n + kSortItems - 1) / kSortItems;
+  for (int shift = 0; shift < bits && n > 0; shift += 8) {
+    sort_hist_kernel<<<nblocks, kSortThreads, 0, st>>>(k_in, n, shift, s.hist, nblocks);
+    scan_kernel<<<1, 1024, 0, st>>>(s.hist, 256 * nblocks);
+    sort_scatter_kernel<<<nblocks, kSortThreads, 0, st>>>(k_in, v_in, k_out, v_out, n, shift, s.hist, nblocks);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    std::swap(k_in, k_out);
+    std::swap(v_in, v_out);
+  }
+  cell_start_kernel<<<(n + 1 + 255) / 256, 256, 0, st>>>(k_in, n, s.cell_start, (int)s.n_cells);
+  // grid gradient: zero all keyframes, then gather into the bracketing ones
+  const size_t gsz = (size_t)net.R * net.R * net.R * net.F;
+  e = cudaMemsetAsync(dgrid, 0, sizeof(float) * gsz * net.nkey, st);
+  if (e != cudaSuccess) return e;
+  int k0 = 0;
+  float f = 0.f;
+  {
+    // keyframe bracket of the step's time (same rule as the kernels' time_weights)
+    if (net.nkey > 1) {
+      const float t = pa.time;
+      if (t <= net.key_times[0]) { k0 = 0; f = 0.f; }
+      else if (t >= net.key_times[net.nkey - 1]) { k0 = net.nkey - 2; f = 1.f; }
+      else {
+        while (k0 < net.nkey - 2 && t >= net.key_times[k0 + 1]) ++k0;
+        f = (t - net.key_times[k0]) / (net.key_times[k0 + 1] - net.key_times[k0]);
+      }
+    }
+  }
+  const float w0 = net.nkey > 1 ? 1.0f - f : 1.0f, w1 = f;
+  float* g0 = dgrid + (size_t)k0 * gsz;
+  float* g1 = net.nkey > 1 ? g0 + gsz : nullptr;
+  const long long n_vert = (long long)net.R * net.R * net.R;
+  const unsigned int gblocks = (unsigned int)((n_vert * 32 + 255) / 256);
+  if (n > 0) {
+    if (net.F == 8)
+      grid_grad_kernel<8><<<gblocks, 256, 0, st>>>(s.pts, s.dz, v_in, s.cell_start, net.R, w0, w1, g0, g1, s.flag);
+    else if (net.F == 16)
+      grid_grad_kernel<16><<<gblocks, 256, 0, st>>>(s.pts, s.dz, v_in, s.cell_start, net.R, w0, w1, g0, g1, s.flag);
+    else if (net.F == 4)
+      grid_grad_kernel<4><<<gblocks, 256, 0, st>>>(s.pts, s.dz, v_in, s.cell_start, net.R, w0, w1, g0, g1, s.flag);
+    else
+      grid_grad_kernel<32><<<gblocks, 256, 0, st>>>(s.pts, s.dz, v_in, s.cell_start, net.R, w0, w1, g0, g1, s.flag);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  const int ne = nW + nb;
+  if (n_cta > 0) {
+    reduce_parts_kernel<<<(ne + 1 + 255) / 256, 256, 0, st>>>(s.part, n_cta, nW, nb, dW, db, loss,
+                                                              1.0f / (float)n, s.flag);
+  } else {
+    e = cudaMemsetAsync(dW, 0, sizeof(float) * nW, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(db, 0, sizeof(float) * nb, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t fit_scratch_alloc(FitScratch& s, const NetDev& net, int max_points) {
   memset(&s, 0, sizeof(s));
   s.max_points = max_points;
-  return cudaSuccess;
+  if (max_points <= 0) return cudaSuccess;
+  s.n_cells = (size_t)(net.R - 1) * (net.R - 1) * (net.R - 1);
+  s.n_entries = net_weight_count(net) + net_bias_count(net);
+  s.n_grid = net_grid_count(net);
+  s.max_cta = std::min(4 * sm_count(), (max_points + kFitThreads - 1) / kFitThreads);
+  const size_t n = (size_t)max_points;
+  const size_t nsb = (n + kSortItems - 1) / kSortItems;
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes < 16 ? 16 : bytes);
+  };
+  alloc((void**)&s.pts, sizeof(float) * 3 * n);
+  alloc((void**)&s.dz, sizeof(float) * net.F * n);
+  alloc((void**)&s.key, sizeof(unsigned int) * n);
+  alloc((void**)&s.key_alt, sizeof(unsigned int) * n);
+  alloc((void**)&s.idx, sizeof(unsigned int) * n);
+  alloc((void**)&s.idx_alt, sizeof(unsigned int) * n);
+  alloc((void**)&s.hist, sizeof(unsigned int) * 256 * nsb);
+  alloc((void**)&s.cell_start, sizeof(unsigned int) * (s.n_cells + 1));
+  alloc((void**)&s.part, sizeof(float) * (size_t)s.max_cta * (s.n_entries + 1));
+  alloc((void**)&s.grads, sizeof(float) * (s.n_grid + s.n_entries));
+  alloc((void**)&s.flag, sizeof(unsigned int) * 4);
+  return e;
 }
-void fit_scratch_free(FitScratch& s) { memset(&s, 0, sizeof(s)); }
-cudaError_t launch_backward(FitScratch&, const NetDev&, const float*, int, float, const float*, float*, float*, float*,
-                            cudaStream_t) {
-  return cudaErrorNotSupported;
+
+void fit_scratch_free(FitScratch& s) {
+  void* ps[] = {s.pts, s.dz, s.key, s.key_alt, s.idx, s.idx_alt, s.hist, s.cell_start, s.part, s.grads, s.flag};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  memset(&s, 0, sizeof(s));
 }
-cudaError_t launch_fit_step(FitScratch&, const NetDev&, const FitArgs&, cudaStream_t) { return cudaErrorNotSupported; }
+
+bool fit_supported(const NetDev& net) {
+  return net.c == 32 && (net.F == 4 || net.F == 8 || net.F == 16 || net.F == 32) && net.l <= kMaxL;
+}
+
+cudaError_t launch_backward(FitScratch& s, const NetDev& net, const float* pts, int n, float time, const float* dout,
+                            float* dgrid, float* dW, float* db, cudaStream_t st) {
+  if (!fit_supported(net)) return cudaErrorNotSupported;
+  PointArgs pa{};
+  pa.n = n;
+  pa.mode = 1;
+  pa.pts_in = pts;
+  pa.dout_in = dout;
+  pa.time = time;
+  return run_backward(s, net, pa, dgrid, dW, db, nullptr, st);
+}
+
+cudaError_t launch_fit_step(FitScratch& s, const NetDev& net, const FitArgs& a, cudaStream_t st) {
+  if (!fit_supported(net)) return cudaErrorNotSupported;
+  PointArgs pa{};
+  pa.n = a.n;
+  pa.mode = 0;
+  pa.seed = a.seed;
+  pa.step = a.step;
+  pa.time = a.time;
+  pa.vol = a.vol;
+  pa.gw = a.grad_weight;
+  pa.gs = a.grad_scale;
+  const size_t ng = s.n_grid, nW = net_weight_count(net), nb = net_bias_count(net);
+  cudaError_t e = run_backward(s, net, pa, s.grads, s.grads + ng, s.grads + ng + nW, a.loss, st);
+  if (e != cudaSuccess) return e;
+  const size_t n = ng + nW + nb;
+  unsigned int blocks = (unsigned int)std::min<size_t>((n + 255) / 256, (size_t)sm_count() * 8);
+  adam_kernel<<<blocks, 256, 0, st>>>(a.grid, a.weights, a.biases, s.grads, a.adam_m, a.adam_v, ng, nW, nb, a.lr_grid,
+                                      a.lr_net, a.step, s.flag, a.status, a.grid_h, a.weights_h);
+  return cudaGetLastError();
+}
+
 }  // namespace srn

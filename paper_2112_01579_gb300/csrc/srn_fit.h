@@ -5,25 +5,24 @@
 
 namespace srn {
 
-// Device scratch owned by a context, sized for max_fit_points points.
+// Device scratch owned by a context, sized for max_points points.
 struct FitScratch {
   int max_points;
-  int n_blocks;              // CTAs of the per-point kernel
-  float* pts;                // [n][3] sampled positions
-  float* target;             // [n] ground-truth density (and [n][3] gradient targets for D = 4)
-  float* dout;               // [n][D] output adjoints
-  float* dz;                 // [n][F] latent adjoints (times keyframe weight applied later)
-  unsigned int* key;         // [n] cell index of each point
-  unsigned int* key_alt;     // [n] radix-sort ping-pong
-  unsigned int* idx;         // [n] point index, sorted by cell
-  unsigned int* idx_alt;     // [n]
-  unsigned int* hist;        // radix histogram [256][n_sort_blocks]
+  int max_cta;             // CTAs of the per-point kernel (partials rows)
+  size_t n_cells;          // (R-1)^3 latent-grid cells
+  size_t n_entries;        // weights + biases
+  size_t n_grid;           // latent-grid entries over all keyframes
+  float* pts;              // [n][3] positions (clamped) of the current step
+  float* dz;               // [n][F] adjoint of the latent vector
+  unsigned int* key;       // [n] cell of each point, and radix ping-pong
+  unsigned int* key_alt;
+  unsigned int* idx;       // [n] point index, sorted by cell
+  unsigned int* idx_alt;
+  unsigned int* hist;      // radix histograms [256][sort blocks]
   unsigned int* cell_start;  // [n_cells + 1]
-  float* dW_part;            // [n_blocks][n_weights + n_biases] per-CTA partial sums
-  float* loss_part;          // [n_blocks] per-CTA loss partials
-  float* grads;              // [grid | W | b] full gradient of one step
-  float* cell_part;          // [n_cells][8][F] per-cell corner partials
-  size_t n_cells;
+  float* part;             // [max_cta][n_entries + 1] per-CTA weight-gradient / loss partials
+  float* grads;            // [n_grid + n_entries] gradient of one step (grid | weights | biases)
+  unsigned int* flag;      // non-finite flag of the current step
 };
 
 struct FitArgs {
@@ -44,6 +43,7 @@ struct FitArgs {
   float* adam_v;
 };
 
+bool fit_supported(const NetDev& net);
 cudaError_t fit_scratch_alloc(FitScratch& s, const NetDev& net, int max_points);
 void fit_scratch_free(FitScratch& s);
 cudaError_t launch_backward(FitScratch& s, const NetDev& net, const float* pts, int n, float time, const float* dout,
