@@ -226,6 +226,39 @@ srn_status srn_fit_step(srn_ctx* ctx, const float* volume_dev, const int dims[3]
                         int step, float time, float lr_grid, float lr_net, float grad_weight, float grad_scale,
                         float* loss_dev, void* stream);
 
+/*
+ * srn_backward for callers that cannot allocate device memory.  The paper
+ * has no counterpart; this exists for integrators, not for the method.
+ *
+ * Some callers must not call cudaMalloc: code that runs while a stream is
+ * being captured into a CUDA graph (allocation is not a capturable
+ * operation), hosts whose device memory is owned by another allocator (a
+ * framework's caching pool, a preallocated arena) or frame loops that may
+ * not take the implicit device synchronization cudaMalloc/cudaFree can
+ * cause.  srn_create allocates scratch, so such callers cannot use
+ * srn_backward; this entry point needs no context and allocates nothing.
+ *
+ * It computes exactly what srn_backward computes for the network described
+ * by *cfg / *params (same arguments, same outputs, overwritten), using a
+ * fixed device scratch area of SRN_STATIC_SCRATCH_BYTES that every GPU
+ * loading the library holds until the process exits.  Limits and rules:
+ * - n is limited by that area; the largest n depends on the network shape
+ *   (about 260k points for an 8^3 x 8 grid, about 150k for 32^3 x 16).  A
+ *   larger n returns SRN_ERR_INVALID_ARG and srn_last_error() states the
+ *   largest n that fits.  cfg->max_fit_points is ignored.
+ * - The first call on each device looks up the area's device address
+ *   (once per device, with that device current); make that first call
+ *   before any stream capture begins.
+ * - All calls share the one area, which keeps the previous call's contents
+ *   (everything the call relies on is rewritten first).  Calls whose work
+ *   overlaps on the GPU (different streams, or different host threads) race
+ *   on it: serialize them.
+ */
+#define SRN_STATIC_SCRATCH_BYTES (16u << 20)
+srn_status srn_backward_static(const srn_config* cfg, const srn_params* params, const float* pts_dev, int n,
+                               float time, const float* dout_dev, float* dgrid_dev, float* dweights_dev,
+                               float* dbiases_dev, void* stream);
+
 /* Synchronize `stream` and return (then clear) the device status word:
  * SRN_OK, SRN_ERR_NONFINITE or SRN_ERR_INTERNAL. */
 srn_status srn_sync_status(srn_ctx* ctx, void* stream);

@@ -6,6 +6,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <mutex>
 #include <new>
 
 #include "srn_fit.h"
@@ -355,3 +357,111 @@ srn_status srn_image_mse(const float* a_dev, const float* b_dev, long long n_pix
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// srn_backward_static: the backward without any allocation, for callers that
+// cannot call cudaMalloc (stream capture in progress, device memory owned by
+// another allocator, frame loops that must not synchronize).  Its scratch is
+// the file-scope device array below.  In host code the array's name is only
+// a host-side stand-in for the symbol, never a device address: the address is
+// looked up with cudaGetSymbolAddress once per device (with that device
+// current) and passed to the kernels.
+
+namespace {
+
+__device__ __align__(256) unsigned char g_static_scratch[SRN_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_addr[kMaxDevices] = {};
+
+srn_status static_scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(SRN_ERR_UNSUPPORTED, "device index %d is out of range", dev);
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return SRN_OK;
+}
+
+// Carves the fit scratch of n points out of the static area; returns the
+// bytes needed (which may exceed the area).
+size_t carve_static(FitScratch& s, const NetDev& net, int n, unsigned char* base, int sms) {
+  memset(&s, 0, sizeof(s));
+  s.max_points = n;
+  s.n_cells = (size_t)(net.R - 1) * (net.R - 1) * (net.R - 1);
+  s.n_entries = net_weight_count(net) + net_bias_count(net);
+  s.n_grid = net_grid_count(net);
+  s.max_cta = std::max(1, std::min(sms, (n + 127) / 128));
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    void* p = (void*)((uintptr_t)base + off);
+    off = (off + bytes + 255) & ~(size_t)255;
+    return p;
+  };
+  const size_t nn = (size_t)std::max(n, 1);
+  s.pts = (float*)take(sizeof(float) * 3 * nn);
+  s.dz = (float*)take(sizeof(float) * net.F * nn);
+  s.key = (unsigned int*)take(sizeof(unsigned int) * nn);
+  s.key_alt = (unsigned int*)take(sizeof(unsigned int) * nn);
+  s.idx = (unsigned int*)take(sizeof(unsigned int) * nn);
+  s.idx_alt = (unsigned int*)take(sizeof(unsigned int) * nn);
+  s.hist = (unsigned int*)take(sizeof(unsigned int) * 256 * ((nn + 2047) / 2048));
+  s.cell_start = (unsigned int*)take(sizeof(unsigned int) * (s.n_cells + 1));
+  s.part = (float*)take(sizeof(float) * (size_t)s.max_cta * (s.n_entries + 1));
+  s.flag = (unsigned int*)take(sizeof(unsigned int) * 4);
+  s.grads = nullptr;  // the backward writes straight into the caller's outputs
+  return off;
+}
+
+}  // namespace
+
+extern "C" srn_status srn_backward_static(const srn_config* cfg, const srn_params* params, const float* pts_dev,
+                                          int n, float time, const float* dout_dev, float* dgrid_dev,
+                                          float* dweights_dev, float* dbiases_dev, void* stream) {
+  srn_status st = check_config(cfg);
+  if (st) return st;
+  st = check_params(cfg, params);
+  if (st) return st;
+  if (n < 0) return fail(SRN_ERR_INVALID_ARG, "n must be >= 0");
+  if (n > 0 && (!pts_dev || !dout_dev)) return fail(SRN_ERR_INVALID_ARG, "points and dout are required");
+  if (!dgrid_dev || !dweights_dev || !dbiases_dev) return fail(SRN_ERR_INVALID_ARG, "gradient outputs are required");
+  srn_ctx view;  // a stack description of the network; nothing is allocated
+  memset(&view, 0, sizeof(view));
+  view.cfg = *cfg;
+  view.prm = *params;
+  const NetDev net = make_net(&view);
+  if (!fit_supported(net)) return fail(SRN_ERR_UNSUPPORTED, "backward does not implement this shape");
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "srn_backward_static");
+  FitScratch s;
+  const size_t need = carve_static(s, net, n, nullptr, sms);
+  if (need > (size_t)SRN_STATIC_SCRATCH_BYTES) {
+    // largest n that fits this network shape
+    int lo = 0, hi = n;
+    while (lo < hi) {
+      const int mid = lo + (hi - lo + 1) / 2;
+      FitScratch t;
+      if (carve_static(t, net, mid, nullptr, sms) <= (size_t)SRN_STATIC_SCRATCH_BYTES) lo = mid;
+      else hi = mid - 1;
+    }
+    return fail(SRN_ERR_INVALID_ARG, "n = %d needs %zu bytes of scratch; the static area holds %u bytes "
+                "(at most n = %d for this network)", n, need, (unsigned)SRN_STATIC_SCRATCH_BYTES, lo);
+  }
+  void* base = nullptr;
+  st = static_scratch_address(&base);
+  if (st) return st;
+  carve_static(s, net, n, (unsigned char*)base, sms);
+  e = launch_backward(s, net, pts_dev, n, time, dout_dev, dgrid_dev, dweights_dev, dbiases_dev,
+                      (cudaStream_t)stream);
+  return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_backward_static");
+}

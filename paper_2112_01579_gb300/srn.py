@@ -25,7 +25,7 @@ SRN_MAX_KEYFRAMES, SRN_MAX_TF_POINTS, SRN_MAX_VIEWS, SRN_MAX_TIMES = 32, 32, 64,
 
 EXPORTED = ["srn_version", "srn_last_error", "srn_create", "srn_destroy", "srn_set_params", "srn_sync_half",
             "srn_render", "srn_dvr_dense", "srn_eval", "srn_density_grad", "srn_backward", "srn_fit_step",
-            "srn_sync_status", "srn_image_mse"]
+            "srn_sync_status", "srn_image_mse", "srn_backward_static"]
 
 
 class SrnError(RuntimeError):
@@ -88,6 +88,8 @@ def lib():
         L.srn_fit_step.argtypes = [vp, vp, C.POINTER(C.c_int), i, C.c_uint64, i, f, f, f, f, f, vp, vp]
         L.srn_sync_status.argtypes = [vp, vp]
         L.srn_image_mse.argtypes = [vp, vp, C.c_longlong, vp, vp]
+        L.srn_backward_static.argtypes = [C.POINTER(srn_config), C.POINTER(srn_params), vp, i, f, vp, vp, vp, vp,
+                                          vp]
         for name in EXPORTED[2:]:
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -188,6 +190,14 @@ def srn_density_grad(ctx, pts, rho, grad=None, time=0.0, stream=None):
 def srn_backward(ctx, pts, dout, dgrid, dweights, dbiases, time=0.0, stream=None):
     _check(lib().srn_backward(ctx, _ptr(pts), pts.shape[0], float(time), _ptr(dout), _ptr(dgrid), _ptr(dweights),
                               _ptr(dbiases), _stream(stream)))
+
+
+def srn_backward_static(cfg, params, pts, dout, dgrid, dweights, dbiases, time=0.0, stream=None):
+    """srn_backward without a context and without any device allocation (a
+    fixed static scratch area inside the library); for callers that may not
+    allocate, e.g. while a stream is being captured into a CUDA graph."""
+    _check(lib().srn_backward_static(C.byref(cfg), C.byref(params), _ptr(pts), pts.shape[0], float(time),
+                                     _ptr(dout), _ptr(dgrid), _ptr(dweights), _ptr(dbiases), _stream(stream)))
 
 
 def srn_fit_step(ctx, volume, n_points, seed, step, loss, lr_grid=1e-2, lr_net=5e-3, time=0.0, grad_weight=0.0,
