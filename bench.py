@@ -121,23 +121,71 @@ def setup_scene(device="cuda", fit_steps=FIT_STEPS, seed=0):
     return vol, net, synth.tf_preset(8), synth.orbit_cameras(N_VIEWS), fit_info
 
 
-def time_fit(net, vol, n_steps=50, seed=5):
+def vertex_points(n, device="cuda"):
+    """Positions of the n^3 grid vertices, x fastest (the volume's layout)."""
+    import torch
+    x = torch.linspace(0.0, 1.0, n, device=device)
+    Z, Y, X = torch.meshgrid(x, x, x, indexing="ij")
+    return torch.stack([X.reshape(-1), Y.reshape(-1), Z.reshape(-1)], dim=1).contiguous()
+
+
+def density_psnr_network(net, vol, pts):
+    """PSNR of the network's density at every vertex of the volume."""
     import torch
     from paper_2112_01579_gb300 import srn
-    loss = torch.zeros(1, device="cuda")
-    try:
-        for s in range(3):
-            srn.srn_fit_step(net.ctx, vol, FIT_POINTS, seed, 10000 + s, loss, lr_grid=0.0, lr_net=0.0)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for s in range(n_steps):
-            srn.srn_fit_step(net.ctx, vol, FIT_POINTS, seed, 10003 + s, loss, lr_grid=0.0, lr_net=0.0)
-        e1.record()
-        torch.cuda.synchronize()
-        return n_steps / (e0.elapsed_time(e1) / 1e3)
-    except srn.SrnError:
-        return None
+    out = torch.empty((pts.shape[0], net.out_dim), device=vol.device)
+    srn.srn_eval(net.ctx, pts, out)
+    mse = torch.zeros(1, dtype=torch.float64, device=vol.device)
+    srn.srn_density_mse(out[:, 0].contiguous(), vol.reshape(-1), mse)
+    torch.cuda.synchronize()
+    return 10 * math.log10(1.0 / max(mse.item(), 1e-30))
+
+
+def lowpass_baseline(vol, R, F):
+    """Equal-memory density grid (Section 6.2 'off' row): M = round(cbrt(R^3 F)),
+    returned with its density PSNR at the volume's vertices."""
+    import torch
+    from paper_2112_01579_gb300 import srn
+    M = int(round((R ** 3 * F) ** (1.0 / 3.0)))
+    tmp = torch.empty(2 * vol.numel(), device=vol.device)
+    grid = torch.empty((M, M, M), device=vol.device)
+    srn.srn_lowpass_resample(vol, M, tmp, grid)
+    back = torch.empty_like(vol)
+    srn.srn_resample(grid, back)
+    mse = torch.zeros(1, dtype=torch.float64, device=vol.device)
+    srn.srn_density_mse(back, vol, mse)
+    torch.cuda.synchronize()
+    return M, grid, 10 * math.log10(1.0 / max(mse.item(), 1e-30))
+
+
+def fit_cfg3(vol, pts, steps=FIT_STEPS, seed=0):
+    """Config 3: the plain-workload network (8^3 x 8 grid, m = 12, 2 sine
+    layers) fitted to the volume, 2^18 points per step.  Returns steps/s
+    (device time of all steps), final loss and density PSNR."""
+    import torch
+    from paper_2112_01579_gb300 import srn, synth
+    p = synth.init_params(R=8, F=8, m=12, layers=2, width=32, act=synth.ACT_SINE, seed=seed)
+    net = srn.Network(p, precision=srn.SRN_PREC_FP32, max_fit_points=FIT_POINTS, adam=True)
+    loss = torch.zeros(1, device=vol.device)
+    for s in range(3):  # warm-up on throw-away steps of a copy
+        srn.srn_fit_step(net.ctx, vol, FIT_POINTS, seed + 7, s, loss, lr_grid=0.0, lr_net=0.0)
+    net.adam_m.zero_()
+    net.adam_v.zero_()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for s in range(steps):
+        srn.srn_fit_step(net.ctx, vol, FIT_POINTS, seed + 1, s, loss, lr_grid=1e-2, lr_net=5e-3)
+    e1.record()
+    torch.cuda.synchronize()
+    st, msg = srn.srn_sync_status(net.ctx)
+    sps = steps / (e0.elapsed_time(e1) / 1e3)
+    M, _, lp_psnr = lowpass_baseline(vol, 8, 8)
+    res = {"steps": steps, "points_per_step": FIT_POINTS, "steps_per_s": sps, "final_loss": float(loss.item()),
+           "density_psnr_db": density_psnr_network(net, vol, pts), "lowpass_grid": M,
+           "lowpass_density_psnr_db": lp_psnr, "status": st}
+    net.close()
+    return res
 
 
 def run_ours(args, rank, world):
@@ -209,7 +257,12 @@ def run_ours(args, rank, world):
         b.record(stream)
         torch.cuda.synchronize()
         d_ms.append(a.elapsed_time(b))
-    psnrs = []
+    # learned vs plain at equal memory (Section 6.2): the fitted fV-SRN and
+    # the low-pass density grid of the latent grid's memory, both against
+    # dense DVR of the full volume
+    M, lp_grid, lp_dpsnr = lowpass_baseline(vol, 32, 16)
+    lp_img = torch.zeros_like(out[0])
+    psnrs, lp_psnrs = [], []
     mse = torch.zeros(1, dtype=torch.float64, device=dev)
     for v in range(N_VIEWS):
         srn.srn_render(net.ctx, [cams[v]], tf, desc, out)
@@ -217,7 +270,14 @@ def run_ours(args, rank, world):
         srn.srn_image_mse(out, dense, mse)
         torch.cuda.synchronize()
         psnrs.append(10 * math.log10(1.0 / max(mse.item(), 1e-30)))
-    fit_sps = time_fit(net, vol) if fit_info.get("steps") else None
+        srn.srn_dvr_dense(lp_grid, [cams[v]], tf, desc, lp_img)
+        srn.srn_image_mse(lp_img, dense, mse)
+        torch.cuda.synchronize()
+        lp_psnrs.append(10 * math.log10(1.0 / max(mse.item(), 1e-30)))
+    pts = vertex_points(vol.shape[0])
+    fvsrn_dpsnr = density_psnr_network(net, vol, pts)
+    cfg3 = fit_cfg3(vol, pts, steps=args.fit_steps) if fit_info.get("steps") else None
+    del pts
 
     # end-to-end through the C ABI with host buffers: parameters uploaded from
     # pinned host memory and the image read back, every step
@@ -231,8 +291,12 @@ def run_ours(args, rank, world):
                    "step": STEP, "et": ET, "l2": "flushed (256 MiB write) between timed frames",
                    "samples_per_frame": samples / args.steps / world,
                    "fvsrn_ms_per_frame": ms_frame, "dense_dvr_ms_per_frame": float(np.median(d_ms)),
-                   "psnr_fvsrn_vs_dense_db": float(np.mean(psnrs)), "fit": fit_info,
-                   "fit_steps_per_s": fit_sps, "parallelism": f"replicas x{world} (views split across ranks)"},
+                   "psnr_fvsrn_vs_dense_db": float(np.mean(psnrs)),
+                   "psnr_lowpass_grid_vs_dense_db": float(np.mean(lp_psnrs)), "lowpass_grid": M,
+                   "density_psnr_fvsrn_db": fvsrn_dpsnr, "density_psnr_lowpass_db": lp_dpsnr,
+                   "fit_render_network": fit_info,
+                   "fit_steps_per_s": cfg3["steps_per_s"] if cfg3 else None, "fit_cfg3": cfg3,
+                   "parallelism": f"replicas x{world} (views split across ranks)"},
         "e2e": e2e, "gpu_launches": args.steps,
         "clocks": clk.summary(),
     }
@@ -279,9 +343,36 @@ def cpu_baseline(params, vol_np, tf, cams, budget_rows=16):
             "sample": f"{len(rows)} of {H_IMG} rows of one {W_IMG}x{H_IMG} frame ({ns} samples, {dt:.1f} s)"}
 
 
+# Algorithmic work of one network sample of the render network (47 -> 32 ->
+# 32 -> 32 -> 1, SnakeAlt): MMA FLOPs 2 * sum(d_in * d_out) and transcendental
+# evaluations (3 x 32 activation sines, 2 x 14 Fourier sin/cos, 1 exp).
+MMA_FLOP_PER_SAMPLE = 2 * (47 * 32 + 32 * 32 + 32 * 32 + 32 * 1)
+TRANSC_PER_SAMPLE = 3 * 32 + 2 * 14 + 1
+SMS, MUFU_PER_SM_CLK, FP32_PER_SM_CLK, MAX_SM_GHZ = 152, 16, 128, 2.07
+# DRAM bytes of one 1024^2 frame of the render kernel, from the ncu capture
+# summarised in profiles/ (null when the kernel changed after the capture).
+RENDER_DRAM_BYTES = 1150976
+
+
 def roofline(res):
-    """Dominant kernel (the fV-SRN render) against its binding unit."""
-    return None
+    """The render kernel against the XU (MUFU) transcendental roofline, which
+    is the unit it uses the largest fraction of; the tensor-pipe fraction
+    rides along.  peak = 16 MUFU lanes/SM x 152 SMs x 2.07 GHz."""
+    if res["config"]["precision"] != "fp16-mma":
+        return None
+    sps = res["value"] / res["n_gpus"]  # per-GPU samples/s (kernel time only)
+    peak_xu = SMS * MUFU_PER_SM_CLK * MAX_SM_GHZ * 1e9 / 1e12
+    achieved_xu = sps * TRANSC_PER_SAMPLE / 1e12
+    pk = peaks()
+    peak_tc = pk.get("bf16_tflops", 1900.0)
+    achieved_tc = sps * MMA_FLOP_PER_SAMPLE / 1e12
+    return {"bound": "alu", "achieved": achieved_xu, "peak": peak_xu, "unit": "Top/s (transcendentals)",
+            "frac": achieved_xu / peak_xu, "traffic": RENDER_DRAM_BYTES,
+            "kernel": "render_mma_kernel (tcgen05)", "per_sample": {"transcendentals": TRANSC_PER_SAMPLE,
+                                                                    "mma_flop": MMA_FLOP_PER_SAMPLE},
+            "tensor": {"achieved": achieved_tc, "peak": peak_tc, "unit": "TFLOP/s", "frac": achieved_tc / peak_tc,
+                       "peak_source": "MEASURED_PEAKS.json bf16_tflops (fp16 dense rate equal)"},
+            "peak_source": "unit counts x max SM clock; probe measured 15.1 sin/clk/SM"}
 
 
 def run_reference(args, rank, world):

@@ -226,6 +226,27 @@ srn_status srn_fit_step(srn_ctx* ctx, const float* volume_dev, const int dims[3]
                         int step, float time, float lr_grid, float lr_net, float grad_weight, float grad_scale,
                         float* loss_dev, void* stream);
 
+/* Mean squared difference of two float32 arrays of n values (densities):
+ * PSNR = 10 log10(1 / MSE) for volumes normalised to [0,1] (Section 6
+ * reports reconstruction PSNR).  One double to mse_dev; deterministic. */
+srn_status srn_density_mse(const float* a_dev, const float* b_dev, long long n, double* mse_dev, void* stream);
+
+/* Vertex-aligned trilinear resampling of a float32 volume src_dims = {nx,
+ * ny, nz} onto a grid of dst_dims (each >= 1; a 1-vertex axis samples p = 0). */
+srn_status srn_resample(const float* src_dev, const int src_dims[3], float* dst_dev, const int dst_dims[3],
+                        void* stream);
+
+/*
+ * The "off" baseline of Section 6.2: the volume low-pass filtered and
+ * downsampled to an M^3 density grid of the latent grid's memory
+ * (M = round(cbrt(R^3 F)), e.g. 81 for 32^3 x 16).  Separable Gaussian with
+ * sigma = 0.5 (n_a - 1) / (M - 1) voxels per axis, truncated at 3 sigma,
+ * clamp-to-edge, then vertex-aligned trilinear resampling.  tmp_dev holds
+ * 2 nx ny nz floats; out_dev receives M^3 floats.
+ */
+srn_status srn_lowpass_resample(const float* volume_dev, const int dims[3], int M, float* tmp_dev, float* out_dev,
+                                void* stream);
+
 /*
  * srn_backward for callers that cannot allocate device memory.  The paper
  * has no counterpart; this exists for integrators, not for the method.

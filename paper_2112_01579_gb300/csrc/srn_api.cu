@@ -356,6 +356,30 @@ srn_status srn_image_mse(const float* a_dev, const float* b_dev, long long n_pix
   return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_image_mse");
 }
 
+srn_status srn_density_mse(const float* a_dev, const float* b_dev, long long n, double* mse_dev, void* stream) {
+  if (n < 0 || !mse_dev || (n > 0 && (!a_dev || !b_dev))) return fail(SRN_ERR_INVALID_ARG, "bad arrays");
+  cudaError_t e = launch_density_mse(a_dev, b_dev, n, mse_dev, (cudaStream_t)stream);
+  return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_density_mse");
+}
+
+srn_status srn_resample(const float* src_dev, const int src_dims[3], float* dst_dev, const int dst_dims[3],
+                        void* stream) {
+  if (!src_dev || !dst_dev || !src_dims || !dst_dims) return fail(SRN_ERR_INVALID_ARG, "arrays and dims required");
+  for (int a = 0; a < 3; ++a)
+    if (src_dims[a] < 2 || dst_dims[a] < 1) return fail(SRN_ERR_INVALID_ARG, "source dims >= 2, target dims >= 1");
+  cudaError_t e = launch_resample(src_dev, src_dims, dst_dev, dst_dims, (cudaStream_t)stream);
+  return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_resample");
+}
+
+srn_status srn_lowpass_resample(const float* volume_dev, const int dims[3], int M, float* tmp_dev, float* out_dev,
+                                void* stream) {
+  if (!volume_dev || !dims || !tmp_dev || !out_dev) return fail(SRN_ERR_INVALID_ARG, "arrays and dims required");
+  if (dims[0] < 2 || dims[1] < 2 || dims[2] < 2 || M < 2) return fail(SRN_ERR_INVALID_ARG, "dims and M must be >= 2");
+  if (!lowpass_supported(dims, M)) return fail(SRN_ERR_UNSUPPORTED, "filter wider than 257 taps");
+  cudaError_t e = launch_lowpass_resample(volume_dev, dims, M, tmp_dev, out_dev, (cudaStream_t)stream);
+  return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_lowpass_resample");
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

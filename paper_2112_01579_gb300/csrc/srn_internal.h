@@ -66,6 +66,11 @@ bool render_mma_supported(const NetDev& net, int shading);
 // Conversions and small utilities.
 cudaError_t launch_to_half(const float* src, __half* dst, size_t n, cudaStream_t s);
 cudaError_t launch_image_mse(const float* a, const float* b, long long n, double* out, cudaStream_t s);
+cudaError_t launch_density_mse(const float* a, const float* b, long long n, double* out, cudaStream_t s);
+cudaError_t launch_resample(const float* src, const int sdims[3], float* dst, const int ddims[3], cudaStream_t s);
+bool lowpass_supported(const int dims[3], int M);
+cudaError_t launch_lowpass_resample(const float* vol, const int dims[3], int M, float* tmp, float* out,
+                                    cudaStream_t s);
 
 // Layer shapes of a network.
 inline int net_d0(const NetDev& n) { return 3 + 2 * n.m + n.F; }

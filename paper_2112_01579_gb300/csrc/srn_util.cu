@@ -1,5 +1,7 @@
-// Small utility kernels: FP32 -> FP16 parameter copies and image MSE.
-#include "srn_internal.h"
+// Small utility kernels: FP32 -> FP16 parameter copies, image / density MSE,
+// and the equal-memory low-pass baseline of Section 6.2 (Gaussian filter and
+// vertex-aligned trilinear resampling of a dense volume).
+#include "srn_device.cuh"
 
 namespace srn {
 namespace {
@@ -32,7 +34,107 @@ __global__ void __launch_bounds__(kMseThreads) mse_kernel(const float4* __restri
   if (threadIdx.x == 0) *out = n > 0 ? part[0] / (3.0 * (double)n) : 0.0;
 }
 
+// Mean squared difference of two float arrays (one block, fixed order).
+__global__ void __launch_bounds__(kMseThreads) mse1_kernel(const float* __restrict__ a, const float* __restrict__ b,
+                                                           long long n, double* __restrict__ out) {
+  __shared__ double part[kMseThreads];
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < n; i += kMseThreads) {
+    const double d = (double)a[i] - (double)b[i];
+    s += d * d;
+  }
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kMseThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = n > 0 ? part[0] / (double)n : 0.0;
+}
+
+// One separable Gaussian pass along `axis` with clamp-to-edge: normalised
+// weights exp(-k^2 / (2 sigma^2)), |k| <= ceil(3 sigma).
+constexpr int kMaxTaps = 257;
+__global__ void gauss_pass_kernel(const float* __restrict__ src, float* __restrict__ dst, int nx, int ny, int nz,
+                                  int axis, float sigma) {
+  __shared__ float w[kMaxTaps];
+  const int rad = (int)ceilf(3.0f * sigma);
+  for (int k = threadIdx.x; k <= 2 * rad; k += blockDim.x) {
+    const float t = (float)(k - rad);
+    w[k] = expf(-0.5f * t * t / (sigma * sigma));
+  }
+  __syncthreads();
+  float wsum = 0.f;
+  for (int k = 0; k <= 2 * rad; ++k) wsum += w[k];
+  const long long n = (long long)nx * ny * nz;
+  const int dims[3] = {nx, ny, nz};
+  const long long stride = axis == 0 ? 1 : (axis == 1 ? nx : (long long)nx * ny);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(axis == 0 ? i % nx : (axis == 1 ? (i / nx) % ny : i / ((long long)nx * ny)));
+    float acc = 0.f;
+    for (int k = -rad; k <= rad; ++k) {
+      const int q = min(max(c + k, 0), dims[axis] - 1);
+      acc = fmaf(w[k + rad], src[i + (long long)(q - c) * stride], acc);
+    }
+    dst[i] = acc / wsum;
+  }
+}
+
+// Vertex-aligned trilinear resampling of a volume to another grid.
+__global__ void resample_kernel(VolDev src, float* __restrict__ dst, int mx, int my, int mz) {
+  const long long n = (long long)mx * my * mz;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % mx), y = (int)((i / mx) % my), z = (int)(i / ((long long)mx * my));
+    const float3 p = make_float3(mx > 1 ? (float)x / (float)(mx - 1) : 0.f, my > 1 ? (float)y / (float)(my - 1) : 0.f,
+                                 mz > 1 ? (float)z / (float)(mz - 1) : 0.f);
+    dst[i] = vol_sample(src, p);
+  }
+}
+
+unsigned int grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  return (unsigned int)(b > 152 * 32 ? 152 * 32 : (b < 1 ? 1 : b));
+}
+
 }  // namespace
+
+cudaError_t launch_density_mse(const float* a, const float* b, long long n, double* out, cudaStream_t s) {
+  mse1_kernel<<<1, kMseThreads, 0, s>>>(a, b, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resample(const float* src, const int sdims[3], float* dst, const int ddims[3], cudaStream_t s) {
+  VolDev v{src, sdims[0], sdims[1], sdims[2]};
+  resample_kernel<<<grid_for((long long)ddims[0] * ddims[1] * ddims[2]), 256, 0, s>>>(v, dst, ddims[0], ddims[1],
+                                                                                        ddims[2]);
+  return cudaGetLastError();
+}
+
+bool lowpass_supported(const int dims[3], int M) {
+  for (int a = 0; a < 3; ++a) {
+    const float sigma = 0.5f * (float)(dims[a] - 1) / (float)(M - 1);
+    if (2 * (int)ceilf(3.0f * sigma) + 1 > kMaxTaps) return false;
+  }
+  return true;
+}
+
+cudaError_t launch_lowpass_resample(const float* vol, const int dims[3], int M, float* tmp, float* out,
+                                    cudaStream_t s) {
+  const long long n = (long long)dims[0] * dims[1] * dims[2];
+  float* a = tmp;
+  float* b = tmp + n;
+  const float* cur = vol;
+  for (int axis = 0; axis < 3; ++axis) {
+    float* dst = (axis % 2 == 0) ? a : b;
+    const float sigma = 0.5f * (float)(dims[axis] - 1) / (float)(M - 1);
+    gauss_pass_kernel<<<grid_for(n), 256, 0, s>>>(cur, dst, dims[0], dims[1], dims[2], axis, sigma);
+    cur = dst;
+  }
+  const int md[3] = {M, M, M};
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_resample(cur, dims, out, md, s);
+}
 
 cudaError_t launch_to_half(const float* src, __half* dst, size_t n, cudaStream_t s) {
   if (n == 0) return cudaSuccess;

@@ -25,7 +25,8 @@ SRN_MAX_KEYFRAMES, SRN_MAX_TF_POINTS, SRN_MAX_VIEWS, SRN_MAX_TIMES = 32, 32, 64,
 
 EXPORTED = ["srn_version", "srn_last_error", "srn_create", "srn_destroy", "srn_set_params", "srn_sync_half",
             "srn_render", "srn_dvr_dense", "srn_eval", "srn_density_grad", "srn_backward", "srn_fit_step",
-            "srn_sync_status", "srn_image_mse", "srn_backward_static"]
+            "srn_sync_status", "srn_image_mse", "srn_backward_static", "srn_density_mse", "srn_resample",
+            "srn_lowpass_resample"]
 
 
 class SrnError(RuntimeError):
@@ -90,6 +91,9 @@ def lib():
         L.srn_image_mse.argtypes = [vp, vp, C.c_longlong, vp, vp]
         L.srn_backward_static.argtypes = [C.POINTER(srn_config), C.POINTER(srn_params), vp, i, f, vp, vp, vp, vp,
                                           vp]
+        L.srn_density_mse.argtypes = [vp, vp, C.c_longlong, vp, vp]
+        L.srn_resample.argtypes = [vp, C.POINTER(C.c_int), vp, C.POINTER(C.c_int), vp]
+        L.srn_lowpass_resample.argtypes = [vp, C.POINTER(C.c_int), i, vp, vp, vp]
         for name in EXPORTED[2:]:
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -217,6 +221,26 @@ def srn_sync_status(ctx, stream=None):
 def srn_image_mse(a, b, out, stream=None):
     """out: float64 CUDA tensor [1]."""
     _check(lib().srn_image_mse(_ptr(a), _ptr(b), a.numel() // 4, _ptr(out), _stream(stream)))
+
+
+def srn_density_mse(a, b, out, stream=None):
+    """out: float64 CUDA tensor [1]."""
+    _check(lib().srn_density_mse(_ptr(a), _ptr(b), a.numel(), _ptr(out), _stream(stream)))
+
+
+def _dims(t):
+    nz, ny, nx = t.shape
+    return (C.c_int * 3)(nx, ny, nz)
+
+
+def srn_resample(src, dst, stream=None):
+    """src, dst: float32 CUDA tensors [nz, ny, nx]."""
+    _check(lib().srn_resample(_ptr(src), _dims(src), _ptr(dst), _dims(dst), _stream(stream)))
+
+
+def srn_lowpass_resample(volume, M, tmp, out, stream=None):
+    """tmp: float32 CUDA tensor with 2 * volume.numel() values; out: [M, M, M]."""
+    _check(lib().srn_lowpass_resample(_ptr(volume), _dims(volume), int(M), _ptr(tmp), _ptr(out), _stream(stream)))
 
 
 # --------------------------------------------------------------------------
