@@ -16,9 +16,12 @@ a bounded sample of the same workload, on the host cores.
 from __future__ import annotations
 
 import argparse
+import collections
+import csv
 import json
 import math
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -400,6 +403,42 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": "network samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ---------------------------------------------------------------- ncu launch list
+
+
+def short(name):
+    name = re.sub(r"\(.*", "", name)
+    name = re.sub(r"^void ", "", name)
+    name = re.sub(r"<.*", "", name) if "srn::" not in name else name
+    for k in ["render_mma_kernel", "render_fp32_kernel", "dvr_dense_kernel", "eval_fp32_kernel", "fit_point_kernel",
+              "sort_hist_kernel", "sort_scatter_kernel", "scan_kernel", "cell_start_kernel", "grid_grad_kernel",
+              "reduce_parts_kernel", "adam_kernel", "to_half_kernel", "mse_kernel", "mse1_kernel",
+              "gauss_pass_kernel", "resample_kernel"]:
+        if k in name:
+            return "srn::" + k
+    return name[:60]
+
+
+def summarize_launches(path):
+    """Per kernel: launches, total device time, share (ncu launch-list CSV)."""
+    rows = [r for r in csv.DictReader(l for l in open(path) if not l.startswith("=="))
+            if r["Metric Name"] == "gpu__time_duration.sum"]
+    agg = collections.defaultdict(lambda: [0, 0.0])
+    for r in rows:
+        v = float(r["Metric Value"].replace(",", ""))
+        unit = r["Metric Unit"]
+        ns = v * {"nsecond": 1, "usecond": 1e3, "msecond": 1e6, "second": 1e9}.get(unit, 1)
+        a = agg[short(r["Kernel Name"])]
+        a[0] += 1
+        a[1] += ns
+    tot = sum(v[1] for v in agg.values())
+    print(f"{'kernel':44s} {'launches':>8s} {'total ms':>10s} {'share':>7s}")
+    for k, (n, t) in sorted(agg.items(), key=lambda kv: -kv[1][1]):
+        print(f"{k:44s} {n:8d} {t / 1e6:10.3f} {100 * t / tot:6.2f}%")
+    print(f"{'all':44s} {sum(v[0] for v in agg.values()):8d} {tot / 1e6:10.3f}")
+
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -408,7 +447,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fit-steps", type=int, default=FIT_STEPS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--summarize-launches", metavar="CSV",
+                    help="print per-kernel launches / time / share of an ncu gpu__time_duration.sum CSV and exit")
     args = ap.parse_args()
+    if args.summarize_launches:
+        summarize_launches(args.summarize_launches)
+        return
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", 1))
     rank = int(os.environ.get("RANK", 0))
