@@ -191,7 +191,9 @@ srn_status srn_dvr_dense(const float* volume_dev, const int dims[3], const srn_c
                          unsigned long long* samples_dev, void* stream);
 
 /* Network output at n points (pts_dev float32 [n][3] in [0,1]^3) at one time:
- * out_dev float32 [n][D].  FP32 arithmetic. */
+ * out_dev float32 [n][D] (Section 3 network, Section 6 random-access decode).
+ * Precision follows the context: FP32 CUDA cores, or the FP16 tensor-core
+ * layers of the render (FP16 grid and weights, FP32 accumulate). */
 srn_status srn_eval(srn_ctx* ctx, const float* pts_dev, int n, float time, float* out_dev, void* stream);
 
 /* Density and its adjoint input gradient (Section 5 "Adjoint"): rho_dev [n],

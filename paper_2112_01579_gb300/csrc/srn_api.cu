@@ -262,7 +262,14 @@ srn_status srn_eval(srn_ctx* ctx, const float* pts_dev, int n, float time, float
   if (n < 0 || (n > 0 && (!pts_dev || !out_dev))) return fail(SRN_ERR_INVALID_ARG, "bad points / output");
   srn_status st = use_device(ctx);
   if (st) return st;
-  cudaError_t e = launch_eval_fp32(make_net(ctx), pts_dev, n, time, out_dev, nullptr, 0, (cudaStream_t)stream);
+  const NetDev net = make_net(ctx);
+  cudaError_t e;
+  if (ctx->cfg.precision == SRN_PREC_FP16) {
+    if (!eval_mma_supported(net)) return fail(SRN_ERR_UNSUPPORTED, "FP16 tensor-core eval does not implement this shape");
+    e = launch_eval_mma(net, pts_dev, n, time, out_dev, ctx->ray_counter, ctx->status, (cudaStream_t)stream);
+  } else {
+    e = launch_eval_fp32(net, pts_dev, n, time, out_dev, nullptr, 0, (cudaStream_t)stream);
+  }
   return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_eval");
 }
 

@@ -62,6 +62,9 @@ bool render_fp32_supported(int width);
 cudaError_t launch_render_mma(const NetDev& net, const BatchDev& b, unsigned long long* ray_counter,
                               unsigned int* status, cudaStream_t s);
 bool render_mma_supported(const NetDev& net, int shading);
+bool eval_mma_supported(const NetDev& net);
+cudaError_t launch_eval_mma(const NetDev& net, const float* pts, long long n, float time, float* out,
+                            unsigned long long* ray_counter, unsigned int* status, cudaStream_t s);
 
 // Conversions and small utilities.
 cudaError_t launch_to_half(const float* src, __half* dst, size_t n, cudaStream_t s);

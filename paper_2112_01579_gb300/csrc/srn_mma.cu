@@ -9,29 +9,52 @@
 //   latent-grid trilinear fetch, Fourier features, transfer function,
 //   compositing, early termination) stays one thread per ray as in the paper,
 //   while the layers run as M=128 x N=32 tensor-core MMAs.
-// * Every sample: the thread writes its FP16 layer-0 input row [p, sin(Fp),
-//   cos(Fp), z, 1] into a 128B-swizzled shared-memory tile; one elected
-//   thread issues tcgen05.mma (kind::f16, FP32 accumulate in TMEM); the
-//   thread reads its row back with tcgen05.ld, applies the activation in FP32
-//   and writes the FP16 result as the next layer's A row.  Biases ride in the
-//   MMA through a constant-1 input column.  The last layer (32 -> D) runs on
-//   the CUDA cores in FP32.
+// * Every sample: the thread writes its FP16 layer-0 input row into a
+//   128B-swizzled shared-memory tile; one elected thread issues tcgen05.mma
+//   (kind::f16, FP32 accumulate in TMEM); the thread reads its row back with
+//   tcgen05.ld, applies the activation in FP32 and writes it into the same
+//   tile as the next layer's A row as an FP16 hi + lo pair (a = hi + lo to
+//   ~2^-22 relative; the B tile holds [W | W]), so the hidden activations
+//   keep FP32 accuracy through the FP16 tensor cores.  Inside the tile the input columns are
+//   [sin_0, cos_0, ..., sin_{m-1}, cos_{m-1}, p, z, 1, 1]; the B tile of
+//   layer 0 is permuted to match, so the arithmetic is that of [p, sin, cos,
+//   z].  Biases ride in the MMA as an FP16 hi + lo pair against two
+//   constant-1 columns (layer 0: columns of its own row; hidden layers: one
+//   extra K=16 MMA against a constant tile), which keeps them FP32-exact.  The last layer
+//   (32 -> D) runs on the CUDA cores in FP32.
+// * SnakeAlt(x) = 0.5 x + sin^2 x = (x - cos 2x + 1) / 2 (Eq. 3).  Every MMA
+//   layer is staged to produce u = 2x (weights and bias doubled, which is
+//   exact in FP16), the epilogue hands a = u / 2 - cos u = 2 SnakeAlt(x) - 1
+//   to the next layer, and the factor 1/2 and the shift 1/2 are folded into
+//   that layer's weights and bias: the doubled next layer then simply uses W
+//   and 2b + sum_j W_j.
 // * Rays are claimed dynamically (warp-aggregated atomic on a work counter);
 //   a thread whose ray terminates (box exit or opacity >= threshold) writes
 //   its pixel and takes the next ray, so tiles stay full.
 // * Every mbarrier wait is bounded; on timeout the warpgroup stops, records
 //   SRN_ERR_TIMEOUT in the status word and the CTA frees its TMEM.
+#include <string.h>
+
 #include "srn_device.cuh"
 
 namespace srn {
 namespace {
 
-constexpr int kWG = 4;                 // warpgroups per CTA
-constexpr int kThreads = 128 * kWG;    // 512 threads, one CTA per SM
+constexpr int kWG = 6;                 // warpgroups per CTA
+constexpr int kThreads = 128 * kWG;    // 768 threads, one CTA per SM
 constexpr int kTile = 128 * 128;       // one A tile: 128 rows x 128 B (64 fp16)
 constexpr int kBTile = 32 * 128;       // one B tile: 32 rows x 128 B
-constexpr int kTmemCols = 32 * kWG;    // one 32-column FP32 accumulator per warpgroup
+constexpr int kTmemCols = 256;         // >= 32 FP32 accumulator columns per warpgroup, power of two
 constexpr long long kWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
+constexpr int kPoints = 4;             // kernel mode: network output at given points (no ray march)
+
+// Point-evaluation arguments (mode kPoints).
+struct PointsDev {
+  const float* pts;  // [n][3]
+  float* out;        // [n][D]
+  long long n;
+  float time;
+};
 
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -151,33 +174,51 @@ __device__ __forceinline__ uint32_t pack_h2(float a, float b) {
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
+// Activation value handed to the next layer from the accumulator value: sin(x)
+// for the sine network; for SnakeAlt the accumulator holds u = 2x and the
+// value is u / 2 - cos u = 2 SnakeAlt(x) - 1.
 template <int ACT>
-__device__ __forceinline__ float act_fast(float x) {
-  float s = __sinf(x);
-  return ACT == SRN_ACT_SNAKEALT ? fmaf(s, s, 0.5f * x) : s;
+__device__ __forceinline__ float act_fold(float acc) {
+  return ACT == SRN_ACT_SNAKEALT ? fmaf(0.5f, acc, -__cosf(acc)) : __sinf(acc);
 }
 
 // ---------------------------------------------------------------- layout
 struct SmemPlan {
-  int oA0, oAh, oB, oWl, oTF, oFm, oMbar, oMisc, total;
+  int oA, oOne, oB, oWl, oTF, oTFinv, oFm, oMbar, oMisc, total;
 };
 
 SmemPlan make_plan(const NetDev& n) {
   SmemPlan s;
   int o = 0;
-  s.oA0 = o; o += kWG * kTile;
-  s.oAh = o; o += kWG * kTile;
-  s.oB = o; o += (n.l - 1) * kBTile;
+  s.oA = o; o += kWG * kTile;
+  s.oOne = o; o += kTile;                       // constant tile: columns 0, 1 = 1
+  s.oB = o; o += (1 + 2 * (n.l - 2)) * kBTile;  // layer 0; per hidden layer: [W | W] and bias
   s.oWl = o; o += (n.D * 32 + 4) * 4;
   o = (o + 15) & ~15;
   s.oTF = o; o += (int)sizeof(TFDev);
   o = (o + 15) & ~15;
+  s.oTFinv = o; o += SRN_MAX_TF_POINTS * 4;
   s.oFm = o; o += ((3 * n.m + 3) & ~3) * 4 + 16;
   o = (o + 7) & ~7;
   s.oMbar = o; o += 8 * kWG;
   s.oMisc = o; o += 16 * 4;
   s.total = o + 1024;  // alignment slack
   return s;
+}
+
+// Transfer function with precomputed reciprocal segment widths (same
+// segments and lerp as the shared tf_eval).
+__device__ __forceinline__ float4 tf_eval_inv(const TFDev& tf, const float* inv, float rho) {
+  const float x = clamp01f(rho);
+  const int n = tf.n;
+  if (x <= tf.pos[0]) return tf.rgba[0];
+  if (x >= tf.pos[n - 1]) return tf.rgba[n - 1];
+  int i = 0;
+  while (i < n - 2 && x >= tf.pos[i + 1]) ++i;
+  const float f = (x - tf.pos[i]) * inv[i];
+  const float4 a = tf.rgba[i], b = tf.rgba[i + 1];
+  return make_float4(fmaf(f, b.x - a.x, a.x), fmaf(f, b.y - a.y, a.y), fmaf(f, b.z - a.z, a.z),
+                     fmaf(f, b.w - a.w, a.w));
 }
 
 struct RayLat {
@@ -224,23 +265,34 @@ __device__ __forceinline__ void latent_h(const __half* __restrict__ G, int R, co
   }
 }
 
-// Layer-0 input row [p, sin(Fp), cos(Fp), z, 1, 0...] (Eq. 1-2 features),
-// written in FP16 into the thread's row of the swizzled A tile.
+// Layer-0 input row (Eq. 1-2 features, Section 4.2 latent vector) in the
+// tile's column order [sin_0, cos_0, ..., sin_{m-1}, cos_{m-1}, p, z, 1, 1,
+// 0...] over the K0 columns layer 0 reads.  Values are packed to FP16 pairs
+// and stored 16 bytes at a time as they are produced.
 template <int M, int F, int K0>
 __device__ __forceinline__ void write_input_row(uint8_t* tile, int row, float3 p, bool nerf, const float* fm,
                                                 const __half* G, int R, const RayLat& rl) {
   constexpr int D0 = 3 + 2 * M + F;
-  float v[K0];
-  v[0] = p.x;
-  v[1] = p.y;
-  v[2] = p.z;
+  static_assert(M >= 3, "the NeRF recurrence needs the three base rows");
+  float z[F];
+  latent_h<F>(G, R, rl, p, z);
+  uint32_t w[4];
+  int nw = 0, chunk = 0;
+  auto emit = [&](float a, float b) {
+    w[nw++] = pack_h2(a, b);
+    if (nw == 4) {
+      *reinterpret_cast<uint4*>(tile + sw_off(row, chunk)) = make_uint4(w[0], w[1], w[2], w[3]);
+      ++chunk;
+      nw = 0;
+    }
+  };
   if (nerf) {
-    // NeRF rows are 2 pi 2^(k div 3) along axis k mod 3: one sincospi per
-    // axis, then exact angle doubling sin 2t = 2 s c, cos 2t = (c - s)(c + s).
+    // NeRF rows are 2 pi 2^(k div 3) along axis k mod 3: one sin/cos per axis,
+    // then exact angle doubling sin 2t = 2 s c, cos 2t = (c - s)(c + s).
     float s[3], c[3];
-    sincospif(2.0f * p.x, &s[0], &c[0]);
-    sincospif(2.0f * p.y, &s[1], &c[1]);
-    sincospif(2.0f * p.z, &s[2], &c[2]);
+    __sincosf(6.28318530717958647f * p.x, &s[0], &c[0]);
+    __sincosf(6.28318530717958647f * p.y, &s[1], &c[1]);
+    __sincosf(6.28318530717958647f * p.z, &s[2], &c[2]);
 #pragma unroll
     for (int k = 0; k < M; ++k) {
       const int a = k % 3;
@@ -249,51 +301,51 @@ __device__ __forceinline__ void write_input_row(uint8_t* tile, int row, float3 p
         s[a] = 2.0f * ss * cc;
         c[a] = (cc - ss) * (cc + ss);
       }
-      v[3 + k] = s[a];
-      v[3 + M + k] = c[a];
+      emit(s[a], c[a]);
     }
   } else {
 #pragma unroll
     for (int k = 0; k < M; ++k) {
       const float e = fm[3 * k] * p.x + fm[3 * k + 1] * p.y + fm[3 * k + 2] * p.z;
-      sincosf(e, &v[3 + k], &v[3 + M + k]);
+      float sv, cv;
+      sincosf(e, &sv, &cv);
+      emit(sv, cv);
     }
   }
-  float z[F];
-  latent_h<F>(G, R, rl, p, z);
+  // remaining columns 2M .. K0-1: p, z, the two bias ones, zeros
+  float tail[K0 - 2 * M];
 #pragma unroll
-  for (int f = 0; f < F; ++f) v[3 + 2 * M + f] = z[f];
-  v[D0] = 1.0f;
-#pragma unroll
-  for (int i = D0 + 1; i < K0; ++i) v[i] = 0.0f;
-#pragma unroll
-  for (int j = 0; j < K0 / 8; ++j) {
-    uint4 q;
-    q.x = pack_h2(v[8 * j], v[8 * j + 1]);
-    q.y = pack_h2(v[8 * j + 2], v[8 * j + 3]);
-    q.z = pack_h2(v[8 * j + 4], v[8 * j + 5]);
-    q.w = pack_h2(v[8 * j + 6], v[8 * j + 7]);
-    *reinterpret_cast<uint4*>(tile + sw_off(row, j)) = q;
+  for (int i = 0; i < K0 - 2 * M; ++i) {
+    const int col = 2 * M + i;
+    float v = 0.0f;
+    if (col < 2 * M + 3) v = col == 2 * M ? p.x : (col == 2 * M + 1 ? p.y : p.z);
+    else if (col < D0) v = z[col - 2 * M - 3];
+    else if (col == D0 || col == D0 + 1) v = 1.0f;
+    tail[i] = v;
   }
+#pragma unroll
+  for (int i = 0; i < K0 - 2 * M; i += 2) emit(tail[i], tail[i + 1]);
 }
 
 // ---------------------------------------------------------------- kernel
 template <int M, int F, int ACT, int SH>
 __global__ void __launch_bounds__(kThreads, 1)
-    render_mma_kernel(const NetDev net, const BatchDev b, const SmemPlan plan, unsigned long long* __restrict__ ray_counter,
-                      unsigned int* __restrict__ status) {
+    render_mma_kernel(const NetDev net, const BatchDev b, const PointsDev pd, const SmemPlan plan,
+                      unsigned long long* __restrict__ ray_counter, unsigned int* __restrict__ status) {
   constexpr int D0 = 3 + 2 * M + F;
-  constexpr int K0 = ((D0 + 1 + 15) / 16) * 16;
-  static_assert(K0 <= 64, "layer-0 input must fit one 128-byte row");
+  constexpr int K0 = ((D0 + 2 + 15) / 16) * 16;  // inputs + two bias columns
+  static_assert(D0 >= 32 && K0 <= 64, "layer-0 input must fit one 128-byte row and cover the hidden width");
   constexpr int NP = SH == SRN_SHADE_FD ? 7 : 1;  // network passes per sample
+  constexpr bool POINTS = SH == kPoints;
+  constexpr bool SNAKE = ACT == SRN_ACT_SNAKEALT;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* A0all = sm + plan.oA0;
-  uint8_t* Ahall = sm + plan.oAh;
+  uint8_t* Aall = sm + plan.oA;
   uint8_t* Bw = sm + plan.oB;
   float* wl = reinterpret_cast<float*>(sm + plan.oWl);
   TFDev& tf = *reinterpret_cast<TFDev*>(sm + plan.oTF);
+  float* tfinv = reinterpret_cast<float*>(sm + plan.oTFinv);
   float* fm = reinterpret_cast<float*>(sm + plan.oFm);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + plan.oMbar);
   volatile int* misc = reinterpret_cast<volatile int*>(sm + plan.oMisc);  // [0] tmem base, [1] nerf, [4+wg] fail
@@ -302,43 +354,90 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int wg = tid >> 7, row = tid & 127, lane = tid & 31;
   const int L = net.l, D = net.D;
 
-  // ---- stage parameters: MMA layers as 32 x 64 FP16 B tiles (row o = output
-  // neuron, K-major, bias in column d_in), last layer FP32, TF, Fourier rows.
-  for (int it = tid; it < (L - 1) * 32 * 8; it += kThreads) {
-    const int layer = it / 256, o = (it >> 3) & 31, j = it & 7;
+  // ---- stage parameters as 32 x 64 FP16 B tiles (row o = output neuron,
+  // K-major).  Layer 0: columns in the tile's input order, FP32 bias as hi +
+  // lo at D0, D0+1.  Hidden layer h: tile 1 + 2(h-1) holds [W | W] (hi and
+  // lo halves of the activation), tile 2 + 2(h-1) the bias hi, lo in columns
+  // 0, 1 (multiplied by the constant tile).  SnakeAlt folding as described at
+  // the top of the file.  One thread stages one row of one layer.
+  for (int it = tid; it < (L - 1) * 32; it += kThreads) {
+    const int layer = it >> 5, o = it & 31;
     const int din = layer == 0 ? D0 : 32;
-    const __half* Wsrc = net.W_h + (layer == 0 ? 0 : (size_t)32 * D0 + (size_t)(layer - 1) * 32 * 32);
-    const float bias = net.b[layer * 32 + o];
-    uint32_t w[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      float a[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int col = 8 * j + 2 * e + h;
-        a[h] = col < din ? __half2float(Wsrc[(size_t)o * din + col]) : (col == din ? bias : 0.0f);
+    const __half* Wsrc = net.W_h + (layer == 0 ? 0 : (size_t)32 * D0 + (size_t)(layer - 1) * 32 * 32) +
+                         (size_t)o * din;
+    float bias = net.b[layer * 32 + o];
+    float scale = 1.0f;
+    if (SNAKE) {
+      scale = layer == 0 ? 2.0f : 1.0f;
+      if (layer > 0) {
+        float rs = 0.0f;
+        for (int c = 0; c < 32; ++c) rs += __half2float(Wsrc[c]);
+        bias = 2.0f * bias + rs;
+      } else {
+        bias = 2.0f * bias;
       }
-      w[e] = pack_h2(a[0], a[1]);
     }
-    *reinterpret_cast<uint4*>(Bw + layer * kBTile + sw_off(o, j)) = make_uint4(w[0], w[1], w[2], w[3]);
+    const __half bh = __float2half_rn(bias);
+    const __half bl = __float2half_rn(bias - __half2float(bh));
+    uint8_t* Wt = Bw + (layer == 0 ? 0 : 1 + 2 * (layer - 1)) * kBTile;
+    for (int j = 0; j < 8; ++j) {
+      uint32_t w[4], wb[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        __half h2[2], hb[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int col = 8 * j + 2 * e + q;
+          __half v = __float2half_rn(0.0f);
+          if (layer == 0) {
+            int src = -1;
+            if (col < 2 * M) src = (col & 1) ? 3 + M + (col >> 1) : 3 + (col >> 1);
+            else if (col < 2 * M + 3) src = col - 2 * M;
+            else if (col < D0) src = col;
+            if (src >= 0) v = __float2half_rn(scale * __half2float(Wsrc[src]));
+            if (col == D0) v = bh;
+            if (col == D0 + 1) v = bl;
+          } else {
+            v = __float2half_rn(scale * __half2float(Wsrc[col & 31]));
+          }
+          h2[q] = v;
+          hb[q] = col == 0 ? bh : (col == 1 ? bl : __float2half_rn(0.0f));
+        }
+        __half2 hh = __halves2half2(h2[0], h2[1]), hbb = __halves2half2(hb[0], hb[1]);
+        w[e] = *reinterpret_cast<uint32_t*>(&hh);
+        wb[e] = *reinterpret_cast<uint32_t*>(&hbb);
+      }
+      *reinterpret_cast<uint4*>(Wt + sw_off(o, j)) = make_uint4(w[0], w[1], w[2], w[3]);
+      if (layer > 0) *reinterpret_cast<uint4*>(Wt + kBTile + sw_off(o, j)) = make_uint4(wb[0], wb[1], wb[2], wb[3]);
+    }
   }
   {
+    // last layer on the CUDA cores: folded like the hidden layers
     const __half* Wl = net.W_h + (size_t)32 * D0 + (size_t)(L - 2) * 32 * 32;
-    for (int i = tid; i < D * 32; i += kThreads) wl[i] = __half2float(Wl[i]);
-    if (tid < D) wl[D * 32 + tid] = net.b[(L - 1) * 32 + tid];
+    for (int i = tid; i < D * 32; i += kThreads) wl[i] = (SNAKE ? 0.5f : 1.0f) * __half2float(Wl[i]);
+    if (tid < D) {
+      float bias = net.b[(L - 1) * 32 + tid];
+      if (SNAKE) {
+        float rs = 0.0f;
+        for (int c = 0; c < 32; ++c) rs += __half2float(Wl[tid * 32 + c]);
+        bias += 0.5f * rs;
+      }
+      wl[D * 32 + tid] = bias;
+    }
     for (int i = tid; i < 3 * M; i += kThreads) fm[i] = net.fourier[i];
   }
   load_tf(tf, b.tf);
-  // zero the thread's A rows; the hidden tile carries the constant-1 bias column at 32
+  // the thread's A row starts at zero; the constant tile has ones in columns
+  // 0 and 1 of every row (the bias MMA of the hidden layers)
   {
-    uint8_t* A0 = A0all + wg * kTile;
-    uint8_t* Ah = Ahall + wg * kTile;
+    uint8_t* A = Aall + wg * kTile;
+    uint8_t* One = sm + plan.oOne;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      *reinterpret_cast<uint4*>(A0 + sw_off(row, j)) = make_uint4(0, 0, 0, 0);
-      uint4 q = make_uint4(0, 0, 0, 0);
-      if (j == 4) q.x = pack_h2(1.0f, 0.0f);
-      *reinterpret_cast<uint4*>(Ah + sw_off(row, j)) = q;
+    for (int j = 0; j < 8; ++j) *reinterpret_cast<uint4*>(A + sw_off(row, j)) = make_uint4(0, 0, 0, 0);
+    if (wg == 0) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        *reinterpret_cast<uint4*>(One + sw_off(row, j)) = make_uint4(j == 0 ? pack_h2(1.0f, 1.0f) : 0u, 0u, 0u, 0u);
     }
   }
   if (row == 0) {
@@ -354,8 +453,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   if (tid == 0) {
-    int ok = 1;
     // row k of a NeRF matrix: 2 pi 2^(k div 3) on axis k mod 3, zero elsewhere
+    int ok = 1;
     for (int k = 0; k < M && ok; ++k)
       for (int a = 0; a < 3; ++a) {
         const float want = (a == k % 3) ? 6.2831855f * (float)(1 << (k / 3)) : 0.0f;
@@ -363,31 +462,44 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     misc[1] = ok;
   }
+  for (int i = tid; i < SRN_MAX_TF_POINTS; i += kThreads) {
+    const float wdt = i + 1 < tf.n ? tf.pos[i + 1] - tf.pos[i] : 0.0f;
+    tfinv[i] = wdt > 0.0f ? 1.0f / wdt : 0.0f;
+  }
   __syncthreads();
   const bool nerf = misc[1] != 0;
   const uint32_t tmem = (uint32_t)misc[0];
   const uint32_t d_tmem = tmem + (uint32_t)(wg * 32);
   const uint32_t t_row = d_tmem + ((uint32_t)((row >> 5) * 32) << 16);  // warp's lane quarter
-  uint8_t* A0 = A0all + wg * kTile;
-  uint8_t* Ah = Ahall + wg * kTile;
-  const uint32_t a0_addr = smem_u32(A0), ah_addr = smem_u32(Ah), b_addr = smem_u32(Bw);
+  uint8_t* A = Aall + wg * kTile;
+  const uint32_t a_addr = smem_u32(A), b_addr = smem_u32(Bw), one_addr = smem_u32(sm + plan.oOne);
   const uint32_t mb = smem_u32(&mbar[wg]);
   const int bar_id = 1 + wg;
 
   // ---- ray state
   const int tiles_x = (b.W + 7) / 8, tiles_y = (b.H + 3) / 4;
   const long long tpf = (long long)tiles_x * tiles_y;
-  const long long n_rays = tpf * 32 * b.n_views * b.n_times;
+  const long long n_rays = POINTS ? pd.n : tpf * 32 * b.n_views * b.n_times;
   const size_t gsz = (size_t)net.R * net.R * net.R * net.F;
   bool active = false, exhausted = false, failed = false;
   long long pix = 0;
   float3 o = make_float3(0.f, 0.f, 0.f), d = o;
-  float t0 = 0.f, t1 = 0.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
+  float t0 = 0.f, t1 = 0.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, Acc = 0.f;
   int k = 0, pass = 0;
   RayLat rl{0, -1, 1.0f, 0.0f};
   float rho_c = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+  float3 ppos = make_float3(0.f, 0.f, 0.f);
   unsigned int ns = 0;
   uint32_t phase = 0;
+  if (POINTS) {
+    int k0;
+    float f;
+    time_weights(net, pd.time, k0, f);
+    rl.g0 = (int)(k0 * gsz);
+    rl.g1 = net.nkey > 1 ? (int)((k0 + 1) * gsz) : -1;
+    rl.w0 = net.nkey > 1 ? 1.0f - f : 1.0f;
+    rl.w1 = f;
+  }
 
   while (true) {
     // ---- refill: threads without a ray claim new ones (warp-aggregated)
@@ -403,6 +515,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         const long long r = (long long)base + __popc(mask & ((1u << lane) - 1u));
         if (r >= n_rays) {
           exhausted = true;
+        } else if (POINTS) {
+          pix = r;
+          ppos = make_float3(clamp01f(pd.pts[3 * r]), clamp01f(pd.pts[3 * r + 1]), clamp01f(pd.pts[3 * r + 2]));
+          active = true;
         } else {
           const long long tile = r >> 5;
           const int li = (int)(r & 31);
@@ -421,7 +537,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               rl.g1 = net.nkey > 1 ? (int)((k0 + 1) * gsz) : -1;
               rl.w0 = net.nkey > 1 ? 1.0f - f : 1.0f;
               rl.w1 = f;
-              C0 = C1 = C2 = A = 0.f;
+              C0 = C1 = C2 = Acc = 0.f;
               k = 0;
               pass = 0;
               active = true;
@@ -434,24 +550,24 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 
     // ---- layer-0 input of this pass
-    float ta = 0.f, len = 0.f;
-    float3 p = make_float3(0.f, 0.f, 0.f);
-    if (active && !failed) {
-      ta = fmaf((float)k, b.step, t0);
+    float len = 0.f;
+    if (POINTS && active && !failed) {
+      write_input_row<M, F, K0>(A, row, ppos, nerf, fm, net.grid_h, net.R, rl);
+    } else if (active && !failed) {
+      const float ta = fmaf((float)k, b.step, t0);
       const float tb = fminf(fmaf((float)(k + 1), b.step, t0), t1);
       len = tb - ta;
       const float tm = 0.5f * (ta + tb);
-      p = make_float3(clamp01f(fmaf(tm, d.x, o.x) + 0.5f), clamp01f(fmaf(tm, d.y, o.y) + 0.5f),
-                      clamp01f(fmaf(tm, d.z, o.z) + 0.5f));
-      float3 q = p;
+      float3 q = make_float3(clamp01f(fmaf(tm, d.x, o.x) + 0.5f), clamp01f(fmaf(tm, d.y, o.y) + 0.5f),
+                             clamp01f(fmaf(tm, d.z, o.z) + 0.5f));
       if (SH == SRN_SHADE_FD && pass > 0) {
         const int ax = (pass - 1) >> 1;
         const float h = (pass & 1) ? b.fd_h : -b.fd_h;
-        if (ax == 0) q.x = clamp01f(p.x + h);
-        if (ax == 1) q.y = clamp01f(p.y + h);
-        if (ax == 2) q.z = clamp01f(p.z + h);
+        if (ax == 0) q.x = clamp01f(q.x + h);
+        if (ax == 1) q.y = clamp01f(q.y + h);
+        if (ax == 2) q.z = clamp01f(q.z + h);
       }
-      write_input_row<M, F, K0>(A0, row, q, nerf, fm, net.grid_h, net.R, rl);
+      write_input_row<M, F, K0>(A, row, q, nerf, fm, net.grid_h, net.R, rl);
     }
     fence_proxy_async();
     tc_fence_before();
@@ -461,7 +577,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_after();
 #pragma unroll
       for (int kk = 0; kk < K0 / 16; ++kk)
-        mma_f16(d_tmem, sw128_desc(a0_addr + kk * 32), sw128_desc(b_addr + kk * 32), kIdesc, kk > 0);
+        mma_f16(d_tmem, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), kIdesc, kk > 0);
       mma_commit(mb);
     }
 
@@ -482,14 +598,20 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!failed) tmem_ld32(t_row, x);
       if (layer < L - 2) {
         if (!failed) {
+          // activation as FP16 hi (columns 0..31) + lo (columns 32..63)
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            uint4 q;
-            q.x = pack_h2(act_fast<ACT>(x[8 * j]), act_fast<ACT>(x[8 * j + 1]));
-            q.y = pack_h2(act_fast<ACT>(x[8 * j + 2]), act_fast<ACT>(x[8 * j + 3]));
-            q.z = pack_h2(act_fast<ACT>(x[8 * j + 4]), act_fast<ACT>(x[8 * j + 5]));
-            q.w = pack_h2(act_fast<ACT>(x[8 * j + 6]), act_fast<ACT>(x[8 * j + 7]));
-            *reinterpret_cast<uint4*>(Ah + sw_off(row, j)) = q;
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float a0 = act_fold<ACT>(x[8 * j + 2 * e]), a1 = act_fold<ACT>(x[8 * j + 2 * e + 1]);
+              const __half2 h = __floats2half2_rn(a0, a1);
+              const float2 hb = __half22float2(h);
+              hi[e] = *reinterpret_cast<const uint32_t*>(&h);
+              lo[e] = pack_h2(a0 - hb.x, a1 - hb.y);
+            }
+            *reinterpret_cast<uint4*>(A + sw_off(row, j)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4*>(A + sw_off(row, 4 + j)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
           }
         }
         fence_proxy_async();
@@ -498,16 +620,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (misc[4 + wg]) { stop = true; break; }
         if (row == 0) {
           tc_fence_after();
-          const uint32_t bl = b_addr + (layer + 1) * kBTile;
+          const uint32_t bw = b_addr + (1 + 2 * layer) * kBTile;
+          mma_f16(d_tmem, sw128_desc(one_addr), sw128_desc(bw + kBTile), kIdesc, 0u);  // bias
 #pragma unroll
-          for (int kk = 0; kk < 3; ++kk)
-            mma_f16(d_tmem, sw128_desc(ah_addr + kk * 32), sw128_desc(bl + kk * 32), kIdesc, kk > 0);
+          for (int kk = 0; kk < 4; ++kk)
+            mma_f16(d_tmem, sw128_desc(a_addr + kk * 32), sw128_desc(bw + kk * 32), kIdesc, 1u);
           mma_commit(mb);
         }
       } else if (!failed) {
         float a[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) a[j] = act_fast<ACT>(x[j]);
+        for (int j = 0; j < 32; ++j) a[j] = act_fold<ACT>(x[j]);
 #pragma unroll
         for (int dd = 0; dd < 4; ++dd) {
           if (dd < D) {
@@ -521,6 +644,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     if (stop) break;
 
+    if (POINTS) {
+      if (active && !failed) {
+        for (int dd = 0; dd < D; ++dd) pd.out[pix * D + dd] = out[dd];
+        ++ns;
+        active = false;
+      }
+      continue;
+    }
     // ---- transfer function, shading, compositing, termination
     if (active && !failed) {
       bool sample_done = true;
@@ -542,17 +673,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (sample_done) {
         ++ns;
-        float4 c = tf_eval(tf, rho_c);
+        float4 c = tf_eval_inv(tf, tfinv, rho_c);
         const float alpha = 1.0f - __expf(-c.w * tf.opacity_scale * len);
         if (SH != SRN_SHADE_NONE) shade(c, g, d);
-        const float w = (1.0f - A) * alpha;
+        const float w = (1.0f - Acc) * alpha;
         C0 = fmaf(w, c.x, C0);
         C1 = fmaf(w, c.y, C1);
         C2 = fmaf(w, c.z, C2);
-        A += w;
+        Acc += w;
         ++k;
-        if (A >= b.et || fmaf((float)k, b.step, t0) >= t1) {
-          reinterpret_cast<float4*>(b.out)[pix] = make_float4(C0, C1, C2, A);
+        if (Acc >= b.et || fmaf((float)k, b.step, t0) >= t1) {
+          reinterpret_cast<float4*>(b.out)[pix] = make_float4(C0, C1, C2, Acc);
           active = false;
         }
       }
@@ -562,7 +693,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (failed || misc[4 + wg]) {
     if (row == 0) atomicExch(status, (unsigned int)SRN_ERR_TIMEOUT);
   }
-  add_samples(b.samples, ns);
+  if (!POINTS) add_samples(b.samples, ns);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -570,8 +701,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 template <int M, int F, int ACT, int SH>
-cudaError_t launch_t(const NetDev& net, const BatchDev& b, unsigned long long* ctr, unsigned int* status,
-                     cudaStream_t s) {
+cudaError_t launch_t(const NetDev& net, const BatchDev& b, const PointsDev& pd, unsigned long long* ctr,
+                     unsigned int* status, cudaStream_t s) {
   SmemPlan plan = make_plan(net);
   auto k = render_mma_kernel<M, F, ACT, SH>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total);
@@ -582,7 +713,7 @@ cudaError_t launch_t(const NetDev& net, const BatchDev& b, unsigned long long* c
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  k<<<sms, kThreads, plan.total, s>>>(net, b, plan, ctr, status);
+  k<<<sms, kThreads, plan.total, s>>>(net, b, pd, plan, ctr, status);
   return cudaGetLastError();
 }
 
@@ -590,9 +721,9 @@ template <int M, int F, int ACT>
 cudaError_t dispatch_shading(const NetDev& net, const BatchDev& b, unsigned long long* ctr, unsigned int* st,
                              cudaStream_t s) {
   switch (b.shading) {
-    case SRN_SHADE_NONE: return launch_t<M, F, ACT, SRN_SHADE_NONE>(net, b, ctr, st, s);
-    case SRN_SHADE_FD: return launch_t<M, F, ACT, SRN_SHADE_FD>(net, b, ctr, st, s);
-    default: return launch_t<M, F, ACT, SRN_SHADE_HEAD>(net, b, ctr, st, s);
+    case SRN_SHADE_NONE: return launch_t<M, F, ACT, SRN_SHADE_NONE>(net, b, PointsDev{}, ctr, st, s);
+    case SRN_SHADE_FD: return launch_t<M, F, ACT, SRN_SHADE_FD>(net, b, PointsDev{}, ctr, st, s);
+    default: return launch_t<M, F, ACT, SRN_SHADE_HEAD>(net, b, PointsDev{}, ctr, st, s);
   }
 }
 
@@ -617,6 +748,27 @@ cudaError_t launch_render_mma(const NetDev& n, const BatchDev& b, unsigned long 
   }
   return n.act == SRN_ACT_SNAKEALT ? dispatch_shading<12, 8, SRN_ACT_SNAKEALT>(n, b, ctr, status, s)
                                    : dispatch_shading<12, 8, SRN_ACT_SINE>(n, b, ctr, status, s);
+}
+
+}  // namespace srn
+
+namespace srn {
+
+bool eval_mma_supported(const NetDev& n) { return render_mma_supported(n, SRN_SHADE_NONE); }
+
+// Network output at n points with the tensor-core layers (mode kPoints).
+cudaError_t launch_eval_mma(const NetDev& n, const float* pts, long long count, float time, float* out,
+                            unsigned long long* ctr, unsigned int* status, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  BatchDev b;
+  memset(&b, 0, sizeof(b));
+  b.tf.n = 2;
+  PointsDev pd{pts, out, count, time};
+  if (n.m == 14 && n.F == 16)
+    return n.act == SRN_ACT_SNAKEALT ? launch_t<14, 16, SRN_ACT_SNAKEALT, kPoints>(n, b, pd, ctr, status, s)
+                                     : launch_t<14, 16, SRN_ACT_SINE, kPoints>(n, b, pd, ctr, status, s);
+  return n.act == SRN_ACT_SNAKEALT ? launch_t<12, 8, SRN_ACT_SNAKEALT, kPoints>(n, b, pd, ctr, status, s)
+                                   : launch_t<12, 8, SRN_ACT_SINE, kPoints>(n, b, pd, ctr, status, s);
 }
 
 }  // namespace srn

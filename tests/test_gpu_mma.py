@@ -154,3 +154,62 @@ def test_mma_rejects_unsupported(srn):
         out = torch.zeros((1, 1, 8, 8, 4), device="cuda")
         S.srn_render(net.ctx, synth.orbit_cameras(1), synth.tf_preset(4), S.render_desc(8, 8, 0.01), out)
     assert e.value.status == S.SRN_ERR_UNSUPPORTED
+
+
+def _eval16(S, net, pts, t=0.0):
+    import torch
+    out = torch.zeros((len(pts), net.out_dim), device="cuda")
+    S.srn_eval(net.ctx, torch.tensor(pts, device="cuda"), out, time=t)
+    torch.cuda.synchronize()
+    st, msg = S.srn_sync_status(net.ctx)
+    assert st == 0, msg
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("shape", ["cfg2", "cfg1", "head", "time"])
+def test_mma_eval_density_parity(srn, shape):
+    """FP16 tensor-core network at points vs the FP64 oracle on the same FP16
+    parameters: relative density error <= 1e-3."""
+    S = srn
+    t = 0.0
+    if shape == "cfg2":
+        p = H.cfg2_params(seed=60)
+    elif shape == "cfg1":
+        p = H.cfg1_params(seed=61)
+    elif shape == "head":
+        p = H.cfg2_params(seed=62, R=16, out_dim=4)
+    else:
+        p = H.cfg2_params(seed=63, R=16, nkey=5, key_times=[0, 4, 8, 12, 15])
+        t = 9.5
+    net, q = _net16(S, p)
+    rng = np.random.default_rng(64)
+    n = 100_003  # ragged against the 128-row tiles
+    pts = rng.uniform(0, 1, (n, 3)).astype(np.float32)
+    pts[:4] = [[0, 0, 0], [1, 1, 1], [0.5, 1, 0], [1e-7, 0.999999, 0.5]]
+    got = _eval16(S, net, pts, t)
+    ref = oracle.net_forward(oracle.OracleNet(q), pts, t)
+    err = H.rel_density_err(got, ref)
+    print(f"fp16 eval {shape}: max rel density error {err.max():.2e}, mean {err.mean():.2e}")
+    assert err.max() <= H.TOL_FP16_RHO
+
+
+def test_mma_eval_trained_network(srn):
+    """The same check on a network fitted by the library (weights and grid
+    move away from their initial ranges during training)."""
+    import torch
+    S = srn
+    vol = synth.noise_volume(96, seed=65)
+    p = synth.init_params(R=32, F=16, m=14, layers=4, width=32, act=synth.ACT_SNAKEALT, seed=66)
+    net = S.Network(p, precision=S.SRN_PREC_FP16, max_fit_points=1 << 16, adam=True)
+    loss = torch.zeros(1, device="cuda")
+    vt = vol.cuda()
+    for s in range(400):
+        S.srn_fit_step(net.ctx, vt, 1 << 16, 9, s, loss)
+    torch.cuda.synchronize()
+    q = net.unpack_half()
+    pts = np.random.default_rng(67).uniform(0, 1, (20000, 3)).astype(np.float32)
+    got = _eval16(S, net, pts)
+    ref = oracle.net_forward(oracle.OracleNet(q), pts)
+    err = H.rel_density_err(got, ref)
+    print(f"fp16 eval trained: max rel density error {err.max():.2e}, mean {err.mean():.2e}, loss {loss.item():.4f}")
+    assert err.max() <= H.TOL_FP16_RHO
