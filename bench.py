@@ -103,6 +103,27 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def rank_views(k, rank, world, n_views=N_VIEWS):
+    """View of timed frame k on a rank: ranks walk the orbit with disjoint
+    offsets, so N replicas render N different frames per step (weak scaling;
+    no data crosses ranks)."""
+    return (k * world + rank) % n_views
+
+
+def aggregate(t_seconds, samples, world, device):
+    """Whole-job timing over ranks: the slowest rank's time and the sum of
+    the samples all ranks took (a max and a sum all-reduce, nothing else)."""
+    if world <= 1:
+        return t_seconds, samples
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_seconds], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    n = torch.tensor([float(samples)], device=device, dtype=torch.float64)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(n.item())
+
+
 def setup_scene(device="cuda", fit_steps=FIT_STEPS, seed=0):
     """Volume, fitted network (FP16 render copy), TF and cameras of config 2."""
     import torch
@@ -215,7 +236,7 @@ def run_ours(args, rank, world):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MiB > L2
 
     def frame(k, samples=None):
-        srn.srn_render(net.ctx, [cams[(k + rank) % N_VIEWS]], tf, desc, out, samples=samples)
+        srn.srn_render(net.ctx, [cams[rank_views(k, rank, world)]], tf, desc, out, samples=samples)
 
     for k in range(args.warmup):
         frame(k)
@@ -237,12 +258,7 @@ def run_ours(args, rank, world):
     ms = [a.elapsed_time(b) for a, b in evs]
     t_total = sum(ms) / 1e3
     samples = int(ctr.item())
-    if world > 1:
-        t = torch.tensor([t_total], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        s = torch.tensor([samples], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(s)
-        t_total, samples = float(t.item()), int(s.item())
+    t_total, samples = aggregate(t_total, samples, world, dev)
     value = samples / t_total
     ms_frame = t_total * 1e3 / args.steps
 

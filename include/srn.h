@@ -282,6 +282,19 @@ srn_status srn_backward_static(const srn_config* cfg, const srn_params* params, 
                                float time, const float* dout_dev, float* dgrid_dev, float* dweights_dev,
                                float* dbiases_dev, void* stream);
 
+/*
+ * Checkpoint of a context's network: the shape fields of its config, the
+ * FP32 grid, weights and biases, the Adam moments when the context has them,
+ * and the caller's step counter (the fit's sampler and bias correction are
+ * keyed by it, so a resumed fit reproduces the uninterrupted one exactly).
+ * Little-endian binary file with a magic, a version and counts.  Both calls
+ * synchronize the device.  srn_load requires a context of the same shape
+ * (SRN_ERR_INVALID_ARG otherwise), writes into the context's parameter
+ * arrays, refreshes the FP16 copies and returns the step in *step_out.
+ */
+srn_status srn_save(srn_ctx* ctx, const char* path, int step);
+srn_status srn_load(srn_ctx* ctx, const char* path, int* step_out);
+
 /* Synchronize `stream` and return (then clear) the device status word:
  * SRN_OK, SRN_ERR_NONFINITE or SRN_ERR_INTERNAL. */
 srn_status srn_sync_status(srn_ctx* ctx, void* stream);

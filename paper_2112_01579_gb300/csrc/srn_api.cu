@@ -363,6 +363,127 @@ srn_status srn_image_mse(const float* a_dev, const float* b_dev, long long n_pix
   return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_image_mse");
 }
 
+namespace {
+
+const char kCkptMagic[8] = {'S', 'R', 'N', 'C', 'K', 'P', 'T', '1'};
+constexpr uint32_t kCkptVersion = 1;
+
+struct CkptHeader {
+  char magic[8];
+  uint32_t version;
+  int32_t shape[9];  // grid_res, feat, n_fourier, layers, width, out_dim, activation, n_keyframes, has_adam
+  int32_t step;
+  uint64_t n_grid, n_weights, n_biases;
+};
+
+void ckpt_shape(const srn_ctx* ctx, int32_t shape[9]) {
+  const srn_config& c = ctx->cfg;
+  shape[0] = c.grid_res; shape[1] = c.feat; shape[2] = c.n_fourier; shape[3] = c.layers; shape[4] = c.width;
+  shape[5] = c.out_dim; shape[6] = c.activation; shape[7] = c.n_keyframes;
+  shape[8] = (ctx->prm.adam_m && ctx->prm.adam_v) ? 1 : 0;
+}
+
+}  // namespace
+
+srn_status srn_save(srn_ctx* ctx, const char* path, int step) {
+  if (!ctx || !path) return fail(SRN_ERR_INVALID_ARG, "ctx and path are required");
+  srn_status st = use_device(ctx);
+  if (st) return st;
+  const NetDev n = make_net(ctx);
+  CkptHeader h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, kCkptMagic, 8);
+  h.version = kCkptVersion;
+  ckpt_shape(ctx, h.shape);
+  h.step = step;
+  h.n_grid = net_grid_count(n);
+  h.n_weights = net_weight_count(n);
+  h.n_biases = net_bias_count(n);
+  const size_t total = h.n_grid + h.n_weights + h.n_biases;
+  float* host = (float*)malloc(sizeof(float) * total * (h.shape[8] ? 3 : 1));
+  if (!host) return fail(SRN_ERR_INTERNAL, "out of host memory");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(host, ctx->prm.grid, sizeof(float) * h.n_grid, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(host + h.n_grid, ctx->prm.weights, sizeof(float) * h.n_weights, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(host + h.n_grid + h.n_weights, ctx->prm.biases, sizeof(float) * h.n_biases,
+                   cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && h.shape[8]) {
+    e = cudaMemcpy(host + total, ctx->prm.adam_m, sizeof(float) * total, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(host + 2 * total, ctx->prm.adam_v, sizeof(float) * total, cudaMemcpyDeviceToHost);
+  }
+  if (e != cudaSuccess) {
+    free(host);
+    return cuda_fail(e, "srn_save");
+  }
+  FILE* f = fopen(path, "wb");
+  if (!f) {
+    free(host);
+    return fail(SRN_ERR_INVALID_ARG, "cannot open %s for writing", path);
+  }
+  const size_t nfl = total * (h.shape[8] ? 3 : 1);
+  const bool ok = fwrite(&h, sizeof(h), 1, f) == 1 && fwrite(host, sizeof(float), nfl, f) == nfl;
+  free(host);
+  if (fclose(f) != 0 || !ok) return fail(SRN_ERR_INTERNAL, "short write to %s", path);
+  return SRN_OK;
+}
+
+srn_status srn_load(srn_ctx* ctx, const char* path, int* step_out) {
+  if (!ctx || !path) return fail(SRN_ERR_INVALID_ARG, "ctx and path are required");
+  srn_status st = use_device(ctx);
+  if (st) return st;
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(SRN_ERR_INVALID_ARG, "cannot open %s", path);
+  CkptHeader h;
+  if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != kCkptVersion) {
+    fclose(f);
+    return fail(SRN_ERR_INVALID_ARG, "%s is not an srn checkpoint of version %u", path, kCkptVersion);
+  }
+  int32_t shape[9];
+  ckpt_shape(ctx, shape);
+  const NetDev n = make_net(ctx);
+  if (memcmp(shape, h.shape, sizeof(int32_t) * 8) != 0 || h.n_grid != net_grid_count(n) ||
+      h.n_weights != net_weight_count(n) || h.n_biases != net_bias_count(n)) {
+    fclose(f);
+    return fail(SRN_ERR_INVALID_ARG, "checkpoint %s has a different network shape", path);
+  }
+  const size_t total = h.n_grid + h.n_weights + h.n_biases;
+  const size_t nfl = total * (h.shape[8] ? 3 : 1);
+  float* host = (float*)malloc(sizeof(float) * nfl);
+  if (!host) {
+    fclose(f);
+    return fail(SRN_ERR_INTERNAL, "out of host memory");
+  }
+  const bool ok = fread(host, sizeof(float), nfl, f) == nfl;
+  fclose(f);
+  if (!ok) {
+    free(host);
+    return fail(SRN_ERR_INVALID_ARG, "checkpoint %s is truncated", path);
+  }
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(ctx->prm.grid, host, sizeof(float) * h.n_grid, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(ctx->prm.weights, host + h.n_grid, sizeof(float) * h.n_weights, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(ctx->prm.biases, host + h.n_grid + h.n_weights, sizeof(float) * h.n_biases,
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && h.shape[8] && shape[8]) {
+    e = cudaMemcpy(ctx->prm.adam_m, host + total, sizeof(float) * total, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->prm.adam_v, host + 2 * total, sizeof(float) * total, cudaMemcpyHostToDevice);
+  }
+  free(host);
+  if (e != cudaSuccess) return cuda_fail(e, "srn_load");
+  if (ctx->prm.grid_h && ctx->prm.weights_h) {
+    e = launch_to_half(n.grid, (__half*)ctx->prm.grid_h, net_grid_count(n), 0);
+    if (e == cudaSuccess) e = launch_to_half(n.W, (__half*)ctx->prm.weights_h, net_weight_count(n), 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "srn_load");
+  }
+  if (step_out) *step_out = h.step;
+  return SRN_OK;
+}
+
 srn_status srn_density_mse(const float* a_dev, const float* b_dev, long long n, double* mse_dev, void* stream) {
   if (n < 0 || !mse_dev || (n > 0 && (!a_dev || !b_dev))) return fail(SRN_ERR_INVALID_ARG, "bad arrays");
   cudaError_t e = launch_density_mse(a_dev, b_dev, n, mse_dev, (cudaStream_t)stream);

@@ -26,7 +26,7 @@ SRN_MAX_KEYFRAMES, SRN_MAX_TF_POINTS, SRN_MAX_VIEWS, SRN_MAX_TIMES = 32, 32, 64,
 EXPORTED = ["srn_version", "srn_last_error", "srn_create", "srn_destroy", "srn_set_params", "srn_sync_half",
             "srn_render", "srn_dvr_dense", "srn_eval", "srn_density_grad", "srn_backward", "srn_fit_step",
             "srn_sync_status", "srn_image_mse", "srn_backward_static", "srn_density_mse", "srn_resample",
-            "srn_lowpass_resample"]
+            "srn_lowpass_resample", "srn_save", "srn_load"]
 
 
 class SrnError(RuntimeError):
@@ -94,6 +94,8 @@ def lib():
         L.srn_density_mse.argtypes = [vp, vp, C.c_longlong, vp, vp]
         L.srn_resample.argtypes = [vp, C.POINTER(C.c_int), vp, C.POINTER(C.c_int), vp]
         L.srn_lowpass_resample.argtypes = [vp, C.POINTER(C.c_int), i, vp, vp, vp]
+        L.srn_save.argtypes = [vp, C.c_char_p, i]
+        L.srn_load.argtypes = [vp, C.c_char_p, C.POINTER(C.c_int)]
         for name in EXPORTED[2:]:
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -221,6 +223,17 @@ def srn_sync_status(ctx, stream=None):
 def srn_image_mse(a, b, out, stream=None):
     """out: float64 CUDA tensor [1]."""
     _check(lib().srn_image_mse(_ptr(a), _ptr(b), a.numel() // 4, _ptr(out), _stream(stream)))
+
+
+def srn_save(ctx, path, step):
+    _check(lib().srn_save(ctx, str(path).encode(), int(step)))
+
+
+def srn_load(ctx, path):
+    """Returns the step stored in the checkpoint."""
+    st = C.c_int()
+    _check(lib().srn_load(ctx, str(path).encode(), C.byref(st)))
+    return st.value
 
 
 def srn_density_mse(a, b, out, stream=None):
