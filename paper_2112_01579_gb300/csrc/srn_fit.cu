@@ -277,27 +277,52 @@ __global__ void __launch_bounds__(kSortThreads) sort_hist_kernel(const unsigned 
   hist[(size_t)d * nblocks + blockIdx.x] = t;
 }
 
-// Exclusive scan of m counts in place (one block, fixed segmentation).
-__global__ void __launch_bounds__(1024) scan_kernel(unsigned int* __restrict__ a, int m) {
-  __shared__ unsigned int part[1024];
+// Exclusive scan of m counts in place by one block: tiles of 8192 values are
+// staged coalesced in shared memory, each thread scans 8 consecutive values,
+// and a block-wide scan of the thread sums plus a running carry links the
+// tiles.  Fixed order, so deterministic.
+constexpr int kScanThreads = 1024, kScanPer = 8, kScanTile = kScanThreads * kScanPer;
+__global__ void __launch_bounds__(kScanThreads) scan_kernel(unsigned int* __restrict__ a, int m) {
+  __shared__ unsigned int tile[kScanTile + kScanTile / 32];  // padded: 8-strided reads stay conflict-free
+  __shared__ unsigned int part[kScanThreads];
+  __shared__ unsigned int carry_s;
   const int tid = threadIdx.x;
-  const int seg = (m + 1023) / 1024;
-  const int b0 = min(tid * seg, m), b1 = min(b0 + seg, m);
-  unsigned int s = 0;
-  for (int i = b0; i < b1; ++i) s += a[i];
-  part[tid] = s;
-  __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    const unsigned int v = tid >= off ? part[tid - off] : 0u;
+  if (tid == 0) carry_s = 0;
+  for (int base = 0; base < m; base += kScanTile) {
+    for (int i = tid; i < kScanTile; i += kScanThreads) {
+      const int g = base + i;
+      tile[i + i / 32] = g < m ? a[g] : 0u;
+    }
     __syncthreads();
-    part[tid] += v;
+    unsigned int v[kScanPer], s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+      const int i = tid * kScanPer + k;
+      v[k] = tile[i + i / 32];
+      s += v[k];
+    }
+    part[tid] = s;
     __syncthreads();
-  }
-  unsigned int run = part[tid] - s;
-  for (int i = b0; i < b1; ++i) {
-    const unsigned int v = a[i];
-    a[i] = run;
-    run += v;
+    for (int off = 1; off < kScanThreads; off <<= 1) {
+      const unsigned int t = tid >= off ? part[tid - off] : 0u;
+      __syncthreads();
+      part[tid] += t;
+      __syncthreads();
+    }
+    unsigned int run = carry_s + part[tid] - s;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+      const int i = tid * kScanPer + k;
+      tile[i + i / 32] = run;
+      run += v[k];
+    }
+    __syncthreads();
+    for (int i = tid; i < kScanTile; i += kScanThreads) {
+      const int g = base + i;
+      if (g < m) a[g] = tile[i + i / 32];
+    }
+    if (tid == kScanThreads - 1) carry_s += part[tid];
+    __syncthreads();
   }
 }
 
@@ -410,22 +435,102 @@ __global__ void grid_grad_kernel(const float* __restrict__ pts, const float* __r
   }
 }
 
-// Fixed-order sum of the CTA partials: weights, biases and the loss.
-__global__ void reduce_parts_kernel(const float* __restrict__ part, int n_cta, int nW, int nb,
-                                    float* __restrict__ outW, float* __restrict__ outb, float* __restrict__ loss,
-                                    float inv_n, unsigned int* __restrict__ flag) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  const int ne = nW + nb;
-  if (e > ne) return;
-  float s = 0.f;
-  for (int c = 0; c < n_cta; ++c) s += part[(size_t)c * (ne + 1) + e];
-  if (e < nW) outW[e] = s;
-  else if (e < ne) outb[e - nW] = s;
-  else if (loss) {
-    s *= inv_n;
-    *loss = s;
+// Dense cells (many points per cell): one warp per (cell, corner) sums
+// w_corner(p) * dz over the cell's points (sorted order, lane-strided, fixed
+// butterfly) into part[cell][corner][F]; vertex_gather_kernel then adds the
+// <= 8 partials of each vertex in a fixed order.
+template <int F>
+__global__ void cell_corner_kernel(const float* __restrict__ pts, const float* __restrict__ dz,
+                                   const unsigned int* __restrict__ sidx, const unsigned int* __restrict__ start,
+                                   int R, long long n_cells, float* __restrict__ part) {
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= n_cells * 8) return;
+  const long long cell = wid >> 3;
+  const int c = (int)(wid & 7);
+  const int dx = c & 1, dy = (c >> 1) & 1, dzz = c >> 2;
+  float acc[F];
+#pragma unroll
+  for (int f = 0; f < F; ++f) acc[f] = 0.f;
+  const int s0 = (int)start[cell], s1 = (int)start[cell + 1];
+  for (int s = s0 + lane; s < s1; s += 32) {
+    const int j = (int)sidx[s];
+    int ix, iy, iz;
+    float fx, fy, fz;
+    cell_coord(pts[3 * j], R, ix, fx);
+    cell_coord(pts[3 * j + 1], R, iy, fy);
+    cell_coord(pts[3 * j + 2], R, iz, fz);
+    const float w = (dx ? fx : 1.0f - fx) * (dy ? fy : 1.0f - fy) * (dzz ? fz : 1.0f - fz);
+    const float4* zz = reinterpret_cast<const float4*>(dz + (size_t)j * F);
+#pragma unroll
+    for (int f = 0; f < F; f += 4) {
+      const float4 q = zz[f / 4];
+      acc[f] = fmaf(w, q.x, acc[f]);
+      acc[f + 1] = fmaf(w, q.y, acc[f + 1]);
+      acc[f + 2] = fmaf(w, q.z, acc[f + 2]);
+      acc[f + 3] = fmaf(w, q.w, acc[f + 3]);
+    }
   }
-  if (!isfinite(s) && (e < ne || loss)) atomicOr(flag, 1u);
+#pragma unroll
+  for (int f = 0; f < F; ++f)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc[f] += __shfl_xor_sync(0xffffffffu, acc[f], off);
+  if (lane == 0) {
+#pragma unroll
+    for (int f = 0; f < F; ++f) part[(size_t)wid * F + f] = acc[f];
+  }
+}
+
+template <int F>
+__global__ void vertex_gather_kernel(const float* __restrict__ part, int R, float w0, float w1,
+                                     float* __restrict__ g0, float* __restrict__ g1, unsigned int* __restrict__ flag) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)R * R * R * F) return;
+  const long long v = i / F;
+  const int f = (int)(i - v * F);
+  const int vx = (int)(v % R), vy = (int)((v / R) % R), vz = (int)(v / ((long long)R * R));
+  float acc = 0.f;
+  for (int c = 0; c < 8; ++c) {
+    const int dx = c & 1, dy = (c >> 1) & 1, dzz = c >> 2;
+    const int cx = vx - dx, cy = vy - dy, cz = vz - dzz;
+    if (cx < 0 || cy < 0 || cz < 0 || cx > R - 2 || cy > R - 2 || cz > R - 2) continue;
+    const long long cell = ((long long)cz * (R - 1) + cy) * (R - 1) + cx;
+    acc += part[(cell * 8 + c) * F + f];
+  }
+  g0[i] = w0 * acc;
+  if (g1) g1[i] = w1 * acc;
+  if (!isfinite(acc)) atomicOr(flag, 1u);
+}
+
+// Fixed-order sum of the CTA partials: weights, biases and the loss.  A
+// block covers 32 entries; its 8 warps each sum a contiguous eighth of the
+// partial rows in row order, then the 8 sums are added in warp order.
+__global__ void __launch_bounds__(256) reduce_parts_kernel(const float* __restrict__ part, int n_cta, int nW, int nb,
+                                                           float* __restrict__ outW, float* __restrict__ outb,
+                                                           float* __restrict__ loss, float inv_n,
+                                                           unsigned int* __restrict__ flag) {
+  __shared__ float acc[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + lane;
+  const int ne = nW + nb;
+  const int r0 = (int)((long long)n_cta * w / 8), r1 = (int)((long long)n_cta * (w + 1) / 8);
+  float s = 0.f;
+  if (e <= ne)
+    for (int c = r0; c < r1; ++c) s += part[(size_t)c * (ne + 1) + e];
+  acc[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && e <= ne) {
+    float t = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += acc[k][lane];
+    if (e < nW) outW[e] = t;
+    else if (e < ne) outb[e - nW] = t;
+    else if (loss) {
+      t *= inv_n;
+      *loss = t;
+    }
+    if (!isfinite(t) && (e < ne || loss)) atomicOr(flag, 1u);
+  }
 }
 
 // Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias correction at step + 1) over
@@ -506,7 +611,7 @@ cudaError_t run_backward(FitScratch& s, const NetDev& net, PointArgs pa, float* 
   const int nblocks = (n + kSortItems - 1) / kSortItems;
   for (int shift = 0; shift < bits && n > 0; shift += 8) {
     sort_hist_kernel<<<nblocks, kSortThreads, 0, st>>>(k_in, n, shift, s.hist, nblocks);
-    scan_kernel<<<1, 1024, 0, st>>>(s.hist, 256 * nblocks);
+    scan_kernel<<<1, kScanThreads, 0, st>>>(s.hist, 256 * nblocks);
     sort_scatter_kernel<<<nblocks, kSortThreads, 0, st>>>(k_in, v_in, k_out, v_out, n, shift, s.hist, nblocks);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     std::swap(k_in, k_out);
@@ -536,7 +641,31 @@ cudaError_t run_backward(FitScratch& s, const NetDev& net, PointArgs pa, float* 
   float* g1 = net.nkey > 1 ? g0 + gsz : nullptr;
   const long long n_vert = (long long)net.R * net.R * net.R;
   const unsigned int gblocks = (unsigned int)((n_vert * 32 + 255) / 256);
-  if (n > 0) {
+  const bool dense_cells = s.cell_part && (size_t)n >= 32 * s.n_cells;
+  if (n > 0 && dense_cells) {
+    const long long nw = (long long)s.n_cells * 8;
+    const unsigned int cb = (unsigned int)((nw * 32 + 255) / 256);
+    const long long nv = n_vert * net.F;
+    const unsigned int vb = (unsigned int)((nv + 255) / 256);
+    switch (net.F) {
+      case 4:
+        cell_corner_kernel<4><<<cb, 256, 0, st>>>(s.pts, s.dz, v_in, s.cell_start, net.R, (long long)s.n_cells, s.cell_part);
+        vertex_gather_kernel<4><<<vb, 256, 0, st>>>(s.cell_part, net.R, w0, w1, g0, g1, s.flag);
+        break;
+      case 8:
+        cell_corner_kernel<8><<<cb, 256, 0, st>>>(s.pts, s.dz, v_in, s.cell_start, net.R, (long long)s.n_cells, s.cell_part);
+        vertex_gather_kernel<8><<<vb, 256, 0, st>>>(s.cell_part, net.R, w0, w1, g0, g1, s.flag);
+        break;
+      case 16:
+        cell_corner_kernel<16><<<cb, 256, 0, st>>>(s.pts, s.dz, v_in, s.cell_start, net.R, (long long)s.n_cells, s.cell_part);
+        vertex_gather_kernel<16><<<vb, 256, 0, st>>>(s.cell_part, net.R, w0, w1, g0, g1, s.flag);
+        break;
+      default:
+        cell_corner_kernel<32><<<cb, 256, 0, st>>>(s.pts, s.dz, v_in, s.cell_start, net.R, (long long)s.n_cells, s.cell_part);
+        vertex_gather_kernel<32><<<vb, 256, 0, st>>>(s.cell_part, net.R, w0, w1, g0, g1, s.flag);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  } else if (n > 0) {
     if (net.F == 8)
       grid_grad_kernel<8><<<gblocks, 256, 0, st>>>(s.pts, s.dz, v_in, s.cell_start, net.R, w0, w1, g0, g1, s.flag);
     else if (net.F == 16)
@@ -549,8 +678,8 @@ cudaError_t run_backward(FitScratch& s, const NetDev& net, PointArgs pa, float* 
   }
   const int ne = nW + nb;
   if (n_cta > 0) {
-    reduce_parts_kernel<<<(ne + 1 + 255) / 256, 256, 0, st>>>(s.part, n_cta, nW, nb, dW, db, loss,
-                                                              1.0f / (float)n, s.flag);
+    reduce_parts_kernel<<<(ne + 1 + 31) / 32, 256, 0, st>>>(s.part, n_cta, nW, nb, dW, db, loss,
+                                                             1.0f / (float)n, s.flag);
   } else {
     e = cudaMemsetAsync(dW, 0, sizeof(float) * nW, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(db, 0, sizeof(float) * nb, st);
@@ -586,11 +715,13 @@ cudaError_t fit_scratch_alloc(FitScratch& s, const NetDev& net, int max_points) 
   alloc((void**)&s.part, sizeof(float) * (size_t)s.max_cta * (s.n_entries + 1));
   alloc((void**)&s.grads, sizeof(float) * (s.n_grid + s.n_entries));
   alloc((void**)&s.flag, sizeof(unsigned int) * 4);
+  if ((size_t)max_points >= 32 * s.n_cells) alloc((void**)&s.cell_part, sizeof(float) * s.n_cells * 8 * net.F);
   return e;
 }
 
 void fit_scratch_free(FitScratch& s) {
-  void* ps[] = {s.pts, s.dz, s.key, s.key_alt, s.idx, s.idx_alt, s.hist, s.cell_start, s.part, s.grads, s.flag};
+  void* ps[] = {s.pts, s.dz, s.key, s.key_alt, s.idx, s.idx_alt, s.hist, s.cell_start, s.part, s.grads, s.flag,
+                s.cell_part};
   for (void* p : ps)
     if (p) cudaFree(p);
   memset(&s, 0, sizeof(s));

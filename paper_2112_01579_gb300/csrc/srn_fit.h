@@ -23,6 +23,7 @@ struct FitScratch {
   float* part;             // [max_cta][n_entries + 1] per-CTA weight-gradient / loss partials
   float* grads;            // [n_grid + n_entries] gradient of one step (grid | weights | biases)
   unsigned int* flag;      // non-finite flag of the current step
+  float* cell_part;        // [n_cells][8][F] per-(cell, corner) partials (small grids; may be null)
 };
 
 struct FitArgs {

@@ -29,12 +29,18 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-30))
 
 
-@pytest.mark.parametrize("shape", ["cfg1", "cfg2", "head", "time"])
+@pytest.mark.parametrize("shape", ["cfg1", "cfg2", "head", "time", "dense_cells"])
 def test_backward_matches_oracle(srn, shape):
     import torch
     S = srn
     t = 0.0
-    if shape == "cfg1":
+    n = 3001  # ragged against the 128-point CTAs and the 2048-key sort blocks
+    if shape == "dense_cells":
+        # >= 32 points per cell: the (cell, corner)-parallel latent-gradient pass
+        p = synth.random_params(R=6, F=16, m=14, layers=3, width=32, act=synth.ACT_SNAKEALT, seed=36,
+                                grid_std=0.5, n_keyframes=2, key_times=[0.0, 1.0])
+        n, t = 20011, 0.3
+    elif shape == "cfg1":
         p = H.cfg1_params(seed=30)
     elif shape == "cfg2":
         p = H.cfg2_params(seed=31, R=16)
@@ -44,7 +50,6 @@ def test_backward_matches_oracle(srn, shape):
         p = synth.random_params(R=6, F=8, m=12, layers=3, width=32, act=synth.ACT_SNAKEALT, seed=33, grid_std=0.5,
                                 n_keyframes=3, key_times=[0.0, 1.0, 4.0])
         t = 2.5
-    n = 3001  # ragged against the 128-point CTAs and the 2048-key sort blocks
     net = S.Network(p, max_fit_points=n)
     rng = np.random.default_rng(34)
     pts = rng.uniform(0, 1, (n, 3)).astype(np.float32)
