@@ -346,6 +346,112 @@ def run_e2e(net, tf, cams, desc, dev, steps):
             "d2h_bytes_per_step": int(host_img.numel() * 4)}
 
 
+def _time_frames(fn, n=3):
+    """Median device time of fn() over n calls after one warm-up (L2 flushed)."""
+    import torch
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    fn()
+    ms = []
+    for _ in range(n):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return float(np.median(ms))
+
+
+def _psnr_imgs(S, a, b):
+    import torch
+    mse = torch.zeros(1, dtype=torch.float64, device="cuda")
+    S.srn_image_mse(a.contiguous(), b.contiguous(), mse)
+    torch.cuda.synchronize()
+    return 10 * math.log10(1.0 / max(mse.item(), 1e-30))
+
+
+def shaded_workload(fit_steps=FIT_STEPS, seed=0):
+    """Config 4: 512^3 anisotropic blobs + noise; 64^3 x 16 FP16 grid, 4
+    SnakeAlt layers; 1024^2 at step 1/1024 with headlight shading from the
+    adjoint gradient (FP32 kernels), central differences (FP16 tensor
+    cores, 6 extra evaluations) and the 4-output head (FP16 tensor cores),
+    against dense DVR of the volume with one-voxel central differences."""
+    import torch
+    from paper_2112_01579_gb300 import srn, synth
+    vol = synth.aniso_blobs_volume(512, 64, seed=seed, device="cuda").contiguous()
+    tf, cams = synth.tf_preset(8), synth.orbit_cameras(N_VIEWS)
+    res = {"workload": "cfg4: 512^3 aniso blobs; 64^3x16 fp16 grid, 4x32 SnakeAlt; 1024^2, step 1/1024, Blinn-Phong"}
+    nets = {}
+    for D, gw in [(1, 0.0), (4, 1.0)]:
+        p = synth.init_params(R=64, F=16, m=14, layers=4, width=32, out_dim=D, act=synth.ACT_SNAKEALT, seed=seed)
+        net = srn.Network(p, precision=srn.SRN_PREC_FP16, max_fit_points=FIT_POINTS, adam=True)
+        loss = torch.zeros(1, device="cuda")
+        for st in range(fit_steps):
+            # head targets: central differences of the volume scaled by 1/100 (|grad V| reaches ~100 per unit)
+            srn.srn_fit_step(net.ctx, vol, FIT_POINTS, seed + 11, st, loss, grad_weight=gw, grad_scale=0.01)
+        srn.srn_sync_half(net.ctx)
+        nets[D] = net
+    out = torch.zeros((1, 1, H_IMG, W_IMG, 4), device="cuda")
+    ref = torch.zeros((1, H_IMG, W_IMG, 4), device="cuda")
+    n32 = srn.Network(nets[1].unpack(), precision=srn.SRN_PREC_FP32)
+    modes = [("none_fp16", nets[1], srn.SRN_SHADE_NONE), ("adjoint_fp32", n32, srn.SRN_SHADE_ADJOINT),
+             ("fd_fp16", nets[1], srn.SRN_SHADE_FD), ("head_fp16", nets[4], srn.SRN_SHADE_HEAD)]
+    for name, net, sh in modes:
+        desc = srn.render_desc(W_IMG, H_IMG, 1 / 1024, ET, sh, 1 / 511)
+        ms = _time_frames(lambda: srn.srn_render(net.ctx, cams[:1], tf, desc, out), n=3)
+        srn.srn_dvr_dense(vol, cams[:1], tf, srn.render_desc(W_IMG, H_IMG, 1 / 1024, ET,
+                                                             srn.SRN_SHADE_FD if sh else 0), ref)
+        res[name] = {"ms_per_frame": ms, "psnr_vs_dense_db": _psnr_imgs(srn, out[0], ref)}
+    desc = srn.render_desc(W_IMG, H_IMG, 1 / 1024, ET, srn.SRN_SHADE_FD)
+    res["dense_fd_ms_per_frame"] = _time_frames(lambda: srn.srn_dvr_dense(vol, cams[:1], tf, desc, ref), n=3)
+    res["ratio_fd_over_head"] = res["fd_fp16"]["ms_per_frame"] / res["head_fp16"]["ms_per_frame"]
+    res["ratio_adjoint_over_head"] = res["adjoint_fp32"]["ms_per_frame"] / res["head_fp16"]["ms_per_frame"]
+    for n in list(nets.values()) + [n32]:
+        n.close()
+    del vol
+    return res
+
+
+def time_workload(fit_steps=FIT_STEPS, seed=0):
+    """Config 5: 16 timesteps of 256^3 moving blobs; five 32^3 x 16 keyframe
+    grids at t = 0, 4, 8, 12, 15 with a shared 4-layer network, fitted on
+    the even timesteps and t = 15; the batch of 16 times x 4 views at 1024^2
+    rendered in one launch; PSNR per timestep against dense DVR."""
+    import torch
+    from paper_2112_01579_gb300 import srn, synth
+    vols = synth.moving_blobs_volumes(256, 16, 32, seed=seed, device="cuda")
+    keys = [0.0, 4.0, 8.0, 12.0, 15.0]
+    p = synth.init_params(R=32, F=16, m=14, layers=4, width=32, act=synth.ACT_SNAKEALT, seed=seed, n_keyframes=5,
+                          key_times=keys)
+    net = srn.Network(p, precision=srn.SRN_PREC_FP16, max_fit_points=FIT_POINTS, adam=True)
+    train_t = [0, 2, 4, 6, 8, 10, 12, 14, 15]
+    loss = torch.zeros(1, device="cuda")
+    for st in range(fit_steps):
+        t = train_t[st % len(train_t)]
+        srn.srn_fit_step(net.ctx, vols[t].contiguous(), FIT_POINTS, seed + 21, st, loss, time=float(t))
+    srn.srn_sync_half(net.ctx)
+    tf, cams = synth.tf_preset(8), synth.orbit_cameras(4)
+    times = list(range(16))
+    out = torch.zeros((16, 4, H_IMG, W_IMG, 4), device="cuda")
+    desc = srn.render_desc(W_IMG, H_IMG, STEP, ET)
+    ctr = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ms = _time_frames(lambda: srn.srn_render(net.ctx, cams, tf, desc, out, times=times), n=3)
+    ctr.zero_()
+    srn.srn_render(net.ctx, cams, tf, desc, out, times=times, samples=ctr)
+    torch.cuda.synchronize()
+    ref = torch.zeros((4, H_IMG, W_IMG, 4), device="cuda")
+    psnr = []
+    for t in times:
+        srn.srn_dvr_dense(vols[t].contiguous(), cams, tf, desc, ref)
+        psnr.append(_psnr_imgs(srn, out[t], ref))
+    net.close()
+    return {"workload": "cfg5: 16 x 256^3 moving blobs; 5 keyframe 32^3x16 fp16 grids; 16 times x 4 views @1024^2 in one launch",
+            "ms_per_batch": ms, "frames": 64, "ms_per_frame": ms / 64,
+            "samples_per_s": int(ctr.item()) / (ms / 1e3), "psnr_per_timestep_db": psnr,
+            "trained_timesteps": train_t}
+
+
 def cpu_baseline(params, vol_np, tf, cams, budget_rows=16):
     """The FP64 oracle on a bounded sample: every (H / budget_rows)-th row of
     one 1024^2 frame of the same scene."""
@@ -399,7 +505,6 @@ def run_reference(args, rank, world):
         return None
     import torch
     from paper_2112_01579_gb300 import synth
-    vol = synth.noise_volume(256, seed=0, device="cpu")
     p = synth.init_params(R=32, F=16, m=14, layers=4, width=32, out_dim=1, act=synth.ACT_SNAKEALT, seed=0)
     p = synth.to_half_exact(p)
     tf, cams = synth.tf_preset(8), synth.orbit_cameras(N_VIEWS)
@@ -463,6 +568,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fit-steps", type=int, default=FIT_STEPS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the shaded and time-varying workloads")
     ap.add_argument("--summarize-launches", metavar="CSV",
                     help="print per-kernel launches / time / share of an ncu gpu__time_duration.sum CSV and exit")
     args = ap.parse_args()
@@ -487,6 +593,9 @@ def main():
     __graft_entry__.build()
     res, net, vol, tf, cams = run_ours(args, rank, world)
     res["roofline"] = roofline(res)
+    if rank == 0 and not args.no_extras:
+        res["config"]["shaded_cfg4"] = shaded_workload(fit_steps=args.fit_steps)
+        res["config"]["time_cfg5"] = time_workload(fit_steps=args.fit_steps)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(net.unpack_half(), None, tf, cams)
     if rank == 0:
