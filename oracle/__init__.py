@@ -41,7 +41,7 @@ def build(force: bool = False) -> str:
 
 class Net(C.Structure):
     _fields_ = [("R", C.c_int), ("F", C.c_int), ("m", C.c_int), ("l", C.c_int), ("c", C.c_int),
-                ("D", C.c_int), ("act", C.c_int), ("nkey", C.c_int),
+                ("D", C.c_int), ("act", C.c_int), ("nkey", C.c_int), ("time_input", C.c_int),
                 ("key_times", C.POINTER(C.c_double)), ("grid", C.POINTER(C.c_double)),
                 ("fourier", C.POINTER(C.c_double)), ("W", C.POINTER(C.c_double)),
                 ("b", C.POINTER(C.c_double))]
@@ -128,9 +128,10 @@ class OracleNet:
         self.key_times = _d(params.get("key_times", np.zeros(max(nkey, 1)))).reshape(-1)
         c = Ws[0].shape[0] if len(Ws) > 1 else 0
         D = Ws[-1].shape[0]
-        self.dims = dict(R=R, F=F, m=m, l=len(Ws), c=c, D=D, act=int(params["act"]), nkey=nkey)
+        ti = int(params.get("time_input", 0))
+        self.dims = dict(R=R, F=F, m=m, l=len(Ws), c=c, D=D, act=int(params["act"]), nkey=nkey, time_input=ti)
         self.layer_shapes = [w.shape for w in Ws]
-        self.s = Net(R, F, m, len(Ws), c, D, int(params["act"]), nkey, _p(self.key_times), _p(self.grid),
+        self.s = Net(R, F, m, len(Ws), c, D, int(params["act"]), nkey, ti, _p(self.key_times), _p(self.grid),
                      _p(self.fourier), _p(self.W), _p(self.b))
         if lib().orc_net_check(C.byref(self.s)) != 0:
             raise ValueError("network outside the oracle's limits")

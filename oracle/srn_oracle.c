@@ -50,6 +50,7 @@ enum { ORC_SHADE_NONE = 0, ORC_SHADE_ADJOINT = 1, ORC_SHADE_FD = 2, ORC_SHADE_HE
  * grid is [nkey][R][R][R][F] with x fastest and channels innermost. */
 typedef struct {
   int R, F, m, l, c, D, act, nkey;
+  int time_input;          /* 1: the time value is one more input after z (Section 7 "direct") */
   const double* key_times; /* nkey increasing keyframe times (nkey > 1) */
   double* grid;
   const double* fourier; /* m x 3 */
@@ -171,7 +172,7 @@ void orc_trilinear_grad(const double* vol, int nx, int ny, int nz, int C, const 
 }
 
 /* ------------------------------------------------------------------------ */
-static int layer_in(const orc_net* n, int i) { return i == 0 ? 3 + 2 * n->m + n->F : n->c; }
+static int layer_in(const orc_net* n, int i) { return i == 0 ? 3 + 2 * n->m + n->F + n->time_input : n->c; }
 static int layer_out(const orc_net* n, int i) { return i == n->l - 1 ? n->D : n->c; }
 
 /* Section 7: keyframe latent grids, linearly interpolated in time between the
@@ -234,6 +235,9 @@ static void forward(const orc_net* n, const double p_in[3], double t, orc_trace*
     v0[3 + n->m + k] = cos(e);
   }
   latent(n, tr->p, t, v0 + 3 + 2 * n->m);
+  /* Section 7 "direct" time encoding: the time is an additional scalar input.
+   * Reading: the time value exactly as given to the call. */
+  if (n->time_input) v0[3 + 2 * n->m + n->F] = t;
   const double* W = n->W;
   const double* b = n->b;
   for (int i = 0; i < n->l; ++i) {
@@ -251,7 +255,8 @@ static void forward(const orc_net* n, const double p_in[3], double t, orc_trace*
 
 int orc_net_check(const orc_net* n) {
   if (n->l < 1 || n->l > ORC_MAXL) return 1;
-  if (3 + 2 * n->m + n->F > ORC_MAXW || n->c > ORC_MAXW || n->D > ORC_MAXW) return 1;
+  if (3 + 2 * n->m + n->F + 1 > ORC_MAXW || n->c > ORC_MAXW || n->D > ORC_MAXW) return 1;
+  if (n->time_input != 0 && n->time_input != 1) return 1;
   if (n->R < 2 || n->nkey < 1 || n->D < 1) return 1;
   return 0;
 }

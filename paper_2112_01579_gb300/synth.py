@@ -186,18 +186,19 @@ def nerf_fourier_matrix(m: int) -> np.ndarray:
     return F
 
 
-def layer_dims(F, m, layers, width, out_dim):
-    d = [3 + 2 * m + F] + [width] * (layers - 1) + [out_dim]
+def layer_dims(F, m, layers, width, out_dim, time_input=0):
+    d = [3 + 2 * m + F + time_input] + [width] * (layers - 1) + [out_dim]
     return list(zip(d[:-1], d[1:]))
 
 
 def init_params(R=8, F=8, m=12, layers=2, width=32, out_dim=1, act=ACT_SINE, n_keyframes=1, seed=0,
-                grid_std=0.01, key_times=None):
+                grid_std=0.01, key_times=None, time_input=0):
     """Initial parameters: Xavier-uniform weights, zero biases, latent grid
-    N(0, grid_std^2), NeRF Fourier matrix.  All float32 numpy arrays."""
+    N(0, grid_std^2), NeRF Fourier matrix.  All float32 numpy arrays.
+    time_input = 1 adds the time as one more network input."""
     rng = np.random.default_rng(seed)
     Ws, bs = [], []
-    for din, dout in layer_dims(F, m, layers, width, out_dim):
+    for din, dout in layer_dims(F, m, layers, width, out_dim, time_input):
         a = math.sqrt(6.0 / (din + dout))
         Ws.append(rng.uniform(-a, a, (dout, din)).astype(np.float32))
         bs.append(np.zeros(dout, dtype=np.float32))
@@ -205,14 +206,14 @@ def init_params(R=8, F=8, m=12, layers=2, width=32, out_dim=1, act=ACT_SINE, n_k
     if key_times is None:
         key_times = np.arange(n_keyframes, dtype=np.float32)
     return dict(grid=grid, fourier=nerf_fourier_matrix(m), weights=Ws, biases=bs, act=act,
-                key_times=np.asarray(key_times, dtype=np.float32))
+                key_times=np.asarray(key_times, dtype=np.float32), time_input=int(time_input))
 
 
 def random_params(R=8, F=8, m=12, layers=2, width=32, out_dim=1, act=ACT_SINE, n_keyframes=1, seed=0,
-                  grid_std=0.5, w_gain=1.0, bias_std=0.1, key_times=None):
+                  grid_std=0.5, w_gain=1.0, bias_std=0.1, key_times=None, time_input=0):
     """Like init_params but with a latent grid and biases large enough that
     every term of the network matters (used by parity tests)."""
-    p = init_params(R, F, m, layers, width, out_dim, act, n_keyframes, seed, grid_std, key_times)
+    p = init_params(R, F, m, layers, width, out_dim, act, n_keyframes, seed, grid_std, key_times, time_input)
     rng = np.random.default_rng(seed + 7919)
     p["weights"] = [(w * w_gain).astype(np.float32) for w in p["weights"]]
     p["biases"] = [rng.normal(0, bias_std, b.shape).astype(np.float32) for b in p["biases"]]

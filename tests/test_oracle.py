@@ -595,3 +595,49 @@ def test_psnr_and_ssim_closed_forms():
     ca, cb = np.full((16, 16, 4), 0.3), np.full((16, 16, 4), 0.6)
     C1 = 0.01 ** 2
     assert abs(oracle.ssim(ca, cb) - (2 * 0.18 + C1) / (0.09 + 0.36 + C1)) < 1e-12
+
+
+def test_direct_time_input_is_the_last_input():
+    """Section 7 'direct' encoding: the time is one more scalar input after
+    the latent vector; a linear net selecting it returns the time."""
+    F, m = 2, 3
+    d0 = 3 + 2 * m + F + 1
+    W = np.zeros((1, d0))
+    W[0, d0 - 1] = 1.0
+    p = dict(grid=np.zeros((2, 3, 3, 3, F)), fourier=_nerf_exact(m), weights=[W], biases=[np.array([0.5])],
+             act=synth.ACT_SINE, key_times=np.array([0.0, 2.0]), time_input=1)
+    net = _net(p)
+    for t in [0.0, 0.7, 1.9, 3.0]:
+        out = oracle.net_forward(net, [[0.2, 0.4, 0.6]], t)[0, 0]
+        assert out == t + 0.5
+    # the time input changes nothing else: same net without it and a zero time weight agree
+    p2 = synth.random_params(R=4, F=4, m=6, layers=3, width=8, seed=90, time_input=1)
+    p2["weights"][0][:, -1] = 0.0
+    p3 = dict(p2)
+    p3["weights"] = [p2["weights"][0][:, :-1]] + p2["weights"][1:]
+    p3["time_input"] = 0
+    pts = np.random.default_rng(91).uniform(0, 1, (20, 3))
+    np.testing.assert_allclose(oracle.net_forward(_net(p2), pts, 0.8), oracle.net_forward(_net(p3), pts, 0.8),
+                               atol=1e-13)
+
+
+def test_direct_time_gradients_match_finite_differences():
+    p = synth.random_params(R=3, F=2, m=3, layers=3, width=5, seed=92, n_keyframes=2, key_times=[0.0, 1.0],
+                            time_input=1)
+    p = {k: (v.astype(np.float64) if isinstance(v, np.ndarray) else v) for k, v in p.items()}
+    p["weights"] = [w.astype(np.float64) for w in p["weights"]]
+    p["biases"] = [b.astype(np.float64) for b in p["biases"]]
+    net = _net(p)
+    pts = np.random.default_rng(93).uniform(0.02, 0.98, (5, 3))
+    dout = np.random.default_rng(94).normal(size=(5, 1))
+    dW, db, dg = oracle.net_backward(net, pts, dout, 0.35)
+    g = np.concatenate([w.ravel() for w in dW])
+    h = 1e-6
+    for i in range(net.W.size):
+        old = net.W[i]
+        net.W[i] = old + h
+        fp = float(np.sum(oracle.net_forward(net, pts, 0.35) * dout))
+        net.W[i] = old - h
+        fm = float(np.sum(oracle.net_forward(net, pts, 0.35) * dout))
+        net.W[i] = old
+        assert abs((fp - fm) / (2 * h) - g[i]) <= 1e-6 * max(1.0, abs(g[i]))
