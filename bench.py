@@ -413,17 +413,20 @@ def shaded_workload(fit_steps=FIT_STEPS, seed=0):
     return res
 
 
-def time_workload(fit_steps=FIT_STEPS, seed=0):
+def time_workload(fit_steps=FIT_STEPS, seed=0, time_input=0, vols=None):
     """Config 5: 16 timesteps of 256^3 moving blobs; five 32^3 x 16 keyframe
     grids at t = 0, 4, 8, 12, 15 with a shared 4-layer network, fitted on
     the even timesteps and t = 15; the batch of 16 times x 4 views at 1024^2
-    rendered in one launch; PSNR per timestep against dense DVR."""
+    rendered in one launch; PSNR per timestep against dense DVR.
+    time_input = 1: the "direct" encoding (time as one more input, Section 7)
+    instead of latent interpolation only."""
     import torch
     from paper_2112_01579_gb300 import srn, synth
-    vols = synth.moving_blobs_volumes(256, 16, 32, seed=seed, device="cuda")
+    if vols is None:
+        vols = synth.moving_blobs_volumes(256, 16, 32, seed=seed, device="cuda")
     keys = [0.0, 4.0, 8.0, 12.0, 15.0]
     p = synth.init_params(R=32, F=16, m=14, layers=4, width=32, act=synth.ACT_SNAKEALT, seed=seed, n_keyframes=5,
-                          key_times=keys)
+                          key_times=keys, time_input=time_input)
     net = srn.Network(p, precision=srn.SRN_PREC_FP16, max_fit_points=FIT_POINTS, adam=True)
     train_t = [0, 2, 4, 6, 8, 10, 12, 14, 15]
     loss = torch.zeros(1, device="cuda")
@@ -595,7 +598,13 @@ def main():
     res["roofline"] = roofline(res)
     if rank == 0 and not args.no_extras:
         res["config"]["shaded_cfg4"] = shaded_workload(fit_steps=args.fit_steps)
-        res["config"]["time_cfg5"] = time_workload(fit_steps=args.fit_steps)
+        from paper_2112_01579_gb300 import synth
+        vols = synth.moving_blobs_volumes(256, 16, 32, seed=0, device="cuda")
+        res["config"]["time_cfg5"] = time_workload(fit_steps=args.fit_steps, vols=vols)
+        direct = time_workload(fit_steps=args.fit_steps, vols=vols, time_input=1)
+        res["config"]["time_cfg5"]["direct_encoding"] = {k: direct[k] for k in
+                                                         ("ms_per_frame", "psnr_per_timestep_db")}
+        del vols
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(net.unpack_half(), None, tf, cams)
     if rank == 0:

@@ -81,6 +81,8 @@ typedef struct srn_config {
   int n_keyframes; /* >= 1 latent grids; > 1 enables time interpolation */
   float key_times[SRN_MAX_KEYFRAMES]; /* increasing keyframe times (n_keyframes > 1) */
   int max_fit_points; /* scratch of srn_fit_step / srn_backward is sized for this many points (0: none) */
+  int time_input;     /* 1: the time value is one more network input after z (Section 7 "direct"
+                         encoding; d_0 = 3 + 2m + F + 1); 0: latent-only time interpolation */
 } srn_config;
 
 /*

@@ -60,7 +60,9 @@ srn_status check_config(const srn_config* c) {
     if (!(c->key_times[k] > c->key_times[k - 1])) return fail(SRN_ERR_INVALID_ARG, "key_times must increase");
   if (c->max_fit_points < 0) return fail(SRN_ERR_INVALID_ARG, "max_fit_points must be >= 0");
   if (!render_fp32_supported(c->width)) return fail(SRN_ERR_UNSUPPORTED, "width %d is not implemented", c->width);
-  if (3 + 2 * c->n_fourier + c->feat > 256) return fail(SRN_ERR_UNSUPPORTED, "network input wider than 256");
+  if (c->time_input != 0 && c->time_input != 1) return fail(SRN_ERR_INVALID_ARG, "time_input must be 0 or 1");
+  if (3 + 2 * c->n_fourier + c->feat + c->time_input > 256)
+    return fail(SRN_ERR_UNSUPPORTED, "network input wider than 256");
   if ((size_t)c->grid_res * c->grid_res * c->grid_res * c->feat * c->n_keyframes > (size_t)1 << 31)
     return fail(SRN_ERR_UNSUPPORTED, "latent grid larger than 2^31 entries");
   return SRN_OK;
@@ -87,7 +89,7 @@ NetDev make_net(const srn_ctx* ctx) {
   n.W_h = reinterpret_cast<const __half*>(ctx->prm.weights_h);
   n.b = ctx->prm.biases;
   n.R = c.grid_res; n.F = c.feat; n.m = c.n_fourier; n.l = c.layers; n.c = c.width; n.D = c.out_dim;
-  n.act = c.activation; n.nkey = c.n_keyframes;
+  n.act = c.activation; n.nkey = c.n_keyframes; n.ti = c.time_input;
   for (int k = 0; k < SRN_MAX_KEYFRAMES; ++k) n.key_times[k] = k < c.n_keyframes ? c.key_times[k] : 0.0f;
   return n;
 }
@@ -366,21 +368,22 @@ srn_status srn_image_mse(const float* a_dev, const float* b_dev, long long n_pix
 namespace {
 
 const char kCkptMagic[8] = {'S', 'R', 'N', 'C', 'K', 'P', 'T', '1'};
-constexpr uint32_t kCkptVersion = 1;
+constexpr uint32_t kCkptVersion = 2;
 
 struct CkptHeader {
   char magic[8];
   uint32_t version;
-  int32_t shape[9];  // grid_res, feat, n_fourier, layers, width, out_dim, activation, n_keyframes, has_adam
+  int32_t shape[10];  // grid_res, feat, n_fourier, layers, width, out_dim, activation, n_keyframes, time_input,
+                      // has_adam
   int32_t step;
   uint64_t n_grid, n_weights, n_biases;
 };
 
-void ckpt_shape(const srn_ctx* ctx, int32_t shape[9]) {
+void ckpt_shape(const srn_ctx* ctx, int32_t shape[10]) {
   const srn_config& c = ctx->cfg;
   shape[0] = c.grid_res; shape[1] = c.feat; shape[2] = c.n_fourier; shape[3] = c.layers; shape[4] = c.width;
-  shape[5] = c.out_dim; shape[6] = c.activation; shape[7] = c.n_keyframes;
-  shape[8] = (ctx->prm.adam_m && ctx->prm.adam_v) ? 1 : 0;
+  shape[5] = c.out_dim; shape[6] = c.activation; shape[7] = c.n_keyframes; shape[8] = c.time_input;
+  shape[9] = (ctx->prm.adam_m && ctx->prm.adam_v) ? 1 : 0;
 }
 
 }  // namespace
@@ -400,7 +403,7 @@ srn_status srn_save(srn_ctx* ctx, const char* path, int step) {
   h.n_weights = net_weight_count(n);
   h.n_biases = net_bias_count(n);
   const size_t total = h.n_grid + h.n_weights + h.n_biases;
-  float* host = (float*)malloc(sizeof(float) * total * (h.shape[8] ? 3 : 1));
+  float* host = (float*)malloc(sizeof(float) * total * (h.shape[9] ? 3 : 1));
   if (!host) return fail(SRN_ERR_INTERNAL, "out of host memory");
   cudaError_t e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMemcpy(host, ctx->prm.grid, sizeof(float) * h.n_grid, cudaMemcpyDeviceToHost);
@@ -409,7 +412,7 @@ srn_status srn_save(srn_ctx* ctx, const char* path, int step) {
   if (e == cudaSuccess)
     e = cudaMemcpy(host + h.n_grid + h.n_weights, ctx->prm.biases, sizeof(float) * h.n_biases,
                    cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess && h.shape[8]) {
+  if (e == cudaSuccess && h.shape[9]) {
     e = cudaMemcpy(host + total, ctx->prm.adam_m, sizeof(float) * total, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(host + 2 * total, ctx->prm.adam_v, sizeof(float) * total, cudaMemcpyDeviceToHost);
   }
@@ -422,7 +425,7 @@ srn_status srn_save(srn_ctx* ctx, const char* path, int step) {
     free(host);
     return fail(SRN_ERR_INVALID_ARG, "cannot open %s for writing", path);
   }
-  const size_t nfl = total * (h.shape[8] ? 3 : 1);
+  const size_t nfl = total * (h.shape[9] ? 3 : 1);
   const bool ok = fwrite(&h, sizeof(h), 1, f) == 1 && fwrite(host, sizeof(float), nfl, f) == nfl;
   free(host);
   if (fclose(f) != 0 || !ok) return fail(SRN_ERR_INTERNAL, "short write to %s", path);
@@ -440,16 +443,16 @@ srn_status srn_load(srn_ctx* ctx, const char* path, int* step_out) {
     fclose(f);
     return fail(SRN_ERR_INVALID_ARG, "%s is not an srn checkpoint of version %u", path, kCkptVersion);
   }
-  int32_t shape[9];
+  int32_t shape[10];
   ckpt_shape(ctx, shape);
   const NetDev n = make_net(ctx);
-  if (memcmp(shape, h.shape, sizeof(int32_t) * 8) != 0 || h.n_grid != net_grid_count(n) ||
+  if (memcmp(shape, h.shape, sizeof(int32_t) * 9) != 0 || h.n_grid != net_grid_count(n) ||
       h.n_weights != net_weight_count(n) || h.n_biases != net_bias_count(n)) {
     fclose(f);
     return fail(SRN_ERR_INVALID_ARG, "checkpoint %s has a different network shape", path);
   }
   const size_t total = h.n_grid + h.n_weights + h.n_biases;
-  const size_t nfl = total * (h.shape[8] ? 3 : 1);
+  const size_t nfl = total * (h.shape[9] ? 3 : 1);
   float* host = (float*)malloc(sizeof(float) * nfl);
   if (!host) {
     fclose(f);
@@ -468,7 +471,7 @@ srn_status srn_load(srn_ctx* ctx, const char* path, int* step_out) {
   if (e == cudaSuccess)
     e = cudaMemcpy(ctx->prm.biases, host + h.n_grid + h.n_weights, sizeof(float) * h.n_biases,
                    cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && h.shape[8] && shape[8]) {
+  if (e == cudaSuccess && h.shape[9] && shape[9]) {
     e = cudaMemcpy(ctx->prm.adam_m, host + total, sizeof(float) * total, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(ctx->prm.adam_v, host + 2 * total, sizeof(float) * total, cudaMemcpyHostToDevice);
   }

@@ -213,6 +213,7 @@ __global__ void __launch_bounds__(kFitThreads) fit_point_kernel(const NetDev net
         v[3 + 2 * L.m + f + 2] = z.z;
         v[3 + 2 * L.m + f + 3] = z.w;
       }
+      if (L.ti) v[3 + 2 * L.m + L.F] = lat.tin;
       if (!valid)
         for (int q = 0; q < d0; ++q) v[q] = 0.f;
     }

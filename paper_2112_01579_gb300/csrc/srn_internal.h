@@ -28,6 +28,7 @@ struct NetDev {
   const __half* W_h;     // fp16 copy of W
   const float* b;        // packed biases
   int R, F, m, l, c, D, act, nkey;
+  int ti;  // 1: time is one more input after the latent vector
   float key_times[SRN_MAX_KEYFRAMES];
 };
 
@@ -76,7 +77,7 @@ cudaError_t launch_lowpass_resample(const float* vol, const int dims[3], int M, 
                                     cudaStream_t s);
 
 // Layer shapes of a network.
-inline int net_d0(const NetDev& n) { return 3 + 2 * n.m + n.F; }
+inline int net_d0(const NetDev& n) { return 3 + 2 * n.m + n.F + n.ti; }
 inline size_t net_weight_count(const NetDev& n) {
   size_t t = (size_t)n.c * net_d0(n);
   t += (size_t)(n.l - 2) * n.c * n.c;

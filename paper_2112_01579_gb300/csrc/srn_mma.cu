@@ -224,6 +224,7 @@ __device__ __forceinline__ float4 tf_eval_inv(const TFDev& tf, const float* inv,
 struct RayLat {
   int g0, g1;     // element offsets of the bracketing keyframe grids (g1 < 0: single grid)
   float w0, w1;   // time weights
+  float tin;      // time value (input of the direct time encoding)
 };
 
 // Latent vector (Section 4.2 trilinear latent grid; Section 7 time blend)
@@ -265,14 +266,15 @@ __device__ __forceinline__ void latent_h(const __half* __restrict__ G, int R, co
   }
 }
 
-// Layer-0 input row (Eq. 1-2 features, Section 4.2 latent vector) in the
-// tile's column order [sin_0, cos_0, ..., sin_{m-1}, cos_{m-1}, p, z, 1, 1,
-// 0...] over the K0 columns layer 0 reads.  Values are packed to FP16 pairs
+// Layer-0 input row (Eq. 1-2 features, Section 4.2 latent vector, Section 7
+// time input when TI) in the tile's column order [sin_0, cos_0, ...,
+// sin_{m-1}, cos_{m-1}, p, z, (t), 1, 1, 0...] over the K0 columns layer 0
+// reads.  Values are packed to FP16 pairs
 // and stored 16 bytes at a time as they are produced.
-template <int M, int F, int K0>
+template <int M, int F, int K0, int TI>
 __device__ __forceinline__ void write_input_row(uint8_t* tile, int row, float3 p, bool nerf, const float* fm,
                                                 const __half* G, int R, const RayLat& rl) {
-  constexpr int D0 = 3 + 2 * M + F;
+  constexpr int D0 = 3 + 2 * M + F + TI;
   static_assert(M >= 3, "the NeRF recurrence needs the three base rows");
   float z[F];
   latent_h<F>(G, R, rl, p, z);
@@ -319,7 +321,8 @@ __device__ __forceinline__ void write_input_row(uint8_t* tile, int row, float3 p
     const int col = 2 * M + i;
     float v = 0.0f;
     if (col < 2 * M + 3) v = col == 2 * M ? p.x : (col == 2 * M + 1 ? p.y : p.z);
-    else if (col < D0) v = z[col - 2 * M - 3];
+    else if (col < 2 * M + 3 + F) v = z[col - 2 * M - 3];
+    else if (col < D0) v = rl.tin;  // Section 7 "direct" time input
     else if (col == D0 || col == D0 + 1) v = 1.0f;
     tail[i] = v;
   }
@@ -328,11 +331,11 @@ __device__ __forceinline__ void write_input_row(uint8_t* tile, int row, float3 p
 }
 
 // ---------------------------------------------------------------- kernel
-template <int M, int F, int ACT, int SH>
+template <int M, int F, int ACT, int SH, int TI>
 __global__ void __launch_bounds__(kThreads, 1)
     render_mma_kernel(const NetDev net, const BatchDev b, const PointsDev pd, const SmemPlan plan,
                       unsigned long long* __restrict__ ray_counter, unsigned int* __restrict__ status) {
-  constexpr int D0 = 3 + 2 * M + F;
+  constexpr int D0 = 3 + 2 * M + F + TI;
   constexpr int K0 = ((D0 + 2 + 15) / 16) * 16;  // inputs + two bias columns
   static_assert(D0 >= 32 && K0 <= 64, "layer-0 input must fit one 128-byte row and cover the hidden width");
   constexpr int NP = SH == SRN_SHADE_FD ? 7 : 1;  // network passes per sample
@@ -486,7 +489,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   float3 o = make_float3(0.f, 0.f, 0.f), d = o;
   float t0 = 0.f, t1 = 0.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, Acc = 0.f;
   int k = 0, pass = 0;
-  RayLat rl{0, -1, 1.0f, 0.0f};
+  RayLat rl{0, -1, 1.0f, 0.0f, 0.0f};
   float rho_c = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
   float3 ppos = make_float3(0.f, 0.f, 0.f);
   unsigned int ns = 0;
@@ -499,6 +502,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     rl.g1 = net.nkey > 1 ? (int)((k0 + 1) * gsz) : -1;
     rl.w0 = net.nkey > 1 ? 1.0f - f : 1.0f;
     rl.w1 = f;
+    rl.tin = pd.time;
   }
 
   while (true) {
@@ -537,6 +541,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               rl.g1 = net.nkey > 1 ? (int)((k0 + 1) * gsz) : -1;
               rl.w0 = net.nkey > 1 ? 1.0f - f : 1.0f;
               rl.w1 = f;
+              rl.tin = b.times[ti];
               C0 = C1 = C2 = Acc = 0.f;
               k = 0;
               pass = 0;
@@ -552,7 +557,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---- layer-0 input of this pass
     float len = 0.f;
     if (POINTS && active && !failed) {
-      write_input_row<M, F, K0>(A, row, ppos, nerf, fm, net.grid_h, net.R, rl);
+      write_input_row<M, F, K0, TI>(A, row, ppos, nerf, fm, net.grid_h, net.R, rl);
     } else if (active && !failed) {
       const float ta = fmaf((float)k, b.step, t0);
       const float tb = fminf(fmaf((float)(k + 1), b.step, t0), t1);
@@ -567,7 +572,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (ax == 1) q.y = clamp01f(q.y + h);
         if (ax == 2) q.z = clamp01f(q.z + h);
       }
-      write_input_row<M, F, K0>(A, row, q, nerf, fm, net.grid_h, net.R, rl);
+      write_input_row<M, F, K0, TI>(A, row, q, nerf, fm, net.grid_h, net.R, rl);
     }
     fence_proxy_async();
     tc_fence_before();
@@ -700,11 +705,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (tid < 32) tmem_dealloc(tmem, kTmemCols);
 }
 
-template <int M, int F, int ACT, int SH>
+template <int M, int F, int ACT, int SH, int TI = 0>
 cudaError_t launch_t(const NetDev& net, const BatchDev& b, const PointsDev& pd, unsigned long long* ctr,
                      unsigned int* status, cudaStream_t s) {
   SmemPlan plan = make_plan(net);
-  auto k = render_mma_kernel<M, F, ACT, SH>;
+  auto k = render_mma_kernel<M, F, ACT, SH, TI>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
@@ -731,6 +736,7 @@ cudaError_t dispatch_shading(const NetDev& net, const BatchDev& b, unsigned long
 
 bool render_mma_supported(const NetDev& n, int shading) {
   if (n.c != 32 || n.l < 2 || n.l > 8) return false;
+  if (n.ti && !(n.m == 14 && n.F == 16 && n.act == SRN_ACT_SNAKEALT && shading == SRN_SHADE_NONE)) return false;
   if (shading == SRN_SHADE_ADJOINT) return false;
   if (shading == SRN_SHADE_HEAD && n.D != 4) return false;
   const bool shape_a = n.m == 14 && n.F == 16;
@@ -742,6 +748,7 @@ bool render_mma_supported(const NetDev& n, int shading) {
 
 cudaError_t launch_render_mma(const NetDev& n, const BatchDev& b, unsigned long long* ctr, unsigned int* status,
                               cudaStream_t s) {
+  if (n.ti) return launch_t<14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 1>(n, b, PointsDev{}, ctr, status, s);
   if (n.m == 14 && n.F == 16) {
     return n.act == SRN_ACT_SNAKEALT ? dispatch_shading<14, 16, SRN_ACT_SNAKEALT>(n, b, ctr, status, s)
                                      : dispatch_shading<14, 16, SRN_ACT_SINE>(n, b, ctr, status, s);
@@ -764,6 +771,7 @@ cudaError_t launch_eval_mma(const NetDev& n, const float* pts, long long count, 
   memset(&b, 0, sizeof(b));
   b.tf.n = 2;
   PointsDev pd{pts, out, count, time};
+  if (n.ti) return launch_t<14, 16, SRN_ACT_SNAKEALT, kPoints, 1>(n, b, pd, ctr, status, s);
   if (n.m == 14 && n.F == 16)
     return n.act == SRN_ACT_SNAKEALT ? launch_t<14, 16, SRN_ACT_SNAKEALT, kPoints>(n, b, pd, ctr, status, s)
                                      : launch_t<14, 16, SRN_ACT_SINE, kPoints>(n, b, pd, ctr, status, s);

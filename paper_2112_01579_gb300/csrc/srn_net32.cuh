@@ -13,7 +13,7 @@ constexpr int kMaxL = 8;  // deepest network the FP32 kernels stash for the adjo
 
 // Shared-memory image of the network, offsets in floats (multiples of 4).
 struct Layout {
-  int d0, l, D, m, F;
+  int d0, l, D, m, F, ti;
   int oF, oW0T, ob0, oHid, hidStride, oWl, obl, total;
   int rowmajor;
 };
@@ -21,7 +21,7 @@ struct Layout {
 inline Layout make_layout(const NetDev& n, bool rowmajor) {
   Layout L;
   const int C = n.c;
-  L.d0 = net_d0(n); L.l = n.l; L.D = n.D; L.m = n.m; L.F = n.F;
+  L.d0 = net_d0(n); L.l = n.l; L.D = n.D; L.m = n.m; L.F = n.F; L.ti = n.ti;
   L.rowmajor = rowmajor ? 1 : 0;
   int o = 0;
   L.oF = o; o += ((3 * n.m + 3) / 4) * 4;
@@ -111,6 +111,7 @@ struct Latent {
   const float* g0;
   const float* g1;
   float tw0, tw1;
+  float tin;  // time value (the extra input of the direct time encoding)
   int R, F;
 };
 
@@ -124,6 +125,7 @@ __device__ __forceinline__ Latent make_latent(const NetDev& n, float t) {
   L.g1 = n.nkey > 1 ? L.g0 + gsz : nullptr;
   L.tw0 = n.nkey > 1 ? 1.0f - f : 1.0f;
   L.tw1 = f;
+  L.tin = t;
   L.R = n.R;
   L.F = n.F;
   return L;
@@ -220,6 +222,7 @@ __device__ __forceinline__ void forward(const float* sm, const Layout& L, int ac
     axpy<C>(h, r + 2 * C, z.z);
     axpy<C>(h, r + 3 * C, z.w);
   }
+  if (L.ti) axpy<C>(h, W0T + (3 + 2 * L.m + L.F) * C, lat.tin);  // Section 7 "direct" time input
   for (int i = 1; i < L.l - 1; ++i) {
     const float* base = sm + L.oHid + (i - 1) * L.hidStride;
     float a[C];

@@ -39,7 +39,7 @@ class srn_config(C.Structure):
     _fields_ = [("grid_res", C.c_int), ("feat", C.c_int), ("n_fourier", C.c_int), ("layers", C.c_int),
                 ("width", C.c_int), ("out_dim", C.c_int), ("activation", C.c_int), ("precision", C.c_int),
                 ("n_keyframes", C.c_int), ("key_times", C.c_float * SRN_MAX_KEYFRAMES),
-                ("max_fit_points", C.c_int)]
+                ("max_fit_points", C.c_int), ("time_input", C.c_int)]
 
 
 class srn_params(C.Structure):
@@ -293,6 +293,7 @@ class Network:
         for k in range(self.nkey):
             cfg.key_times[k] = float(kt[k])
         cfg.max_fit_points = int(max_fit_points)
+        cfg.time_input = int(params.get("time_input", 0))
         self.cfg = cfg
         self.ctx = srn_create(cfg, self._params())
         srn_sync_half(self.ctx)
@@ -318,7 +319,8 @@ class Network:
             ob += s[0]
         return dict(grid=self.grid.cpu().numpy().reshape(self.nkey, self.R, self.R, self.R, self.F),
                     fourier=self.fourier.cpu().numpy().reshape(-1, 3), weights=Ws, biases=bs,
-                    act=self.cfg.activation, key_times=np.array(self.cfg.key_times[:self.nkey], np.float32))
+                    act=self.cfg.activation, key_times=np.array(self.cfg.key_times[:self.nkey], np.float32),
+                    time_input=int(self.cfg.time_input))
 
     def unpack_half(self):
         """The FP16 copies widened to float32 (what the FP16 path computes with)."""

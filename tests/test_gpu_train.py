@@ -71,7 +71,7 @@ def test_torch_optimizer_trains_the_module(mods, precision):
         opt.zero_grad()
         loss.backward()
         opt.step()
-        losses.append(float(loss))
+        losses.append(float(loss.detach()))
     assert np.mean(losses[-10:]) < 0.5 * np.mean(losses[:10])
 
 
