@@ -295,6 +295,17 @@ def run_ours(args, rank, world):
         lp_psnrs.append(10 * math.log10(1.0 / max(mse.item(), 1e-30)))
     pts = vertex_points(vol.shape[0])
     fvsrn_dpsnr = density_psnr_network(net, vol, pts)
+    # the paper's 8-bit latent grid (Section 4.2) on the same fitted network
+    n8 = srn.Network(net.unpack(), precision=srn.SRN_PREC_FP16, grid_u8=True)
+    c8 = torch.zeros(1, dtype=torch.int64, device=dev)
+    ms8 = _time_frames(lambda: srn.srn_render(n8.ctx, cams[:1], tf, desc, out, samples=c8), n=5)
+    c8.zero_()
+    srn.srn_render(n8.ctx, cams[:1], tf, desc, out, samples=c8)
+    srn.srn_dvr_dense(vol, cams[:1], tf, desc, dense)
+    u8 = {"ms_per_frame": ms8, "samples_per_s": int(c8.item()) / (ms8 / 1e3),
+          "psnr_vs_dense_db": _psnr_imgs(srn, out[0], dense), "density_psnr_db": density_psnr_network(n8, vol, pts),
+          "grid_bytes": n8.grid_q.numel()}
+    n8.close()
     cfg3 = fit_cfg3(vol, pts, steps=args.fit_steps) if fit_info.get("steps") else None
     del pts
 
@@ -312,7 +323,7 @@ def run_ours(args, rank, world):
                    "fvsrn_ms_per_frame": ms_frame, "dense_dvr_ms_per_frame": float(np.median(d_ms)),
                    "psnr_fvsrn_vs_dense_db": float(np.mean(psnrs)),
                    "psnr_lowpass_grid_vs_dense_db": float(np.mean(lp_psnrs)), "lowpass_grid": M,
-                   "density_psnr_fvsrn_db": fvsrn_dpsnr, "density_psnr_lowpass_db": lp_dpsnr,
+                   "density_psnr_fvsrn_db": fvsrn_dpsnr, "density_psnr_lowpass_db": lp_dpsnr, "u8_grid": u8,
                    "fit_render_network": fit_info,
                    "fit_steps_per_s": cfg3["steps_per_s"] if cfg3 else None, "fit_cfg3": cfg3,
                    "parallelism": f"replicas x{world} (views split across ranks)"},

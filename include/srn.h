@@ -83,6 +83,8 @@ typedef struct srn_config {
   int max_fit_points; /* scratch of srn_fit_step / srn_backward is sized for this many points (0: none) */
   int time_input;     /* 1: the time value is one more network input after z (Section 7 "direct"
                          encoding; d_0 = 3 + 2m + F + 1); 0: latent-only time interpolation */
+  int grid_u8;        /* 1: the FP16 path reads an 8-bit latent grid (Section 4.2: per-channel
+                         min/max mapped to [0,1], 8-bit codes) instead of grid_h */
 } srn_config;
 
 /*
@@ -106,6 +108,8 @@ typedef struct srn_params {
   void* weights_h;
   float* adam_m;
   float* adam_v;
+  void* grid_q;    /* uint8 codes, layout of grid (grid_u8 only) */
+  float* grid_qp;  /* float32 [F][2]: per-channel minimum and step (max - min) / 255 (grid_u8 only) */
 } srn_params;
 
 /* Pinhole camera: row 0 is the top row, rays through pixel centres. */
@@ -166,7 +170,11 @@ srn_status srn_destroy(srn_ctx* ctx);
 /* Replace the parameter pointers (same shapes). */
 srn_status srn_set_params(srn_ctx* ctx, const srn_params* params);
 
-/* Write grid_h / weights_h as the round-to-nearest FP16 of grid / weights. */
+/* Write grid_h / weights_h as the round-to-nearest FP16 of grid / weights;
+ * with grid_u8, also the 8-bit grid: per channel f over all keyframes and
+ * vertices, lo = min, step = (max - lo) / 255 (1 if max == lo), code =
+ * round((g - lo) / step) clamped to [0, 255]; the network then sees
+ * lo + step * code (Section 4.2 8-bit latent grid). */
 srn_status srn_sync_half(srn_ctx* ctx, void* stream);
 
 /*

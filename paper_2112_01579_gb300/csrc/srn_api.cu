@@ -61,6 +61,9 @@ srn_status check_config(const srn_config* c) {
   if (c->max_fit_points < 0) return fail(SRN_ERR_INVALID_ARG, "max_fit_points must be >= 0");
   if (!render_fp32_supported(c->width)) return fail(SRN_ERR_UNSUPPORTED, "width %d is not implemented", c->width);
   if (c->time_input != 0 && c->time_input != 1) return fail(SRN_ERR_INVALID_ARG, "time_input must be 0 or 1");
+  if (c->grid_u8 != 0 && c->grid_u8 != 1) return fail(SRN_ERR_INVALID_ARG, "grid_u8 must be 0 or 1");
+  if (c->grid_u8 && c->precision != SRN_PREC_FP16)
+    return fail(SRN_ERR_INVALID_ARG, "the 8-bit grid is read by the FP16 path only");
   if (3 + 2 * c->n_fourier + c->feat + c->time_input > 256)
     return fail(SRN_ERR_UNSUPPORTED, "network input wider than 256");
   if ((size_t)c->grid_res * c->grid_res * c->grid_res * c->feat * c->n_keyframes > (size_t)1 << 31)
@@ -76,6 +79,8 @@ srn_status check_params(const srn_config* c, const srn_params* p) {
     return fail(SRN_ERR_INVALID_ARG, "parameter arrays must be 16-byte aligned");
   if (c->precision == SRN_PREC_FP16 && (!p->grid_h || !p->weights_h))
     return fail(SRN_ERR_INVALID_ARG, "FP16 precision needs grid_h and weights_h");
+  if (c->grid_u8 && (!p->grid_q || !p->grid_qp || !aligned16(p->grid_q)))
+    return fail(SRN_ERR_INVALID_ARG, "the 8-bit grid needs 16-byte aligned grid_q and grid_qp");
   return SRN_OK;
 }
 
@@ -90,6 +95,9 @@ NetDev make_net(const srn_ctx* ctx) {
   n.b = ctx->prm.biases;
   n.R = c.grid_res; n.F = c.feat; n.m = c.n_fourier; n.l = c.layers; n.c = c.width; n.D = c.out_dim;
   n.act = c.activation; n.nkey = c.n_keyframes; n.ti = c.time_input;
+  n.gq = c.grid_u8;
+  n.grid_q = reinterpret_cast<const uint8_t*>(ctx->prm.grid_q);
+  n.grid_qp = ctx->prm.grid_qp;
   for (int k = 0; k < SRN_MAX_KEYFRAMES; ++k) n.key_times[k] = k < c.n_keyframes ? c.key_times[k] : 0.0f;
   return n;
 }
@@ -217,6 +225,8 @@ srn_status srn_sync_half(srn_ctx* ctx, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = launch_to_half(n.grid, (__half*)ctx->prm.grid_h, net_grid_count(n), s);
   if (e == cudaSuccess) e = launch_to_half(n.W, (__half*)ctx->prm.weights_h, net_weight_count(n), s);
+  if (e == cudaSuccess && ctx->cfg.grid_u8)
+    e = launch_quantize_grid(n.grid, net_grid_count(n) / n.F, n.F, (uint8_t*)ctx->prm.grid_q, ctx->prm.grid_qp, s);
   return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_sync_half");
 }
 
@@ -337,7 +347,11 @@ srn_status srn_fit_step(srn_ctx* ctx, const float* volume_dev, const int dims[3]
   a.grid = ctx->prm.grid;
   a.weights = ctx->prm.weights;
   a.biases = ctx->prm.biases;
-  cudaError_t e = launch_fit_step(ctx->fit, make_net(ctx), a, (cudaStream_t)stream);
+  const NetDev net = make_net(ctx);
+  cudaError_t e = launch_fit_step(ctx->fit, net, a, (cudaStream_t)stream);
+  if (e == cudaSuccess && ctx->cfg.grid_u8)
+    e = launch_quantize_grid(net.grid, net_grid_count(net) / net.F, net.F, (uint8_t*)ctx->prm.grid_q,
+                             ctx->prm.grid_qp, (cudaStream_t)stream);
   return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_fit_step");
 }
 

@@ -29,6 +29,9 @@ struct NetDev {
   const float* b;        // packed biases
   int R, F, m, l, c, D, act, nkey;
   int ti;  // 1: time is one more input after the latent vector
+  int gq;  // 1: the FP16 path reads the 8-bit grid
+  const uint8_t* grid_q;  // 8-bit codes
+  const float* grid_qp;   // [F][2] per-channel lo, step
   float key_times[SRN_MAX_KEYFRAMES];
 };
 
@@ -69,6 +72,7 @@ cudaError_t launch_eval_mma(const NetDev& net, const float* pts, long long n, fl
 
 // Conversions and small utilities.
 cudaError_t launch_to_half(const float* src, __half* dst, size_t n, cudaStream_t s);
+cudaError_t launch_quantize_grid(const float* grid, size_t n_vert, int F, uint8_t* q, float* qp, cudaStream_t s);
 cudaError_t launch_image_mse(const float* a, const float* b, long long n, double* out, cudaStream_t s);
 cudaError_t launch_density_mse(const float* a, const float* b, long long n, double* out, cudaStream_t s);
 cudaError_t launch_resample(const float* src, const int sdims[3], float* dst, const int ddims[3], cudaStream_t s);

@@ -184,7 +184,7 @@ __device__ __forceinline__ float act_fold(float acc) {
 
 // ---------------------------------------------------------------- layout
 struct SmemPlan {
-  int oA, oOne, oB, oWl, oTF, oTFinv, oFm, oMbar, oMisc, total;
+  int oA, oOne, oB, oWl, oTF, oTFinv, oFm, oQp, oMbar, oMisc, total;
 };
 
 SmemPlan make_plan(const NetDev& n) {
@@ -199,6 +199,7 @@ SmemPlan make_plan(const NetDev& n) {
   o = (o + 15) & ~15;
   s.oTFinv = o; o += SRN_MAX_TF_POINTS * 4;
   s.oFm = o; o += ((3 * n.m + 3) & ~3) * 4 + 16;
+  s.oQp = o; o += 2 * 32 * 4;
   o = (o + 7) & ~7;
   s.oMbar = o; o += 8 * kWG;
   s.oMisc = o; o += 16 * 4;
@@ -266,18 +267,70 @@ __device__ __forceinline__ void latent_h(const __half* __restrict__ G, int R, co
   }
 }
 
+// Latent vector from the 8-bit grid (Section 4.2: per-channel codes, value
+// lo + step * code).  F = 16 codes of a vertex are one 16-byte load; each
+// byte is spliced into the FP16 value 1024 + code (exact), widened and
+// accumulated in FP32 as sum_c w_c (1024 + code_c); the offset 1024 * sum w
+// is removed and lo, step applied once per channel.
+template <int F>
+__device__ __forceinline__ void latent_q(const uint8_t* __restrict__ Q, const float* qp, int R, const RayLat& rl,
+                                         float3 p, float (&z)[F]) {
+  static_assert(F == 16, "one 16-byte load per vertex");
+  int ix, iy, iz;
+  float fx, fy, fz;
+  cell_coord(p.x, R, ix, fx);
+  cell_coord(p.y, R, iy, fy);
+  cell_coord(p.z, R, iz, fz);
+  const int sx = F, sy = R * F, sz = R * R * F;
+  const int base = iz * sz + iy * sy + ix * sx;
+#pragma unroll
+  for (int f = 0; f < F; ++f) z[f] = 0.0f;
+  float wsum = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+    const float w = (dx ? fx : 1.0f - fx) * (dy ? fy : 1.0f - fy) * (dz ? fz : 1.0f - fz);
+    const int off = base + dx * sx + dy * sy + dz * sz;
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+      const int g = kk ? rl.g1 : rl.g0;
+      if (kk && g < 0) break;
+      const float ww = w * (kk ? rl.w1 : rl.w0);
+      wsum += ww;
+      const uint4 q = __ldg(reinterpret_cast<const uint4*>(Q + g + off));
+      const uint32_t words[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        uint32_t lo2 = __byte_perm(words[e], 0x64646464u, 0x4140u);
+        uint32_t hi2 = __byte_perm(words[e], 0x64646464u, 0x4342u);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&lo2));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hi2));
+        z[4 * e] = fmaf(ww, a.x, z[4 * e]);
+        z[4 * e + 1] = fmaf(ww, a.y, z[4 * e + 1]);
+        z[4 * e + 2] = fmaf(ww, b.x, z[4 * e + 2]);
+        z[4 * e + 3] = fmaf(ww, b.y, z[4 * e + 3]);
+      }
+    }
+  }
+  const float off1024 = 1024.0f * wsum;
+#pragma unroll
+  for (int f = 0; f < F; ++f) z[f] = fmaf(qp[2 * f + 1], z[f] - off1024, qp[2 * f]);
+}
+
 // Layer-0 input row (Eq. 1-2 features, Section 4.2 latent vector, Section 7
 // time input when TI) in the tile's column order [sin_0, cos_0, ...,
 // sin_{m-1}, cos_{m-1}, p, z, (t), 1, 1, 0...] over the K0 columns layer 0
 // reads.  Values are packed to FP16 pairs
 // and stored 16 bytes at a time as they are produced.
-template <int M, int F, int K0, int TI>
+template <int M, int F, int K0, int TI, int GQ>
 __device__ __forceinline__ void write_input_row(uint8_t* tile, int row, float3 p, bool nerf, const float* fm,
-                                                const __half* G, int R, const RayLat& rl) {
+                                                const __half* G, const uint8_t* Q, const float* qp, int R,
+                                                const RayLat& rl) {
   constexpr int D0 = 3 + 2 * M + F + TI;
   static_assert(M >= 3, "the NeRF recurrence needs the three base rows");
   float z[F];
-  latent_h<F>(G, R, rl, p, z);
+  if constexpr (GQ != 0) latent_q<F>(Q, qp, R, rl, p, z);
+  else latent_h<F>(G, R, rl, p, z);
   uint32_t w[4];
   int nw = 0, chunk = 0;
   auto emit = [&](float a, float b) {
@@ -331,7 +384,7 @@ __device__ __forceinline__ void write_input_row(uint8_t* tile, int row, float3 p
 }
 
 // ---------------------------------------------------------------- kernel
-template <int M, int F, int ACT, int SH, int TI>
+template <int M, int F, int ACT, int SH, int TI, int GQ>
 __global__ void __launch_bounds__(kThreads, 1)
     render_mma_kernel(const NetDev net, const BatchDev b, const PointsDev pd, const SmemPlan plan,
                       unsigned long long* __restrict__ ray_counter, unsigned int* __restrict__ status) {
@@ -350,6 +403,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   TFDev& tf = *reinterpret_cast<TFDev*>(sm + plan.oTF);
   float* tfinv = reinterpret_cast<float*>(sm + plan.oTFinv);
   float* fm = reinterpret_cast<float*>(sm + plan.oFm);
+  float* qp = reinterpret_cast<float*>(sm + plan.oQp);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + plan.oMbar);
   volatile int* misc = reinterpret_cast<volatile int*>(sm + plan.oMisc);  // [0] tmem base, [1] nerf, [4+wg] fail
 
@@ -428,6 +482,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       wl[D * 32 + tid] = bias;
     }
     for (int i = tid; i < 3 * M; i += kThreads) fm[i] = net.fourier[i];
+    if (GQ)
+      for (int i = tid; i < 2 * F; i += kThreads) qp[i] = net.grid_qp[i];
   }
   load_tf(tf, b.tf);
   // the thread's A row starts at zero; the constant tile has ones in columns
@@ -557,7 +613,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---- layer-0 input of this pass
     float len = 0.f;
     if (POINTS && active && !failed) {
-      write_input_row<M, F, K0, TI>(A, row, ppos, nerf, fm, net.grid_h, net.R, rl);
+      write_input_row<M, F, K0, TI, GQ>(A, row, ppos, nerf, fm, net.grid_h, net.grid_q, qp, net.R, rl);
     } else if (active && !failed) {
       const float ta = fmaf((float)k, b.step, t0);
       const float tb = fminf(fmaf((float)(k + 1), b.step, t0), t1);
@@ -572,7 +628,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (ax == 1) q.y = clamp01f(q.y + h);
         if (ax == 2) q.z = clamp01f(q.z + h);
       }
-      write_input_row<M, F, K0, TI>(A, row, q, nerf, fm, net.grid_h, net.R, rl);
+      write_input_row<M, F, K0, TI, GQ>(A, row, q, nerf, fm, net.grid_h, net.grid_q, qp, net.R, rl);
     }
     fence_proxy_async();
     tc_fence_before();
@@ -705,11 +761,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (tid < 32) tmem_dealloc(tmem, kTmemCols);
 }
 
-template <int M, int F, int ACT, int SH, int TI = 0>
+template <int M, int F, int ACT, int SH, int TI = 0, int GQ = 0>
 cudaError_t launch_t(const NetDev& net, const BatchDev& b, const PointsDev& pd, unsigned long long* ctr,
                      unsigned int* status, cudaStream_t s) {
   SmemPlan plan = make_plan(net);
-  auto k = render_mma_kernel<M, F, ACT, SH, TI>;
+  auto k = render_mma_kernel<M, F, ACT, SH, TI, GQ>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
@@ -737,6 +793,8 @@ cudaError_t dispatch_shading(const NetDev& net, const BatchDev& b, unsigned long
 bool render_mma_supported(const NetDev& n, int shading) {
   if (n.c != 32 || n.l < 2 || n.l > 8) return false;
   if (n.ti && !(n.m == 14 && n.F == 16 && n.act == SRN_ACT_SNAKEALT && shading == SRN_SHADE_NONE)) return false;
+  if (n.gq && !(n.m == 14 && n.F == 16 && n.act == SRN_ACT_SNAKEALT && shading == SRN_SHADE_NONE && !n.ti))
+    return false;
   if (shading == SRN_SHADE_ADJOINT) return false;
   if (shading == SRN_SHADE_HEAD && n.D != 4) return false;
   const bool shape_a = n.m == 14 && n.F == 16;
@@ -749,6 +807,7 @@ bool render_mma_supported(const NetDev& n, int shading) {
 cudaError_t launch_render_mma(const NetDev& n, const BatchDev& b, unsigned long long* ctr, unsigned int* status,
                               cudaStream_t s) {
   if (n.ti) return launch_t<14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 1>(n, b, PointsDev{}, ctr, status, s);
+  if (n.gq) return launch_t<14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 0, 1>(n, b, PointsDev{}, ctr, status, s);
   if (n.m == 14 && n.F == 16) {
     return n.act == SRN_ACT_SNAKEALT ? dispatch_shading<14, 16, SRN_ACT_SNAKEALT>(n, b, ctr, status, s)
                                      : dispatch_shading<14, 16, SRN_ACT_SINE>(n, b, ctr, status, s);
@@ -772,6 +831,7 @@ cudaError_t launch_eval_mma(const NetDev& n, const float* pts, long long count, 
   b.tf.n = 2;
   PointsDev pd{pts, out, count, time};
   if (n.ti) return launch_t<14, 16, SRN_ACT_SNAKEALT, kPoints, 1>(n, b, pd, ctr, status, s);
+  if (n.gq) return launch_t<14, 16, SRN_ACT_SNAKEALT, kPoints, 0, 1>(n, b, pd, ctr, status, s);
   if (n.m == 14 && n.F == 16)
     return n.act == SRN_ACT_SNAKEALT ? launch_t<14, 16, SRN_ACT_SNAKEALT, kPoints>(n, b, pd, ctr, status, s)
                                      : launch_t<14, 16, SRN_ACT_SINE, kPoints>(n, b, pd, ctr, status, s);

@@ -91,6 +91,45 @@ __global__ void resample_kernel(VolDev src, float* __restrict__ dst, int mx, int
   }
 }
 
+// Per-channel min / max of the latent grid (one block per channel, fixed
+// reduction tree) and the 8-bit codes of Section 4.2.
+constexpr int kQThreads = 256;
+__global__ void __launch_bounds__(kQThreads) channel_range_kernel(const float* __restrict__ g, size_t n_vert, int F,
+                                                                  float* __restrict__ qp) {
+  __shared__ float lo_s[kQThreads], hi_s[kQThreads];
+  const int f = blockIdx.x;
+  float lo = INFINITY, hi = -INFINITY;
+  for (size_t v = threadIdx.x; v < n_vert; v += kQThreads) {
+    const float x = g[v * F + f];
+    lo = fminf(lo, x);
+    hi = fmaxf(hi, x);
+  }
+  lo_s[threadIdx.x] = lo;
+  hi_s[threadIdx.x] = hi;
+  __syncthreads();
+  for (int w = kQThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      lo_s[threadIdx.x] = fminf(lo_s[threadIdx.x], lo_s[threadIdx.x + w]);
+      hi_s[threadIdx.x] = fmaxf(hi_s[threadIdx.x], hi_s[threadIdx.x + w]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const float step = hi_s[0] > lo_s[0] ? (hi_s[0] - lo_s[0]) / 255.0f : 1.0f;
+    qp[2 * f] = lo_s[0];
+    qp[2 * f + 1] = step;
+  }
+}
+
+__global__ void quantize_kernel(const float* __restrict__ g, size_t n, int F, const float* __restrict__ qp,
+                                uint8_t* __restrict__ q) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int f = (int)(i % F);
+    const float c = rintf((g[i] - qp[2 * f]) / qp[2 * f + 1]);
+    q[i] = (uint8_t)fminf(fmaxf(c, 0.0f), 255.0f);
+  }
+}
+
 unsigned int grid_for(long long n) {
   long long b = (n + 255) / 256;
   return (unsigned int)(b > 152 * 32 ? 152 * 32 : (b < 1 ? 1 : b));
@@ -147,6 +186,16 @@ cudaError_t launch_to_half(const float* src, __half* dst, size_t n, cudaStream_t
 cudaError_t launch_image_mse(const float* a, const float* b, long long n, double* out, cudaStream_t s) {
   mse_kernel<<<1, kMseThreads, 0, s>>>(reinterpret_cast<const float4*>(a), reinterpret_cast<const float4*>(b), n,
                                        out);
+  return cudaGetLastError();
+}
+
+}  // namespace srn
+
+namespace srn {
+
+cudaError_t launch_quantize_grid(const float* grid, size_t n_vert, int F, uint8_t* q, float* qp, cudaStream_t s) {
+  channel_range_kernel<<<F, kQThreads, 0, s>>>(grid, n_vert, F, qp);
+  quantize_kernel<<<grid_for((long long)(n_vert * F)), 256, 0, s>>>(grid, n_vert * F, F, qp, q);
   return cudaGetLastError();
 }
 

@@ -39,13 +39,13 @@ class srn_config(C.Structure):
     _fields_ = [("grid_res", C.c_int), ("feat", C.c_int), ("n_fourier", C.c_int), ("layers", C.c_int),
                 ("width", C.c_int), ("out_dim", C.c_int), ("activation", C.c_int), ("precision", C.c_int),
                 ("n_keyframes", C.c_int), ("key_times", C.c_float * SRN_MAX_KEYFRAMES),
-                ("max_fit_points", C.c_int), ("time_input", C.c_int)]
+                ("max_fit_points", C.c_int), ("time_input", C.c_int), ("grid_u8", C.c_int)]
 
 
 class srn_params(C.Structure):
     _fields_ = [("grid", C.c_void_p), ("fourier", C.c_void_p), ("weights", C.c_void_p), ("biases", C.c_void_p),
                 ("grid_h", C.c_void_p), ("weights_h", C.c_void_p), ("adam_m", C.c_void_p),
-                ("adam_v", C.c_void_p)]
+                ("adam_v", C.c_void_p), ("grid_q", C.c_void_p), ("grid_qp", C.c_void_p)]
 
 
 class srn_camera(C.Structure):
@@ -265,7 +265,8 @@ class Network:
     ``key_times``) into the flat layouts of ``srn_params``.
     """
 
-    def __init__(self, params: dict, precision=SRN_PREC_FP32, max_fit_points=0, device="cuda", adam=False):
+    def __init__(self, params: dict, precision=SRN_PREC_FP32, max_fit_points=0, device="cuda", adam=False,
+                 grid_u8=False):
         import torch
         g = np.asarray(params["grid"], np.float32)
         self.nkey, self.R = g.shape[0], g.shape[1]
@@ -282,6 +283,8 @@ class Network:
         self.biases = torch.tensor(np.concatenate(bs), device=dev)
         self.grid_h = torch.empty(self.grid.numel(), dtype=torch.float16, device=dev)
         self.weights_h = torch.empty(self.weights.numel(), dtype=torch.float16, device=dev)
+        self.grid_q = torch.zeros(self.grid.numel(), dtype=torch.uint8, device=dev) if grid_u8 else None
+        self.grid_qp = torch.zeros((self.F, 2), dtype=torch.float32, device=dev) if grid_u8 else None
         n_par = self.grid.numel() + self.weights.numel() + self.biases.numel()
         self.adam_m = torch.zeros(n_par, device=dev) if adam else None
         self.adam_v = torch.zeros(n_par, device=dev) if adam else None
@@ -294,6 +297,7 @@ class Network:
             cfg.key_times[k] = float(kt[k])
         cfg.max_fit_points = int(max_fit_points)
         cfg.time_input = int(params.get("time_input", 0))
+        cfg.grid_u8 = 1 if grid_u8 else 0
         self.cfg = cfg
         self.ctx = srn_create(cfg, self._params())
         srn_sync_half(self.ctx)
@@ -305,6 +309,8 @@ class Network:
         p.grid_h, p.weights_h = self.grid_h.data_ptr(), self.weights_h.data_ptr()
         if self.adam_m is not None:
             p.adam_m, p.adam_v = self.adam_m.data_ptr(), self.adam_v.data_ptr()
+        if self.grid_q is not None:
+            p.grid_q, p.grid_qp = self.grid_q.data_ptr(), self.grid_qp.data_ptr()
         return p
 
     def unpack(self):
@@ -332,6 +338,17 @@ class Network:
             Ws.append(Wh[o:o + s[0] * s[1]].reshape(s))
             o += s[0] * s[1]
         d["grid"], d["weights"] = gh, Ws
+        return d
+
+    def unpack_u8(self):
+        """Parameters as the 8-bit FP16 path sees them: the dequantized grid
+        lo + step * code (float64 -> float32 exact for these values is not
+        needed: the oracle takes float64), FP16 weights."""
+        d = self.unpack_half()
+        q = self.grid_q.cpu().numpy().astype(np.float64).reshape(-1, self.F)
+        qp = self.grid_qp.cpu().numpy().astype(np.float64)
+        g = qp[None, :, 0] + qp[None, :, 1] * q
+        d["grid"] = g.reshape(self.nkey, self.R, self.R, self.R, self.F)
         return d
 
     def close(self):

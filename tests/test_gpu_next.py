@@ -75,3 +75,72 @@ def test_direct_time_fit_step(srn):
     g = grads[on.grid.size:on.grid.size + on.W.size]
     big = np.abs(g) > 1e-2 * np.abs(g).max()
     assert np.abs(Wg - on.W)[big].max() <= 5e-3 * 5e-3 + 1e-7
+
+
+def _quantize_np(grid, F):
+    """The 8-bit rule stated in srn.h, in float32 like the device."""
+    g = np.asarray(grid, np.float32).reshape(-1, F)
+    lo = g.min(axis=0)
+    hi = g.max(axis=0)
+    step = np.where(hi > lo, (hi - lo) / np.float32(255.0), np.float32(1.0)).astype(np.float32)
+    code = np.clip(np.rint((g - lo[None]) / step[None]), 0, 255).astype(np.uint8)
+    return code.reshape(-1), lo, step
+
+
+def test_u8_grid_codes_are_exact(srn):
+    """Section 4.2 8-bit latent grid: per-channel min / max over all keyframes
+    and vertices, codes round((g - lo) / step).  Integer results: bit-exact."""
+    import torch
+    S = srn
+    p = synth.random_params(R=12, F=16, m=14, layers=3, width=32, act=synth.ACT_SNAKEALT, seed=104, n_keyframes=2,
+                            key_times=[0.0, 1.0])
+    p["grid"][..., 3] = 0.25  # a constant channel: step 1, codes 0
+    net = S.Network(synth.to_half_exact(p), precision=S.SRN_PREC_FP16, grid_u8=True)
+    torch.cuda.synchronize()
+    code, lo, step = _quantize_np(net.grid.cpu().numpy(), 16)
+    assert np.array_equal(net.grid_q.cpu().numpy(), code)
+    qp = net.grid_qp.cpu().numpy()
+    assert np.array_equal(qp[:, 0], lo) and np.array_equal(qp[:, 1], step)
+    assert qp[3, 1] == 1.0 and np.all(code.reshape(-1, 16)[:, 3] == 0)
+
+
+@pytest.mark.parametrize("kind", ["render", "eval"])
+def test_u8_grid_parity(srn, kind):
+    """The FP16 path on the 8-bit grid against the oracle evaluated on the
+    dequantized grid lo + step * code."""
+    import torch
+    S = srn
+    p = synth.to_half_exact(H.cfg2_params(seed=105))
+    net = S.Network(p, precision=S.SRN_PREC_FP16, grid_u8=True)
+    q = net.unpack_u8()
+    on = oracle.OracleNet(q)
+    if kind == "render":
+        tf = synth.tf_preset(8)
+        cams = synth.orbit_cameras(2)
+        out = torch.zeros((1, 2, 40, 48, 4), device="cuda")
+        S.srn_render(net.ctx, cams, tf, S.render_desc(48, 40, 1 / 128, 0.99), out)
+        torch.cuda.synchronize()
+        ref, mg, _ = oracle.render(on, cams, H.oracle_tf(tf), 48, 40, 1 / 128, 0.99, want_margin=True)
+        r = H.compare_images(out.cpu().numpy(), ref, mg, H.TOL_FP16_IMG, 0.99)
+        assert r["ok"], r
+    else:
+        pts = np.random.default_rng(106).uniform(0, 1, (50000, 3)).astype(np.float32)
+        o = torch.zeros((len(pts), 1), device="cuda")
+        S.srn_eval(net.ctx, torch.tensor(pts, device="cuda"), o)
+        torch.cuda.synchronize()
+        err = H.rel_density_err(o.cpu().numpy(), oracle.net_forward(on, pts))
+        assert err.max() <= H.TOL_FP16_RHO, err.max()
+
+
+def test_u8_grid_follows_the_fit(srn):
+    import torch
+    S = srn
+    vol = torch.tensor(synth.blobs_volume(48, 6, seed=107).numpy(), device="cuda")
+    p = synth.init_params(R=16, F=16, m=14, layers=4, width=32, act=synth.ACT_SNAKEALT, seed=108)
+    net = S.Network(p, precision=S.SRN_PREC_FP16, max_fit_points=1 << 14, adam=True, grid_u8=True)
+    loss = torch.zeros(1, device="cuda")
+    for s in range(5):
+        S.srn_fit_step(net.ctx, vol, 1 << 14, 3, s, loss)
+    torch.cuda.synchronize()
+    code, lo, step = _quantize_np(net.grid.cpu().numpy(), 16)
+    assert np.array_equal(net.grid_q.cpu().numpy(), code)
