@@ -466,6 +466,45 @@ def time_workload(fit_steps=FIT_STEPS, seed=0, time_input=0, vols=None):
             "trained_timesteps": train_t}
 
 
+def width_sweep(seed=0, size=512, step=1 / 256):
+    """Width / layer sweep of the network render (Section 4.1 performance
+    figure): hidden width c in {32, 48, 64} x l in {2, 4, 6} layers, 32^3 x 16
+    latent grid, m Fourier rows so the input is c + 16 wide, random
+    parameters, one size^2 view with early termination off (every ray
+    marches the whole box, so all points take the same samples).  FP16
+    tensor-core path against the FP32 CUDA-core path: ms per frame, ns per
+    sample, and the network's algorithmic FLOP rate."""
+    import torch
+    from paper_2112_01579_gb300 import srn, synth
+    tf, cams = synth.tf_preset(8), synth.orbit_cameras(1)
+    out = torch.zeros((1, 1, size, size, 4), device="cuda")
+    desc = srn.render_desc(size, size, step, 2.0)
+    ctr = torch.zeros(1, dtype=torch.int64, device="cuda")
+    rows = []
+    for c in (32, 48, 64):
+        m = synth.fourier_rows_for_width(c)
+        for l in (2, 4, 6):
+            p = synth.to_half_exact(synth.random_params(R=32, F=16, m=m, layers=l, width=c, act=synth.ACT_SNAKEALT,
+                                                        seed=seed + c + l, grid_std=0.5, bias_std=0.2))
+            d0 = 3 + 2 * m + 16
+            flops = 2 * (d0 * c + (l - 2) * c * c + c)  # multiply-adds x 2 per sample
+            row = {"width": c, "layers": l, "fourier_rows": m, "net_flops_per_sample": flops}
+            for name, prec in (("fp16_tensor", srn.SRN_PREC_FP16), ("fp32_cuda_cores", srn.SRN_PREC_FP32)):
+                net = srn.Network(p, precision=prec)
+                ms = _time_frames(lambda: srn.srn_render(net.ctx, cams, tf, desc, out), n=3)
+                ctr.zero_()
+                srn.srn_render(net.ctx, cams, tf, desc, out, samples=ctr)
+                torch.cuda.synchronize()
+                ns = int(ctr.item())
+                row[name] = {"ms_per_frame": ms, "ns_per_sample": ms * 1e6 / ns,
+                             "net_tflops": flops * ns / (ms * 1e-3) / 1e12}
+                net.close()
+            row["fp32_over_fp16"] = row["fp32_cuda_cores"]["ms_per_frame"] / row["fp16_tensor"]["ms_per_frame"]
+            rows.append(row)
+    return {"workload": f"width/layer sweep: 32^3x16 grid, SnakeAlt, {size}^2, step 1/{round(1 / step)}, no early "
+                        "termination, random parameters", "samples_per_frame": ns, "points": rows}
+
+
 def cpu_baseline(params, vol_np, tf, cams, budget_rows=16):
     """The FP64 oracle on a bounded sample: every (H / budget_rows)-th row of
     one 1024^2 frame of the same scene."""
@@ -616,6 +655,7 @@ def main():
         res["config"]["time_cfg5"]["direct_encoding"] = {k: direct[k] for k in
                                                          ("ms_per_frame", "psnr_per_timestep_db")}
         del vols
+        res["config"]["width_sweep"] = width_sweep()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(net.unpack_half(), None, tf, cams)
     if rank == 0:

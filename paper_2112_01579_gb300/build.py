@@ -53,7 +53,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), hm):
             jobs.append((s, o))
     if jobs:
-        with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
+        with cf.ThreadPoolExecutor(max_workers=min(os.cpu_count() or 8, 16, len(jobs))) as ex:
             for (s, o), err in zip(jobs, ex.map(lambda so: _compile(*so, list(extra)), jobs)):
                 if verbose and err.strip():
                     print(f"[{os.path.basename(s)}]\n{err}")

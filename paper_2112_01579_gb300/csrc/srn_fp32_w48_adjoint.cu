@@ -1,0 +1,12 @@
+// FP32 CUDA-core render with adjoint gradient shading and the density +
+// adjoint-gradient point evaluation for hidden width 48.
+#include "srn_fp32_kernel.cuh"
+
+namespace srn {
+namespace fp32 {
+
+SRN_FP32_RENDER(48, SRN_SHADE_ADJOINT)
+SRN_FP32_EVAL(48, 1)
+
+}  // namespace fp32
+}  // namespace srn

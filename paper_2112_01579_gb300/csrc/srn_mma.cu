@@ -1,824 +1,68 @@
-// FP16 tensor-core fV-SRN render for sm_103a: tcgen05.mma with TMEM
-// accumulators, persistent CTAs, one thread per ray.
-//
-// Design (GB300-first restatement of the fused TensorCore network of
-// Section 4.1):
-// * A CTA holds 4 warpgroups.  Each warpgroup owns a tile of 128 rays, one
-//   per thread; thread i of the warpgroup is row i of the MMA operand A and
-//   TMEM lane i of the accumulator, so the per-ray work (ray stepping,
-//   latent-grid trilinear fetch, Fourier features, transfer function,
-//   compositing, early termination) stays one thread per ray as in the paper,
-//   while the layers run as M=128 x N=32 tensor-core MMAs.
-// * Every sample: the thread writes its FP16 layer-0 input row into a
-//   128B-swizzled shared-memory tile; one elected thread issues tcgen05.mma
-//   (kind::f16, FP32 accumulate in TMEM); the thread reads its row back with
-//   tcgen05.ld, applies the activation in FP32 and writes it into the same
-//   tile as the next layer's A row as an FP16 hi + lo pair (a = hi + lo to
-//   ~2^-22 relative; the B tile holds [W | W]), so the hidden activations
-//   keep FP32 accuracy through the FP16 tensor cores.  Inside the tile the input columns are
-//   [sin_0, cos_0, ..., sin_{m-1}, cos_{m-1}, p, z, 1, 1]; the B tile of
-//   layer 0 is permuted to match, so the arithmetic is that of [p, sin, cos,
-//   z].  Biases ride in the MMA as an FP16 hi + lo pair against two
-//   constant-1 columns (layer 0: columns of its own row; hidden layers: one
-//   extra K=16 MMA against a constant tile), which keeps them FP32-exact.  The last layer
-//   (32 -> D) runs on the CUDA cores in FP32.
-// * SnakeAlt(x) = 0.5 x + sin^2 x = (x - cos 2x + 1) / 2 (Eq. 3).  Every MMA
-//   layer is staged to produce u = 2x (weights and bias doubled, which is
-//   exact in FP16), the epilogue hands a = u / 2 - cos u = 2 SnakeAlt(x) - 1
-//   to the next layer, and the factor 1/2 and the shift 1/2 are folded into
-//   that layer's weights and bias: the doubled next layer then simply uses W
-//   and 2b + sum_j W_j.
-// * Rays are claimed dynamically (warp-aggregated atomic on a work counter);
-//   a thread whose ray terminates (box exit or opacity >= threshold) writes
-//   its pixel and takes the next ray, so tiles stay full.
-// * Every mbarrier wait is bounded; on timeout the warpgroup stops, records
-//   SRN_ERR_TIMEOUT in the status word and the CTA frees its TMEM.
+// Dispatch of the FP16 tensor-core render / point evaluation: which network
+// shapes and shading modes have a kernel variant, and which variant runs.
+// The kernel itself is in srn_mma_kernel.cuh.
 #include <string.h>
 
-#include "srn_device.cuh"
+#include "srn_mma.h"
 
 namespace srn {
+using mma::kPoints;
+using mma::launch_t;
+using mma::PointsDev;
+
 namespace {
 
-constexpr int kWG = 6;                 // warpgroups per CTA
-constexpr int kThreads = 128 * kWG;    // 768 threads, one CTA per SM
-constexpr int kTile = 128 * 128;       // one A tile: 128 rows x 128 B (64 fp16)
-constexpr int kBTile = 32 * 128;       // one B tile: 32 rows x 128 B
-constexpr int kTmemCols = 256;         // >= 32 FP32 accumulator columns per warpgroup, power of two
-constexpr long long kWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
-constexpr int kPoints = 4;             // kernel mode: network output at given points (no ray march)
-
-// Point-evaluation arguments (mode kPoints).
-struct PointsDev {
-  const float* pts;  // [n][3]
-  float* out;        // [n][D]
-  long long n;
-  float time;
-};
-
-// ---------------------------------------------------------------- PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(a), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait on an mbarrier phase: gives up after kWaitCycles.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t a, uint32_t parity) {
-  if (mbar_try_wait(a, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_try_wait(a, parity)) {
-    if (clock64() - t0 > kWaitCycles) return false;
-  }
-  return true;
-}
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void bar_sync(int id, int n) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
-__device__ __forceinline__ bool bar_red_or(int id, int n, bool pred) {
-  uint32_t r;
-  asm volatile(
-      "{\n\t.reg .pred q, p;\n\t"
-      "setp.ne.u32 q, %1, 0;\n\t"
-      "bar.red.or.pred p, %2, %3, q;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(r)
-      : "r"((uint32_t)pred), "r"(id), "r"(n)
-      : "memory");
-  return r != 0;
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
-               : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish() {
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (FP16 inputs, FP32 accumulate).
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                        uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-               : "memory");
-}
-
-// Thread's TMEM lane, 32 consecutive FP32 columns, waited for.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
-      "tcgen05.wait::ld.sync.aligned;"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms
-// 1024 bytes apart (SBO), sm100 descriptor version 1.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1u << 16;              // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024u >> 4) << 32;    // stride byte offset
-  d |= (uint64_t)1u << 46;              // descriptor version
-  d |= (uint64_t)2u << 61;              // SWIZZLE_128B
-  return d;
-}
-
-// Instruction descriptor: kind::f16, A = B = FP16, D = FP32, both K-major,
-// N = 32, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
-
-// Byte offset of 16-byte chunk j of row r in a 128B-swizzled tile.
-__device__ __forceinline__ uint32_t sw_off(int r, int j) { return (uint32_t)(r * 128 + ((j ^ (r & 7)) << 4)); }
-
-__device__ __forceinline__ uint32_t pack_h2(float a, float b) {
-  __half2 h = __floats2half2_rn(a, b);
-  return *reinterpret_cast<uint32_t*>(&h);
-}
-
-// Activation value handed to the next layer from the accumulator value: sin(x)
-// for the sine network; for SnakeAlt the accumulator holds u = 2x and the
-// value is u / 2 - cos u = 2 SnakeAlt(x) - 1.
-template <int ACT>
-__device__ __forceinline__ float act_fold(float acc) {
-  return ACT == SRN_ACT_SNAKEALT ? fmaf(0.5f, acc, -__cosf(acc)) : __sinf(acc);
-}
-
-// ---------------------------------------------------------------- layout
-struct SmemPlan {
-  int oA, oOne, oB, oWl, oTF, oTFinv, oFm, oQp, oMbar, oMisc, total;
-};
-
-SmemPlan make_plan(const NetDev& n) {
-  SmemPlan s;
-  int o = 0;
-  s.oA = o; o += kWG * kTile;
-  s.oOne = o; o += kTile;                       // constant tile: columns 0, 1 = 1
-  s.oB = o; o += (1 + 2 * (n.l - 2)) * kBTile;  // layer 0; per hidden layer: [W | W] and bias
-  s.oWl = o; o += (n.D * 32 + 4) * 4;
-  o = (o + 15) & ~15;
-  s.oTF = o; o += (int)sizeof(TFDev);
-  o = (o + 15) & ~15;
-  s.oTFinv = o; o += SRN_MAX_TF_POINTS * 4;
-  s.oFm = o; o += ((3 * n.m + 3) & ~3) * 4 + 16;
-  s.oQp = o; o += 2 * 32 * 4;
-  o = (o + 7) & ~7;
-  s.oMbar = o; o += 8 * kWG;
-  s.oMisc = o; o += 16 * 4;
-  s.total = o + 1024;  // alignment slack
-  return s;
-}
-
-// Transfer function with precomputed reciprocal segment widths (same
-// segments and lerp as the shared tf_eval).
-__device__ __forceinline__ float4 tf_eval_inv(const TFDev& tf, const float* inv, float rho) {
-  const float x = clamp01f(rho);
-  const int n = tf.n;
-  if (x <= tf.pos[0]) return tf.rgba[0];
-  if (x >= tf.pos[n - 1]) return tf.rgba[n - 1];
-  int i = 0;
-  while (i < n - 2 && x >= tf.pos[i + 1]) ++i;
-  const float f = (x - tf.pos[i]) * inv[i];
-  const float4 a = tf.rgba[i], b = tf.rgba[i + 1];
-  return make_float4(fmaf(f, b.x - a.x, a.x), fmaf(f, b.y - a.y, a.y), fmaf(f, b.z - a.z, a.z),
-                     fmaf(f, b.w - a.w, a.w));
-}
-
-struct RayLat {
-  int g0, g1;     // element offsets of the bracketing keyframe grids (g1 < 0: single grid)
-  float w0, w1;   // time weights
-  float tin;      // time value (input of the direct time encoding)
-};
-
-// Latent vector (Section 4.2 trilinear latent grid; Section 7 time blend)
-// from the FP16 grid, accumulated in FP32.
-template <int F>
-__device__ __forceinline__ void latent_h(const __half* __restrict__ G, int R, const RayLat& rl, float3 p,
-                                         float (&z)[F]) {
-  int ix, iy, iz;
-  float fx, fy, fz;
-  cell_coord(p.x, R, ix, fx);
-  cell_coord(p.y, R, iy, fy);
-  cell_coord(p.z, R, iz, fz);
-  const int sx = F, sy = R * F, sz = R * R * F;
-  const int base = iz * sz + iy * sy + ix * sx;
-#pragma unroll
-  for (int f = 0; f < F; ++f) z[f] = 0.0f;
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
-    const float w = (dx ? fx : 1.0f - fx) * (dy ? fy : 1.0f - fy) * (dz ? fz : 1.0f - fz);
-    const int off = base + dx * sx + dy * sy + dz * sz;
-#pragma unroll
-    for (int kk = 0; kk < 2; ++kk) {
-      const int g = kk ? rl.g1 : rl.g0;
-      if (kk && g < 0) break;
-      const float ww = w * (kk ? rl.w1 : rl.w0);
-#pragma unroll
-      for (int c = 0; c < F; c += 8) {
-        uint4 q = __ldg(reinterpret_cast<const uint4*>(G + g + off + c));
-        const __half2* h = reinterpret_cast<const __half2*>(&q);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          float2 v = __half22float2(h[e]);
-          z[c + 2 * e] = fmaf(ww, v.x, z[c + 2 * e]);
-          z[c + 2 * e + 1] = fmaf(ww, v.y, z[c + 2 * e + 1]);
-        }
-      }
-    }
-  }
-}
-
-// Latent vector from the 8-bit grid (Section 4.2: per-channel codes, value
-// lo + step * code).  F = 16 codes of a vertex are one 16-byte load; each
-// byte is spliced into the FP16 value 1024 + code (exact), widened and
-// accumulated in FP32 as sum_c w_c (1024 + code_c); the offset 1024 * sum w
-// is removed and lo, step applied once per channel.
-template <int F>
-__device__ __forceinline__ void latent_q(const uint8_t* __restrict__ Q, const float* qp, int R, const RayLat& rl,
-                                         float3 p, float (&z)[F]) {
-  static_assert(F == 16, "one 16-byte load per vertex");
-  int ix, iy, iz;
-  float fx, fy, fz;
-  cell_coord(p.x, R, ix, fx);
-  cell_coord(p.y, R, iy, fy);
-  cell_coord(p.z, R, iz, fz);
-  const int sx = F, sy = R * F, sz = R * R * F;
-  const int base = iz * sz + iy * sy + ix * sx;
-#pragma unroll
-  for (int f = 0; f < F; ++f) z[f] = 0.0f;
-  float wsum = 0.0f;
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
-    const float w = (dx ? fx : 1.0f - fx) * (dy ? fy : 1.0f - fy) * (dz ? fz : 1.0f - fz);
-    const int off = base + dx * sx + dy * sy + dz * sz;
-#pragma unroll
-    for (int kk = 0; kk < 2; ++kk) {
-      const int g = kk ? rl.g1 : rl.g0;
-      if (kk && g < 0) break;
-      const float ww = w * (kk ? rl.w1 : rl.w0);
-      wsum += ww;
-      const uint4 q = __ldg(reinterpret_cast<const uint4*>(Q + g + off));
-      const uint32_t words[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        uint32_t lo2 = __byte_perm(words[e], 0x64646464u, 0x4140u);
-        uint32_t hi2 = __byte_perm(words[e], 0x64646464u, 0x4342u);
-        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&lo2));
-        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hi2));
-        z[4 * e] = fmaf(ww, a.x, z[4 * e]);
-        z[4 * e + 1] = fmaf(ww, a.y, z[4 * e + 1]);
-        z[4 * e + 2] = fmaf(ww, b.x, z[4 * e + 2]);
-        z[4 * e + 3] = fmaf(ww, b.y, z[4 * e + 3]);
-      }
-    }
-  }
-  const float off1024 = 1024.0f * wsum;
-#pragma unroll
-  for (int f = 0; f < F; ++f) z[f] = fmaf(qp[2 * f + 1], z[f] - off1024, qp[2 * f]);
-}
-
-// Layer-0 input row (Eq. 1-2 features, Section 4.2 latent vector, Section 7
-// time input when TI) in the tile's column order [sin_0, cos_0, ...,
-// sin_{m-1}, cos_{m-1}, p, z, (t), 1, 1, 0...] over the K0 columns layer 0
-// reads.  Values are packed to FP16 pairs
-// and stored 16 bytes at a time as they are produced.
-template <int M, int F, int K0, int TI, int GQ>
-__device__ __forceinline__ void write_input_row(uint8_t* tile, int row, float3 p, bool nerf, const float* fm,
-                                                const __half* G, const uint8_t* Q, const float* qp, int R,
-                                                const RayLat& rl) {
-  constexpr int D0 = 3 + 2 * M + F + TI;
-  static_assert(M >= 3, "the NeRF recurrence needs the three base rows");
-  float z[F];
-  if constexpr (GQ != 0) latent_q<F>(Q, qp, R, rl, p, z);
-  else latent_h<F>(G, R, rl, p, z);
-  uint32_t w[4];
-  int nw = 0, chunk = 0;
-  auto emit = [&](float a, float b) {
-    w[nw++] = pack_h2(a, b);
-    if (nw == 4) {
-      *reinterpret_cast<uint4*>(tile + sw_off(row, chunk)) = make_uint4(w[0], w[1], w[2], w[3]);
-      ++chunk;
-      nw = 0;
-    }
-  };
-  if (nerf) {
-    // NeRF rows are 2 pi 2^(k div 3) along axis k mod 3: one sin/cos per axis,
-    // then exact angle doubling sin 2t = 2 s c, cos 2t = (c - s)(c + s).
-    float s[3], c[3];
-    __sincosf(6.28318530717958647f * p.x, &s[0], &c[0]);
-    __sincosf(6.28318530717958647f * p.y, &s[1], &c[1]);
-    __sincosf(6.28318530717958647f * p.z, &s[2], &c[2]);
-#pragma unroll
-    for (int k = 0; k < M; ++k) {
-      const int a = k % 3;
-      if (k >= 3) {
-        const float ss = s[a], cc = c[a];
-        s[a] = 2.0f * ss * cc;
-        c[a] = (cc - ss) * (cc + ss);
-      }
-      emit(s[a], c[a]);
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < M; ++k) {
-      const float e = fm[3 * k] * p.x + fm[3 * k + 1] * p.y + fm[3 * k + 2] * p.z;
-      float sv, cv;
-      sincosf(e, &sv, &cv);
-      emit(sv, cv);
-    }
-  }
-  // remaining columns 2M .. K0-1: p, z, the two bias ones, zeros
-  float tail[K0 - 2 * M];
-#pragma unroll
-  for (int i = 0; i < K0 - 2 * M; ++i) {
-    const int col = 2 * M + i;
-    float v = 0.0f;
-    if (col < 2 * M + 3) v = col == 2 * M ? p.x : (col == 2 * M + 1 ? p.y : p.z);
-    else if (col < 2 * M + 3 + F) v = z[col - 2 * M - 3];
-    else if (col < D0) v = rl.tin;  // Section 7 "direct" time input
-    else if (col == D0 || col == D0 + 1) v = 1.0f;
-    tail[i] = v;
-  }
-#pragma unroll
-  for (int i = 0; i < K0 - 2 * M; i += 2) emit(tail[i], tail[i + 1]);
-}
-
-// ---------------------------------------------------------------- kernel
-template <int M, int F, int ACT, int SH, int TI, int GQ>
-__global__ void __launch_bounds__(kThreads, 1)
-    render_mma_kernel(const NetDev net, const BatchDev b, const PointsDev pd, const SmemPlan plan,
-                      unsigned long long* __restrict__ ray_counter, unsigned int* __restrict__ status) {
-  constexpr int D0 = 3 + 2 * M + F + TI;
-  constexpr int K0 = ((D0 + 2 + 15) / 16) * 16;  // inputs + two bias columns
-  static_assert(D0 >= 32 && K0 <= 64, "layer-0 input must fit one 128-byte row and cover the hidden width");
-  constexpr int NP = SH == SRN_SHADE_FD ? 7 : 1;  // network passes per sample
-  constexpr bool POINTS = SH == kPoints;
-  constexpr bool SNAKE = ACT == SRN_ACT_SNAKEALT;
-
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* Aall = sm + plan.oA;
-  uint8_t* Bw = sm + plan.oB;
-  float* wl = reinterpret_cast<float*>(sm + plan.oWl);
-  TFDev& tf = *reinterpret_cast<TFDev*>(sm + plan.oTF);
-  float* tfinv = reinterpret_cast<float*>(sm + plan.oTFinv);
-  float* fm = reinterpret_cast<float*>(sm + plan.oFm);
-  float* qp = reinterpret_cast<float*>(sm + plan.oQp);
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + plan.oMbar);
-  volatile int* misc = reinterpret_cast<volatile int*>(sm + plan.oMisc);  // [0] tmem base, [1] nerf, [4+wg] fail
-
-  const int tid = threadIdx.x;
-  const int wg = tid >> 7, row = tid & 127, lane = tid & 31;
-  const int L = net.l, D = net.D;
-
-  // ---- stage parameters as 32 x 64 FP16 B tiles (row o = output neuron,
-  // K-major).  Layer 0: columns in the tile's input order, FP32 bias as hi +
-  // lo at D0, D0+1.  Hidden layer h: tile 1 + 2(h-1) holds [W | W] (hi and
-  // lo halves of the activation), tile 2 + 2(h-1) the bias hi, lo in columns
-  // 0, 1 (multiplied by the constant tile).  SnakeAlt folding as described at
-  // the top of the file.  One thread stages one row of one layer.
-  for (int it = tid; it < (L - 1) * 32; it += kThreads) {
-    const int layer = it >> 5, o = it & 31;
-    const int din = layer == 0 ? D0 : 32;
-    const __half* Wsrc = net.W_h + (layer == 0 ? 0 : (size_t)32 * D0 + (size_t)(layer - 1) * 32 * 32) +
-                         (size_t)o * din;
-    float bias = net.b[layer * 32 + o];
-    float scale = 1.0f;
-    if (SNAKE) {
-      scale = layer == 0 ? 2.0f : 1.0f;
-      if (layer > 0) {
-        float rs = 0.0f;
-        for (int c = 0; c < 32; ++c) rs += __half2float(Wsrc[c]);
-        bias = 2.0f * bias + rs;
-      } else {
-        bias = 2.0f * bias;
-      }
-    }
-    const __half bh = __float2half_rn(bias);
-    const __half bl = __float2half_rn(bias - __half2float(bh));
-    uint8_t* Wt = Bw + (layer == 0 ? 0 : 1 + 2 * (layer - 1)) * kBTile;
-    for (int j = 0; j < 8; ++j) {
-      uint32_t w[4], wb[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        __half h2[2], hb[2];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int col = 8 * j + 2 * e + q;
-          __half v = __float2half_rn(0.0f);
-          if (layer == 0) {
-            int src = -1;
-            if (col < 2 * M) src = (col & 1) ? 3 + M + (col >> 1) : 3 + (col >> 1);
-            else if (col < 2 * M + 3) src = col - 2 * M;
-            else if (col < D0) src = col;
-            if (src >= 0) v = __float2half_rn(scale * __half2float(Wsrc[src]));
-            if (col == D0) v = bh;
-            if (col == D0 + 1) v = bl;
-          } else {
-            v = __float2half_rn(scale * __half2float(Wsrc[col & 31]));
-          }
-          h2[q] = v;
-          hb[q] = col == 0 ? bh : (col == 1 ? bl : __float2half_rn(0.0f));
-        }
-        __half2 hh = __halves2half2(h2[0], h2[1]), hbb = __halves2half2(hb[0], hb[1]);
-        w[e] = *reinterpret_cast<uint32_t*>(&hh);
-        wb[e] = *reinterpret_cast<uint32_t*>(&hbb);
-      }
-      *reinterpret_cast<uint4*>(Wt + sw_off(o, j)) = make_uint4(w[0], w[1], w[2], w[3]);
-      if (layer > 0) *reinterpret_cast<uint4*>(Wt + kBTile + sw_off(o, j)) = make_uint4(wb[0], wb[1], wb[2], wb[3]);
-    }
-  }
-  {
-    // last layer on the CUDA cores: folded like the hidden layers
-    const __half* Wl = net.W_h + (size_t)32 * D0 + (size_t)(L - 2) * 32 * 32;
-    for (int i = tid; i < D * 32; i += kThreads) wl[i] = (SNAKE ? 0.5f : 1.0f) * __half2float(Wl[i]);
-    if (tid < D) {
-      float bias = net.b[(L - 1) * 32 + tid];
-      if (SNAKE) {
-        float rs = 0.0f;
-        for (int c = 0; c < 32; ++c) rs += __half2float(Wl[tid * 32 + c]);
-        bias += 0.5f * rs;
-      }
-      wl[D * 32 + tid] = bias;
-    }
-    for (int i = tid; i < 3 * M; i += kThreads) fm[i] = net.fourier[i];
-    if (GQ)
-      for (int i = tid; i < 2 * F; i += kThreads) qp[i] = net.grid_qp[i];
-  }
-  load_tf(tf, b.tf);
-  // the thread's A row starts at zero; the constant tile has ones in columns
-  // 0 and 1 of every row (the bias MMA of the hidden layers)
-  {
-    uint8_t* A = Aall + wg * kTile;
-    uint8_t* One = sm + plan.oOne;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) *reinterpret_cast<uint4*>(A + sw_off(row, j)) = make_uint4(0, 0, 0, 0);
-    if (wg == 0) {
-#pragma unroll
-      for (int j = 0; j < 8; ++j)
-        *reinterpret_cast<uint4*>(One + sw_off(row, j)) = make_uint4(j == 0 ? pack_h2(1.0f, 1.0f) : 0u, 0u, 0u, 0u);
-    }
-  }
-  if (row == 0) {
-    mbar_init(smem_u32(&mbar[wg]), 1);
-    misc[4 + wg] = 0;
-  }
-  if (tid < 32) {
-    tmem_alloc(smem_u32((const void*)&misc[0]), kTmemCols);
-    tmem_relinquish();
-  }
-  fence_proxy_async();
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  if (tid == 0) {
-    // row k of a NeRF matrix: 2 pi 2^(k div 3) on axis k mod 3, zero elsewhere
-    int ok = 1;
-    for (int k = 0; k < M && ok; ++k)
-      for (int a = 0; a < 3; ++a) {
-        const float want = (a == k % 3) ? 6.2831855f * (float)(1 << (k / 3)) : 0.0f;
-        if (fm[3 * k + a] != want) ok = 0;
-      }
-    misc[1] = ok;
-  }
-  for (int i = tid; i < SRN_MAX_TF_POINTS; i += kThreads) {
-    const float wdt = i + 1 < tf.n ? tf.pos[i + 1] - tf.pos[i] : 0.0f;
-    tfinv[i] = wdt > 0.0f ? 1.0f / wdt : 0.0f;
-  }
-  __syncthreads();
-  const bool nerf = misc[1] != 0;
-  const uint32_t tmem = (uint32_t)misc[0];
-  const uint32_t d_tmem = tmem + (uint32_t)(wg * 32);
-  const uint32_t t_row = d_tmem + ((uint32_t)((row >> 5) * 32) << 16);  // warp's lane quarter
-  uint8_t* A = Aall + wg * kTile;
-  const uint32_t a_addr = smem_u32(A), b_addr = smem_u32(Bw), one_addr = smem_u32(sm + plan.oOne);
-  const uint32_t mb = smem_u32(&mbar[wg]);
-  const int bar_id = 1 + wg;
-
-  // ---- ray state
-  const int tiles_x = (b.W + 7) / 8, tiles_y = (b.H + 3) / 4;
-  const long long tpf = (long long)tiles_x * tiles_y;
-  const long long n_rays = POINTS ? pd.n : tpf * 32 * b.n_views * b.n_times;
-  const size_t gsz = (size_t)net.R * net.R * net.R * net.F;
-  bool active = false, exhausted = false, failed = false;
-  long long pix = 0;
-  float3 o = make_float3(0.f, 0.f, 0.f), d = o;
-  float t0 = 0.f, t1 = 0.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, Acc = 0.f;
-  int k = 0, pass = 0;
-  RayLat rl{0, -1, 1.0f, 0.0f, 0.0f};
-  float rho_c = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-  float3 ppos = make_float3(0.f, 0.f, 0.f);
-  unsigned int ns = 0;
-  uint32_t phase = 0;
-  if (POINTS) {
-    int k0;
-    float f;
-    time_weights(net, pd.time, k0, f);
-    rl.g0 = (int)(k0 * gsz);
-    rl.g1 = net.nkey > 1 ? (int)((k0 + 1) * gsz) : -1;
-    rl.w0 = net.nkey > 1 ? 1.0f - f : 1.0f;
-    rl.w1 = f;
-    rl.tin = pd.time;
-  }
-
-  while (true) {
-    // ---- refill: threads without a ray claim new ones (warp-aggregated)
-    while (true) {
-      const bool need = !active && !exhausted && !failed;
-      const unsigned int mask = __ballot_sync(0xffffffffu, need);
-      if (mask == 0) break;
-      unsigned long long base = 0;
-      const int leader = __ffs(mask) - 1;
-      if (lane == leader) base = atomicAdd(ray_counter, (unsigned long long)__popc(mask));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      if (need) {
-        const long long r = (long long)base + __popc(mask & ((1u << lane) - 1u));
-        if (r >= n_rays) {
-          exhausted = true;
-        } else if (POINTS) {
-          pix = r;
-          ppos = make_float3(clamp01f(pd.pts[3 * r]), clamp01f(pd.pts[3 * r + 1]), clamp01f(pd.pts[3 * r + 2]));
-          active = true;
-        } else {
-          const long long tile = r >> 5;
-          const int li = (int)(r & 31);
-          const long long frame = tile / tpf;
-          const int tt = (int)(tile - frame * tpf);
-          const int px = (tt % tiles_x) * 8 + (li & 7), py = (tt / tiles_x) * 4 + (li >> 3);
-          if (px < b.W && py < b.H) {
-            const int view = (int)(frame % b.n_views), ti = (int)(frame / b.n_views);
-            pix = (frame * b.H + py) * (long long)b.W + px;
-            camera_ray(b.cams[view], b.W, b.H, px, py, o, d);
-            if (box_intersect(o, d, t0, t1)) {
-              int k0;
-              float f;
-              time_weights(net, b.times[ti], k0, f);
-              rl.g0 = (int)(k0 * gsz);
-              rl.g1 = net.nkey > 1 ? (int)((k0 + 1) * gsz) : -1;
-              rl.w0 = net.nkey > 1 ? 1.0f - f : 1.0f;
-              rl.w1 = f;
-              rl.tin = b.times[ti];
-              C0 = C1 = C2 = Acc = 0.f;
-              k = 0;
-              pass = 0;
-              active = true;
-            } else {
-              reinterpret_cast<float4*>(b.out)[pix] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-          }
-        }
-      }
-    }
-
-    // ---- layer-0 input of this pass
-    float len = 0.f;
-    if (POINTS && active && !failed) {
-      write_input_row<M, F, K0, TI, GQ>(A, row, ppos, nerf, fm, net.grid_h, net.grid_q, qp, net.R, rl);
-    } else if (active && !failed) {
-      const float ta = fmaf((float)k, b.step, t0);
-      const float tb = fminf(fmaf((float)(k + 1), b.step, t0), t1);
-      len = tb - ta;
-      const float tm = 0.5f * (ta + tb);
-      float3 q = make_float3(clamp01f(fmaf(tm, d.x, o.x) + 0.5f), clamp01f(fmaf(tm, d.y, o.y) + 0.5f),
-                             clamp01f(fmaf(tm, d.z, o.z) + 0.5f));
-      if (SH == SRN_SHADE_FD && pass > 0) {
-        const int ax = (pass - 1) >> 1;
-        const float h = (pass & 1) ? b.fd_h : -b.fd_h;
-        if (ax == 0) q.x = clamp01f(q.x + h);
-        if (ax == 1) q.y = clamp01f(q.y + h);
-        if (ax == 2) q.z = clamp01f(q.z + h);
-      }
-      write_input_row<M, F, K0, TI, GQ>(A, row, q, nerf, fm, net.grid_h, net.grid_q, qp, net.R, rl);
-    }
-    fence_proxy_async();
-    tc_fence_before();
-    const bool any = bar_red_or(bar_id, 128, active && !failed);
-    if (!any || misc[4 + wg]) break;
-    if (row == 0) {
-      tc_fence_after();
-#pragma unroll
-      for (int kk = 0; kk < K0 / 16; ++kk)
-        mma_f16(d_tmem, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), kIdesc, kk > 0);
-      mma_commit(mb);
-    }
-
-    // ---- layers: wait, read the accumulator row, activation, next MMA
-    float out[4] = {0.f, 0.f, 0.f, 0.f};
-    bool stop = false;
-    for (int layer = 0; layer < L - 1; ++layer) {
-      // the failure decision is warp-uniform so tcgen05.ld stays convergent;
-      // a failed thread keeps arriving at the warpgroup barriers, which all
-      // threads leave together once the flag is visible
-      if (!__all_sync(0xffffffffu, mbar_wait_bounded(mb, phase))) {
-        failed = true;
-        misc[4 + wg] = 1;
-      }
-      phase ^= 1u;
-      tc_fence_after();
-      float x[32];
-      if (!failed) tmem_ld32(t_row, x);
-      if (layer < L - 2) {
-        if (!failed) {
-          // activation as FP16 hi (columns 0..31) + lo (columns 32..63)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            uint32_t hi[4], lo[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const float a0 = act_fold<ACT>(x[8 * j + 2 * e]), a1 = act_fold<ACT>(x[8 * j + 2 * e + 1]);
-              const __half2 h = __floats2half2_rn(a0, a1);
-              const float2 hb = __half22float2(h);
-              hi[e] = *reinterpret_cast<const uint32_t*>(&h);
-              lo[e] = pack_h2(a0 - hb.x, a1 - hb.y);
-            }
-            *reinterpret_cast<uint4*>(A + sw_off(row, j)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-            *reinterpret_cast<uint4*>(A + sw_off(row, 4 + j)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-          }
-        }
-        fence_proxy_async();
-        tc_fence_before();
-        bar_sync(bar_id, 128);
-        if (misc[4 + wg]) { stop = true; break; }
-        if (row == 0) {
-          tc_fence_after();
-          const uint32_t bw = b_addr + (1 + 2 * layer) * kBTile;
-          mma_f16(d_tmem, sw128_desc(one_addr), sw128_desc(bw + kBTile), kIdesc, 0u);  // bias
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk)
-            mma_f16(d_tmem, sw128_desc(a_addr + kk * 32), sw128_desc(bw + kk * 32), kIdesc, 1u);
-          mma_commit(mb);
-        }
-      } else if (!failed) {
-        float a[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) a[j] = act_fold<ACT>(x[j]);
-#pragma unroll
-        for (int dd = 0; dd < 4; ++dd) {
-          if (dd < D) {
-            float s = wl[D * 32 + dd];
-#pragma unroll
-            for (int j = 0; j < 32; ++j) s = fmaf(wl[dd * 32 + j], a[j], s);
-            out[dd] = s;
-          }
-        }
-      }
-    }
-    if (stop) break;
-
-    if (POINTS) {
-      if (active && !failed) {
-        for (int dd = 0; dd < D; ++dd) pd.out[pix * D + dd] = out[dd];
-        ++ns;
-        active = false;
-      }
-      continue;
-    }
-    // ---- transfer function, shading, compositing, termination
-    if (active && !failed) {
-      bool sample_done = true;
-      float3 g = make_float3(0.f, 0.f, 0.f);
-      if (SH == SRN_SHADE_FD) {
-        if (pass == 0) rho_c = out[0];
-        else if (pass == 1) gx = out[0];
-        else if (pass == 2) gx = (gx - out[0]) / (2.0f * b.fd_h);
-        else if (pass == 3) gy = out[0];
-        else if (pass == 4) gy = (gy - out[0]) / (2.0f * b.fd_h);
-        else if (pass == 5) gz = out[0];
-        else gz = (gz - out[0]) / (2.0f * b.fd_h);
-        sample_done = pass == NP - 1;
-        pass = sample_done ? 0 : pass + 1;
-        g = make_float3(gx, gy, gz);
-      } else {
-        rho_c = out[0];
-        if (SH == SRN_SHADE_HEAD) g = make_float3(out[1], out[2], out[3]);
-      }
-      if (sample_done) {
-        ++ns;
-        float4 c = tf_eval_inv(tf, tfinv, rho_c);
-        const float alpha = 1.0f - __expf(-c.w * tf.opacity_scale * len);
-        if (SH != SRN_SHADE_NONE) shade(c, g, d);
-        const float w = (1.0f - Acc) * alpha;
-        C0 = fmaf(w, c.x, C0);
-        C1 = fmaf(w, c.y, C1);
-        C2 = fmaf(w, c.z, C2);
-        Acc += w;
-        ++k;
-        if (Acc >= b.et || fmaf((float)k, b.step, t0) >= t1) {
-          reinterpret_cast<float4*>(b.out)[pix] = make_float4(C0, C1, C2, Acc);
-          active = false;
-        }
-      }
-    }
-  }
-
-  if (failed || misc[4 + wg]) {
-    if (row == 0) atomicExch(status, (unsigned int)SRN_ERR_TIMEOUT);
-  }
-  if (!POINTS) add_samples(b.samples, ns);
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  if (tid < 32) tmem_dealloc(tmem, kTmemCols);
-}
-
-template <int M, int F, int ACT, int SH, int TI = 0, int GQ = 0>
-cudaError_t launch_t(const NetDev& net, const BatchDev& b, const PointsDev& pd, unsigned long long* ctr,
-                     unsigned int* status, cudaStream_t s) {
-  SmemPlan plan = make_plan(net);
-  auto k = render_mma_kernel<M, F, ACT, SH, TI, GQ>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total);
-  if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0;
-  e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), s);
-  if (e != cudaSuccess) return e;
-  k<<<sms, kThreads, plan.total, s>>>(net, b, pd, plan, ctr, status);
-  return cudaGetLastError();
-}
-
-template <int M, int F, int ACT>
+template <int C, int M, int F, int ACT>
 cudaError_t dispatch_shading(const NetDev& net, const BatchDev& b, unsigned long long* ctr, unsigned int* st,
                              cudaStream_t s) {
   switch (b.shading) {
-    case SRN_SHADE_NONE: return launch_t<M, F, ACT, SRN_SHADE_NONE>(net, b, PointsDev{}, ctr, st, s);
-    case SRN_SHADE_FD: return launch_t<M, F, ACT, SRN_SHADE_FD>(net, b, PointsDev{}, ctr, st, s);
-    default: return launch_t<M, F, ACT, SRN_SHADE_HEAD>(net, b, PointsDev{}, ctr, st, s);
+    case SRN_SHADE_NONE: return launch_t<C, M, F, ACT, SRN_SHADE_NONE, 0, 0>(net, b, PointsDev{}, ctr, st, s);
+    case SRN_SHADE_FD: return launch_t<C, M, F, ACT, SRN_SHADE_FD, 0, 0>(net, b, PointsDev{}, ctr, st, s);
+    default: return launch_t<C, M, F, ACT, SRN_SHADE_HEAD, 0, 0>(net, b, PointsDev{}, ctr, st, s);
   }
+}
+
+// Shared memory the kernel needs for this network (0: the shape is not tiled).
+int mma_smem_bytes(const NetDev& n) {
+  if (n.c != 32 && n.c != 48 && n.c != 64) return 0;
+  return mma::make_plan(n, n.c, mma::wgs_for(n.c)).total;
 }
 
 }  // namespace
 
 bool render_mma_supported(const NetDev& n, int shading) {
-  if (n.c != 32 || n.l < 2 || n.l > 8) return false;
-  if (n.ti && !(n.m == 14 && n.F == 16 && n.act == SRN_ACT_SNAKEALT && shading == SRN_SHADE_NONE)) return false;
-  if (n.gq && !(n.m == 14 && n.F == 16 && n.act == SRN_ACT_SNAKEALT && shading == SRN_SHADE_NONE && !n.ti))
-    return false;
+  if (n.l < 2 || n.l > 8) return false;
   if (shading == SRN_SHADE_ADJOINT) return false;
   if (shading == SRN_SHADE_HEAD && n.D != 4) return false;
-  const bool shape_a = n.m == 14 && n.F == 16;
-  const bool shape_b = n.m == 12 && n.F == 8;
-  if (!shape_a && !shape_b) return false;
+  if (n.ti && !(n.c == 32 && n.m == 14 && n.F == 16 && n.act == SRN_ACT_SNAKEALT && shading == SRN_SHADE_NONE))
+    return false;
+  if (n.gq && !(n.c == 32 && n.m == 14 && n.F == 16 && n.act == SRN_ACT_SNAKEALT && shading == SRN_SHADE_NONE &&
+                !n.ti))
+    return false;
+  const bool shape_a = n.c == 32 && n.m == 14 && n.F == 16;
+  const bool shape_b = n.c == 32 && n.m == 12 && n.F == 8;
+  const bool shape_c = n.c == 48 && n.m == 22 && n.F == 16 && n.act == SRN_ACT_SNAKEALT && shading == SRN_SHADE_NONE;
+  const bool shape_d = n.c == 64 && n.m == 30 && n.F == 16 && n.act == SRN_ACT_SNAKEALT && shading == SRN_SHADE_NONE;
+  if (!shape_a && !shape_b && !shape_c && !shape_d) return false;
+  const int smem = mma_smem_bytes(n);
+  if (smem == 0 || smem > 227 * 1024) return false;
   if ((size_t)n.nkey * n.R * n.R * n.R * n.F >= (size_t)1 << 31) return false;
   return n.act == SRN_ACT_SINE || n.act == SRN_ACT_SNAKEALT;
 }
 
 cudaError_t launch_render_mma(const NetDev& n, const BatchDev& b, unsigned long long* ctr, unsigned int* status,
                               cudaStream_t s) {
-  if (n.ti) return launch_t<14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 1>(n, b, PointsDev{}, ctr, status, s);
-  if (n.gq) return launch_t<14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 0, 1>(n, b, PointsDev{}, ctr, status, s);
+  if (n.ti) return launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 1, 0>(n, b, PointsDev{}, ctr, status, s);
+  if (n.gq) return launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 0, 1>(n, b, PointsDev{}, ctr, status, s);
+  if (n.c == 48) return launch_t<48, 22, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 0, 0>(n, b, PointsDev{}, ctr, status, s);
+  if (n.c == 64) return launch_t<64, 30, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 0, 0>(n, b, PointsDev{}, ctr, status, s);
   if (n.m == 14 && n.F == 16) {
-    return n.act == SRN_ACT_SNAKEALT ? dispatch_shading<14, 16, SRN_ACT_SNAKEALT>(n, b, ctr, status, s)
-                                     : dispatch_shading<14, 16, SRN_ACT_SINE>(n, b, ctr, status, s);
+    return n.act == SRN_ACT_SNAKEALT ? dispatch_shading<32, 14, 16, SRN_ACT_SNAKEALT>(n, b, ctr, status, s)
+                                     : dispatch_shading<32, 14, 16, SRN_ACT_SINE>(n, b, ctr, status, s);
   }
-  return n.act == SRN_ACT_SNAKEALT ? dispatch_shading<12, 8, SRN_ACT_SNAKEALT>(n, b, ctr, status, s)
-                                   : dispatch_shading<12, 8, SRN_ACT_SINE>(n, b, ctr, status, s);
+  return n.act == SRN_ACT_SNAKEALT ? dispatch_shading<32, 12, 8, SRN_ACT_SNAKEALT>(n, b, ctr, status, s)
+                                   : dispatch_shading<32, 12, 8, SRN_ACT_SINE>(n, b, ctr, status, s);
 }
-
-}  // namespace srn
-
-namespace srn {
 
 bool eval_mma_supported(const NetDev& n) { return render_mma_supported(n, SRN_SHADE_NONE); }
 
@@ -830,13 +74,15 @@ cudaError_t launch_eval_mma(const NetDev& n, const float* pts, long long count, 
   memset(&b, 0, sizeof(b));
   b.tf.n = 2;
   PointsDev pd{pts, out, count, time};
-  if (n.ti) return launch_t<14, 16, SRN_ACT_SNAKEALT, kPoints, 1>(n, b, pd, ctr, status, s);
-  if (n.gq) return launch_t<14, 16, SRN_ACT_SNAKEALT, kPoints, 0, 1>(n, b, pd, ctr, status, s);
+  if (n.ti) return launch_t<32, 14, 16, SRN_ACT_SNAKEALT, kPoints, 1, 0>(n, b, pd, ctr, status, s);
+  if (n.gq) return launch_t<32, 14, 16, SRN_ACT_SNAKEALT, kPoints, 0, 1>(n, b, pd, ctr, status, s);
+  if (n.c == 48) return launch_t<48, 22, 16, SRN_ACT_SNAKEALT, kPoints, 0, 0>(n, b, pd, ctr, status, s);
+  if (n.c == 64) return launch_t<64, 30, 16, SRN_ACT_SNAKEALT, kPoints, 0, 0>(n, b, pd, ctr, status, s);
   if (n.m == 14 && n.F == 16)
-    return n.act == SRN_ACT_SNAKEALT ? launch_t<14, 16, SRN_ACT_SNAKEALT, kPoints>(n, b, pd, ctr, status, s)
-                                     : launch_t<14, 16, SRN_ACT_SINE, kPoints>(n, b, pd, ctr, status, s);
-  return n.act == SRN_ACT_SNAKEALT ? launch_t<12, 8, SRN_ACT_SNAKEALT, kPoints>(n, b, pd, ctr, status, s)
-                                   : launch_t<12, 8, SRN_ACT_SINE, kPoints>(n, b, pd, ctr, status, s);
+    return n.act == SRN_ACT_SNAKEALT ? launch_t<32, 14, 16, SRN_ACT_SNAKEALT, kPoints, 0, 0>(n, b, pd, ctr, status, s)
+                                     : launch_t<32, 14, 16, SRN_ACT_SINE, kPoints, 0, 0>(n, b, pd, ctr, status, s);
+  return n.act == SRN_ACT_SNAKEALT ? launch_t<32, 12, 8, SRN_ACT_SNAKEALT, kPoints, 0, 0>(n, b, pd, ctr, status, s)
+                                   : launch_t<32, 12, 8, SRN_ACT_SINE, kPoints, 0, 0>(n, b, pd, ctr, status, s);
 }
 
 }  // namespace srn

@@ -1,0 +1,71 @@
+// Declarations shared by the tensor-core render kernel (srn_mma_kernel.cuh),
+// its explicit instantiations (srn_mma_k*.cu) and the dispatcher
+// (srn_mma.cu).  Each kernel variant is compiled in exactly one translation
+// unit, so the variants build in parallel.
+#pragma once
+#include "srn_internal.h"
+
+namespace srn {
+namespace mma {
+
+
+// Warpgroups per CTA for hidden width C (one CTA per SM): what the shared
+// memory of the A tiles and weight tiles allows.
+constexpr int wgs_for(int C) { return C == 32 ? 6 : (C == 48 ? 4 : 3); }
+constexpr int kTile = 128 * 128;       // one A K-atom: 128 rows x 128 B (64 fp16)
+constexpr int kTmemCols = 256;         // >= warpgroups x C FP32 accumulator columns, power of two
+constexpr long long kWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
+constexpr int kPoints = 4;             // kernel mode: network output at given points (no ray march)
+
+// Point-evaluation arguments (mode kPoints).
+struct PointsDev {
+  const float* pts;  // [n][3]
+  float* out;        // [n][D]
+  long long n;
+  float time;
+};
+
+// ---------------------------------------------------------------- layout
+struct SmemPlan {
+  int oA, oOne, oB0, oBh, oBb, oWl, oTF, oTFinv, oFm, oQp, oMbar, oMisc, total;
+};
+
+// Shared memory for hidden width C and WGS warpgroups.  An operand row spans
+// ceil(K / 64) K-atoms of 64 FP16 columns; atoms of an A tile are kTile
+// bytes apart, atoms of a B tile C * 128 bytes apart.
+inline SmemPlan make_plan(const NetDev& n, int C, int WGS) {
+  const int D0 = net_d0(n);
+  const int K0 = ((D0 + 2 + 15) / 16) * 16;
+  const int NA0 = (K0 + 63) / 64, NAH = (2 * C + 63) / 64, NA = NA0 > NAH ? NA0 : NAH;
+  const int BT = C * 128;
+  const int NBB = n.l > 2 ? (16 * (n.l - 2) + 63) / 64 : 1;
+  SmemPlan s;
+  int o = 0;
+  s.oA = o; o += WGS * NA * kTile;
+  s.oOne = o; o += kTile;                   // constant tile: columns 0, 1 = 1
+  s.oB0 = o; o += NA0 * BT;                 // layer 0
+  s.oBh = o; o += (n.l - 2) * NAH * BT;     // hidden layers: [W | W]
+  s.oBb = o; o += NBB * BT;                 // hidden biases, one 16-column K-block per layer
+  s.oWl = o; o += (n.D * C + 4) * 4;
+  o = (o + 15) & ~15;
+  s.oTF = o; o += (int)sizeof(TFDev);
+  o = (o + 15) & ~15;
+  s.oTFinv = o; o += SRN_MAX_TF_POINTS * 4;
+  s.oFm = o; o += ((3 * n.m + 3) & ~3) * 4 + 16;
+  s.oQp = o; o += 2 * 32 * 4;
+  o = (o + 7) & ~7;
+  s.oMbar = o; o += 8 * WGS;
+  s.oMisc = o; o += 16 * 4;
+  s.total = o + 1024;  // alignment slack
+  return s;
+}
+
+// One kernel variant: hidden width C, M Fourier rows, F latent channels,
+// activation ACT, shading SH (or kPoints), direct time input TI, 8-bit grid
+// GQ.  Defined in srn_mma_kernel.cuh, instantiated in srn_mma_k*.cu.
+template <int C, int M, int F, int ACT, int SH, int TI, int GQ>
+cudaError_t launch_t(const NetDev& net, const BatchDev& b, const PointsDev& pd, unsigned long long* ctr,
+                     unsigned int* status, cudaStream_t s);
+
+}  // namespace mma
+}  // namespace srn

@@ -193,6 +193,30 @@ __device__ __forceinline__ void latent4_grad(const Latent& lat, const Cell& c, i
   }
 }
 
+// sin and cos of the Fourier argument e = F_k . p (Eq. 2) with e carried to
+// about twice FP32 precision: each product split exactly into hi + lo by an
+// FMA, the three products summed with error-free two-sums, then
+// sin(hi + lo) = sin hi + lo cos hi and cos(hi + lo) = cos hi - lo sin hi.
+// A plain FP32 dot product would lose |e| * 2^-24 of the argument, which for
+// the high NeRF octaves (|e| in the thousands) dominates the error; the
+// rounded-to-nearest intrinsics keep the compiler from contracting the steps.
+__device__ __forceinline__ void fourier_sincos(const float* f, float3 p, float& s, float& c) {
+  const float p0 = __fmul_rn(f[0], p.x), e0 = fmaf(f[0], p.x, -p0);
+  const float p1 = __fmul_rn(f[1], p.y), e1 = fmaf(f[1], p.y, -p1);
+  const float p2 = __fmul_rn(f[2], p.z), e2 = fmaf(f[2], p.z, -p2);
+  const float s1 = __fadd_rn(p0, p1);
+  const float b1 = __fsub_rn(s1, p0);
+  const float t1 = __fadd_rn(__fsub_rn(p0, __fsub_rn(s1, b1)), __fsub_rn(p1, b1));
+  const float hi = __fadd_rn(s1, p2);
+  const float b2 = __fsub_rn(hi, s1);
+  const float t2 = __fadd_rn(__fsub_rn(s1, __fsub_rn(hi, b2)), __fsub_rn(p2, b2));
+  const float lo = e0 + e1 + e2 + t1 + t2;
+  float sh, ch;
+  sincosf(hi, &sh, &ch);
+  s = fmaf(ch, lo, sh);
+  c = fmaf(-sh, lo, ch);
+}
+
 // Full forward pass at p.  out[0..D-1]; when STASH, hs[i] receives the
 // pre-activation of layer i (i = 0..l-2) for the adjoint.
 template <int C, bool STASH>
@@ -207,9 +231,8 @@ __device__ __forceinline__ void forward(const float* sm, const Layout& L, int ac
   axpy<C>(h, W0T + 2 * C, p.z);
   const float* Fm = sm + L.oF;
   for (int k = 0; k < L.m; ++k) {
-    float e = Fm[3 * k] * p.x + Fm[3 * k + 1] * p.y + Fm[3 * k + 2] * p.z;
     float s, c;
-    sincosf(e, &s, &c);
+    fourier_sincos(Fm + 3 * k, p, s, c);
     axpy<C>(h, W0T + (3 + k) * C, s);
     axpy<C>(h, W0T + (3 + L.m + k) * C, c);
   }
@@ -274,9 +297,8 @@ __device__ __forceinline__ float3 adjoint(const float* sm, const Layout& L, int 
   for (int k = 0; k < L.m; ++k) {
     float gs = dotrow<C>(W0T + (3 + k) * C, delta);
     float gc = dotrow<C>(W0T + (3 + L.m + k) * C, delta);
-    float e = Fm[3 * k] * p.x + Fm[3 * k + 1] * p.y + Fm[3 * k + 2] * p.z;
     float s, c;
-    sincosf(e, &s, &c);
+    fourier_sincos(Fm + 3 * k, p, s, c);
     float coef = gs * c - gc * s;
     dp.x = fmaf(coef, Fm[3 * k], dp.x);
     dp.y = fmaf(coef, Fm[3 * k + 1], dp.y);

@@ -186,6 +186,16 @@ def nerf_fourier_matrix(m: int) -> np.ndarray:
     return F
 
 
+def fourier_rows_for_width(width: int, F: int = 16) -> int:
+    """Fourier rows m for hidden width c in the width sweep: the input vector
+    3 + 2m + F plus one padding column is c + 16 wide, as the 48-column
+    input of the 32-channel network (Section 4.2 figure) is."""
+    m2 = width + 16 - 1 - 3 - F
+    if m2 <= 0 or m2 % 2:
+        raise ValueError("no Fourier count fits this width")
+    return m2 // 2
+
+
 def layer_dims(F, m, layers, width, out_dim, time_input=0):
     d = [3 + 2 * m + F + time_input] + [width] * (layers - 1) + [out_dim]
     return list(zip(d[:-1], d[1:]))

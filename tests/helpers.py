@@ -47,6 +47,42 @@ def compare_images(got, ref, margin, tol, et):
                 ok=bool((strict.size == 0 or strict.max() <= tol) and (not near.any() or err[near].max() <= TOL_ET_FLIP)))
 
 
+def conditioned_tol(render, tol, delta=2.0 ** -23):
+    """FP32 image tolerance that accounts for the conditioning of the image.
+
+    The FP32 kernels compute camera rays and sample positions in FP32, so a
+    sample position carries a rounding error of a few units of 2^-24.  For
+    networks with high Fourier octaves (or large inputs such as a raw time
+    value) the exact FP64 image already changes by more than the fixed
+    tolerance when the camera moves by that much.  The tolerance returned is
+    the larger of ``tol`` and twice the largest change of the oracle image
+    when every camera eye moves by +-delta along (1, -1, 1).  ``render(cams)``
+    renders with the given cameras (a list of camera dicts)."""
+    import copy
+    base = None
+    worst = 0.0
+    for sgn in (1.0, -1.0):
+        cams = render.cameras
+        shifted = copy.deepcopy(cams)
+        for c in shifted:
+            c["eye"] = [c["eye"][0] + sgn * delta, c["eye"][1] - sgn * delta, c["eye"][2] + sgn * delta]
+        if base is None:
+            base = np.asarray(render(cams), np.float64)
+        worst = max(worst, float(np.abs(np.asarray(render(shifted), np.float64) - base).max()))
+    return max(tol, 2.0 * worst)
+
+
+class OracleRender:
+    """Oracle render with fixed network, TF and image settings; called with
+    a camera list (for conditioned_tol)."""
+
+    def __init__(self, net, cams, tf, W, H, step, et, **kw):
+        self.net, self.cameras, self.tf, self.args, self.kw = net, cams, tf, (W, H, step, et), kw
+
+    def __call__(self, cams):
+        return oracle.render(self.net, cams, oracle_tf(self.tf), *self.args, **self.kw)[0]
+
+
 def cfg1_params(seed=0):
     """Config 1 network: 8^3 x 8 FP32 latent grid N(0, 0.01^2) (here wider so
     the latent term matters), 4 Fourier frequencies (m = 12), 2 layers of

@@ -43,7 +43,11 @@ def test_direct_time_render_and_eval(srn, precision):
     S.srn_render(net.ctx, cams, tf, S.render_desc(32, 24, 1 / 64, 2.0), out, times=times)
     torch.cuda.synchronize()
     ref, _, _ = oracle.render(on, cams, H.oracle_tf(tf), 32, 24, 1 / 64, 2.0, times=times)
-    tol = H.TOL_FP16_IMG if precision else H.TOL_FP32_IMG
+    # the raw time value (up to 15) as an input makes this image sensitive to
+    # FP32 position rounding: the FP32 bound follows the image's conditioning
+    tol = H.TOL_FP16_IMG if precision else H.conditioned_tol(
+        H.OracleRender(on, cams, tf, 32, 24, 1 / 64, 2.0, times=times), H.TOL_FP32_IMG)
+    assert tol <= 1e-4
     assert np.abs(out.cpu().numpy() - ref).max() <= tol
     pts = np.random.default_rng(101).uniform(0, 1, (20000, 3)).astype(np.float32)
     for t in [1.0, 9.25]:
