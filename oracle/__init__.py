@@ -81,15 +81,21 @@ def lib():
             L.orc_dvr_dense.argtypes = [dp, C.c_int, C.c_int, C.c_int, C.POINTER(Camera), C.c_int, C.POINTER(TF),
                                         C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
                                         C.POINTER(C.c_longlong), C.c_longlong, dp, dp, C.POINTER(C.c_longlong)]
+            u64p = C.POINTER(C.c_uint64)
             L.orc_fit_loss_grad.restype = C.c_double
             L.orc_fit_loss_grad.argtypes = [C.POINTER(Net), dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64,
-                                            C.c_int, C.c_double, C.c_double, C.c_double, dp, dp, dp]
+                                            C.c_int, C.c_double, C.c_double, C.c_double, dp, dp, dp, u64p, C.c_int]
             L.orc_adam.argtypes = [dp, dp, dp, dp, C.c_size_t, C.c_double, C.c_int, C.c_double, C.c_double,
                                    C.c_double]
             L.orc_fit_step.restype = C.c_double
             L.orc_fit_step.argtypes = [C.POINTER(Net), dp, dp, dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64,
                                        C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, dp,
-                                       C.POINTER(C.c_int)]
+                                       C.POINTER(C.c_int), u64p, C.c_int]
+            L.orc_error_grid.argtypes = [C.POINTER(Net), dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64,
+                                         C.c_double, dp]
+            L.orc_adaptive_cdf.restype = C.c_int
+            L.orc_adaptive_cdf.argtypes = [C.POINTER(C.c_float), C.c_int, u64p]
+            L.orc_adaptive_point.argtypes = [u64p, C.c_int, C.c_uint64, C.c_int, C.c_int, C.c_int, dp]
             L.orc_lowpass_resample.argtypes = [dp, C.c_int, C.c_int, C.c_int, C.c_int, dp]
             L.orc_psnr.restype = C.c_double
             L.orc_psnr.argtypes = [dp, dp, C.c_longlong]
@@ -293,15 +299,55 @@ def dvr_dense(vol, cams, tf: OracleTF, W, H, step, et, shading=SHADE_NONE, pixel
     return out, mg, ns.value
 
 
-def fit_loss_grad(net: OracleNet, vol, n_points, seed, step, t=0.0, gw=0.0, gs=1.0):
+def _cdf_args(cdf):
+    """(pointer, res) of an adaptive distribution from adaptive_cdf, or (None, 0)."""
+    if cdf is None:
+        return None, 0
+    S, res = cdf
+    assert S.dtype == np.uint64 and S.flags.c_contiguous and S.size == res ** 3 + 1
+    return S.ctypes.data_as(C.POINTER(C.c_uint64)), res
+
+
+def fit_loss_grad(net: OracleNet, vol, n_points, seed, step, t=0.0, gw=0.0, gs=1.0, cdf=None):
     v = _d(vol)
     nz, ny, nx = v.shape
     dW = np.zeros_like(net.W)
     db = np.zeros_like(net.b)
     dg = np.zeros_like(net.grid)
+    cp, cres = _cdf_args(cdf)
     loss = lib().orc_fit_loss_grad(C.byref(net.s), _p(v), nx, ny, nz, n_points, seed, step, t, gw, gs, _p(dW),
-                                   _p(db), _p(dg))
+                                   _p(db), _p(dg), cp, cres)
     return loss, net.unpack_W(dW), net.unpack_b(db), dg
+
+
+def error_grid(net: OracleNet, vol, res, spv, seed, t=0.0):
+    """Section 6.2 error grid E [res, res, res] (z, y, x) in float64."""
+    v = _d(vol)
+    nz, ny, nx = v.shape
+    E = np.zeros(res ** 3)
+    lib().orc_error_grid(C.byref(net.s), _p(v), nx, ny, nz, res, spv, seed, t, _p(E))
+    return E.reshape(res, res, res)
+
+
+def adaptive_cdf(E_f32, res):
+    """Integer distribution (S, res) from FP32 error values; raises on a
+    negative or non-finite entry."""
+    e = np.ascontiguousarray(np.asarray(E_f32, np.float32).reshape(-1))
+    assert e.size == res ** 3
+    S = np.zeros(res ** 3 + 1, np.uint64)
+    st = lib().orc_adaptive_cdf(e.ctypes.data_as(C.POINTER(C.c_float)), res, S.ctypes.data_as(C.POINTER(C.c_uint64)))
+    if st:
+        raise ValueError("error grid has a negative or non-finite entry")
+    return S, res
+
+
+def adaptive_points(cdf, seed, step, n):
+    S, res = cdf
+    out = np.zeros((n, 3))
+    sp = S.ctypes.data_as(C.POINTER(C.c_uint64))
+    for j in range(n):
+        lib().orc_adaptive_point(sp, res, seed, step, j, n, _p(out[j]))
+    return out
 
 
 def adam(theta, m, v, g, lr, step, beta1=0.9, beta2=0.999, eps=1e-8):
@@ -312,7 +358,8 @@ def adam(theta, m, v, g, lr, step, beta1=0.9, beta2=0.999, eps=1e-8):
     lib().orc_adam(_p(theta), _p(m), _p(v), _p(gg), theta.size, lr, step, beta1, beta2, eps)
 
 
-def fit_step(net: OracleNet, adam_m, adam_v, vol, n_points, seed, step, lr_grid, lr_net, t=0.0, gw=0.0, gs=1.0):
+def fit_step(net: OracleNet, adam_m, adam_v, vol, n_points, seed, step, lr_grid, lr_net, t=0.0, gw=0.0, gs=1.0,
+             cdf=None):
     """One fit step on the oracle's FP64 parameters (updated in place).
 
     Returns (loss, grads [grid | W | b] flat, status)."""
@@ -320,8 +367,9 @@ def fit_step(net: OracleNet, adam_m, adam_v, vol, n_points, seed, step, lr_grid,
     nz, ny, nx = v.shape
     grads = np.zeros(net.grid.size + net.W.size + net.b.size)
     st = C.c_int()
+    cp, cres = _cdf_args(cdf)
     loss = lib().orc_fit_step(C.byref(net.s), _p(adam_m), _p(adam_v), _p(v), nx, ny, nz, n_points, seed, step, t,
-                              lr_grid, lr_net, gw, gs, _p(grads), C.byref(st))
+                              lr_grid, lr_net, gw, gs, _p(grads), C.byref(st), cp, cres)
     return loss, grads, st.value
 
 

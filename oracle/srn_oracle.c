@@ -27,6 +27,11 @@
  *                          step index; shaded linear ramp closed form
  *   orc_dvr_dense          Gaussian blob line integral via erf
  *   orc_fit_step           finite differences of the loss + torch.optim.Adam
+ *   orc_error_grid         constant network vs constant / linear volume
+ *                          closed forms; every sample inside its voxel
+ *   orc_adaptive_cdf /     one-hot, uniform and 1:3 error grids give
+ *   orc_adaptive_point     exactly proportional point counts (+-1); points
+ *                          inside the chosen voxel; zero-error voxels empty
  *   orc_lowpass_resample   constant and affine fields preserved
  *   orc_psnr / orc_ssim    SSIM of constant images in closed form; identity
  * Head-mode training quality (loss design in the paper's missing supplement)
@@ -593,14 +598,111 @@ static void volume_fd_grad(const double* vol, int nx, int ny, int nz, const doub
 
 static double sgn(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
 
+/* ------------------------------------------------------------------------ */
+/* Section 6.2 adaptive resampling.  Every N fit steps the prediction error is
+ * estimated on a coarse voxel grid E (res^3 voxels, paper: 128^3) from a few
+ * positions per voxel (paper: 8), and the next steps draw their training
+ * points with counts proportional to E.
+ *
+ * Position i of voxel v = (vx, vy, vz) (v = (vz res + vy) res + vx):
+ * Philox4x32-10 of counter (v, i, 0x4552, 0), key (seed low, seed high);
+ * u_a = (word_a >> 8) 2^-24 and p_a = (v_a + u_a) / res, both operations in
+ * FP32 round-to-nearest (the position is an input both implementations
+ * derive identically).  Reading: the error is the L1 error of output 0 (the
+ * density) against the trilinear volume, the loss of the fit. */
+static float orc_voxel_coord(int va, uint32_t word, int res) {
+  float u = (float)(word >> 8) * (1.0f / 16777216.0f);
+  volatile float s = (float)va + u; /* one FP32 rounding, no contraction */
+  return s / (float)res;
+}
+
+void orc_error_grid(const orc_net* n, const double* vol, int nx, int ny, int nz, int res, int spv, uint64_t seed,
+                    double t, double* E) {
+  size_t nvox = (size_t)res * res * res;
+  orc_trace* tr = (orc_trace*)malloc(sizeof(orc_trace));
+  uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  for (size_t v = 0; v < nvox; ++v) {
+    int vx = (int)(v % res), vy = (int)((v / res) % res), vz = (int)(v / ((size_t)res * res));
+    double acc = 0.0;
+    for (int i = 0; i < spv; ++i) {
+      uint32_t ctr[4] = {(uint32_t)v, (uint32_t)i, 0x4552u, 0u}, o[4];
+      orc_philox4x32_10(ctr, key, o);
+      double p[3] = {orc_voxel_coord(vx, o[0], res), orc_voxel_coord(vy, o[1], res), orc_voxel_coord(vz, o[2], res)};
+      double y;
+      orc_trilinear(vol, nx, ny, nz, 1, p, &y);
+      forward(n, p, t, tr);
+      acc += fabs(tr->v[n->l][0] - y);
+    }
+    E[v] = acc / (double)spv;
+  }
+  free(tr);
+}
+
+/* Integer sampling distribution from an error grid (given as the FP32 values
+ * the GPU holds): q_v = floor(E_v * (65535 / max E)) in FP32, clamped to
+ * [0, 65535]; S is the exclusive prefix sum of q (S[0] = 0, S[nvox] = Q).
+ * Returns 0, or 1 when an entry is negative or not finite.  Q = 0 (a zero
+ * grid) means uniform sampling. */
+int orc_adaptive_cdf(const float* E, int res, uint64_t* S) {
+  size_t nvox = (size_t)res * res * res;
+  float mx = 0.0f;
+  for (size_t v = 0; v < nvox; ++v) {
+    if (!isfinite(E[v]) || E[v] < 0.0f) return 1;
+    if (E[v] > mx) mx = E[v];
+  }
+  S[0] = 0;
+  volatile float scale = mx > 0.0f ? 65535.0f / mx : 0.0f;
+  for (size_t v = 0; v < nvox; ++v) {
+    volatile float x = E[v] * scale;
+    float f = floorf(x);
+    uint32_t q = f >= 65535.0f ? 65535u : (uint32_t)f;
+    S[v + 1] = S[v] + q;
+  }
+  return 0;
+}
+
+/* Point j of n for fit step `step` under the distribution S: the voxel holds
+ * the stratum midpoint t_j = floor((2j + 1) Q / (2n)), i.e. the voxel v with
+ * S[v] <= t_j < S[v + 1] (so voxel v receives round(n q_v / Q) points, +-1);
+ * the offset inside it uses the uniform sampler's Philox draw (counter
+ * (j, step, 0x5352, 0)).  Requires (2n + 1) Q < 2^64. */
+void orc_adaptive_point(const uint64_t* S, int res, uint64_t seed, int step, int j, int n, double p[3]) {
+  size_t nvox = (size_t)res * res * res;
+  uint64_t Q = S[nvox];
+  uint64_t tj = ((uint64_t)(2 * (uint64_t)j + 1) * Q) / (2 * (uint64_t)n);
+  size_t lo = 0, hi = nvox; /* S[lo] <= tj < S[hi] */
+  while (hi - lo > 1) {
+    size_t mid = (lo + hi) / 2;
+    if (S[mid] <= tj) lo = mid; else hi = mid;
+  }
+  int vx = (int)(lo % res), vy = (int)((lo / res) % res), vz = (int)(lo / ((size_t)res * res));
+  uint32_t ctr[4] = {(uint32_t)j, (uint32_t)step, 0x5352u, 0u};
+  uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+  uint32_t o[4];
+  orc_philox4x32_10(ctr, key, o);
+  p[0] = orc_voxel_coord(vx, o[0], res);
+  p[1] = orc_voxel_coord(vy, o[1], res);
+  p[2] = orc_voxel_coord(vz, o[2], res);
+}
+
+/* The training point j of a fit step: uniform (S == NULL or Q == 0) or
+ * adaptive. */
+static void fit_point(const uint64_t* S, int res, uint64_t seed, int step, int j, int n, double p[3]) {
+  if (S && S[(size_t)res * res * res] > 0) orc_adaptive_point(S, res, seed, step, j, n, p);
+  else orc_sample_point(seed, step, j, p);
+}
+
 /* Loss and parameter gradients of one fit step without the update.
  * Section 5 world-space training: L1 loss between the prediction and the
  * trilinear ground truth at uniformly drawn points.  Reading for the 4-output
  * head (loss in the paper's missing supplement): L = mean_j(|rho_j - y_j|
  * + gw * sum_a |g_ja - gs * dV_a(p_j)|), dV by central differences.
- * The time of every point is t (one frame).  Gradients are overwritten. */
+ * The time of every point is t (one frame).  Gradients are overwritten.
+ * cdf (may be NULL): the Section 6.2 adaptive distribution of
+ * orc_adaptive_cdf over cdf_res^3 voxels. */
 double orc_fit_loss_grad(const orc_net* n, const double* vol, int nx, int ny, int nz, int n_points, uint64_t seed,
-                         int step, double t, double gw, double gs, double* dW, double* db, double* dgrid) {
+                         int step, double t, double gw, double gs, double* dW, double* db, double* dgrid,
+                         const uint64_t* cdf, int cdf_res) {
   size_t nW = 0, nb = 0;
   for (int i = 0; i < n->l; ++i) { nW += (size_t)layer_out(n, i) * layer_in(n, i); nb += layer_out(n, i); }
   size_t ng = (size_t)n->nkey * n->R * n->R * n->R * n->F;
@@ -612,7 +714,7 @@ double orc_fit_loss_grad(const orc_net* n, const double* vol, int nx, int ny, in
   double inv_n = 1.0 / (double)n_points;
   for (int j = 0; j < n_points; ++j) {
     double p[3];
-    orc_sample_point(seed, step, j, p);
+    fit_point(cdf, cdf_res, seed, step, j, n_points, p);
     double y;
     orc_trilinear(vol, nx, ny, nz, 1, p, &y);
     forward(n, p, t, tr);
@@ -655,12 +757,13 @@ void orc_adam(double* theta, double* m, double* v, const double* g, size_t n, do
  * unchanged and *status is set to 1. */
 double orc_fit_step(orc_net* n, double* adam_m, double* adam_v, const double* vol, int nx, int ny, int nz,
                     int n_points, uint64_t seed, int step, double t, double lr_grid, double lr_net, double gw,
-                    double gs, double* grads_out, int* status) {
+                    double gs, double* grads_out, int* status, const uint64_t* cdf, int cdf_res) {
   size_t nW = 0, nb = 0;
   for (int i = 0; i < n->l; ++i) { nW += (size_t)layer_out(n, i) * layer_in(n, i); nb += layer_out(n, i); }
   size_t ng = (size_t)n->nkey * n->R * n->R * n->R * n->F;
   double* g = (double*)malloc(sizeof(double) * (ng + nW + nb));
-  double loss = orc_fit_loss_grad(n, vol, nx, ny, nz, n_points, seed, step, t, gw, gs, g + ng, g + ng + nW, g);
+  double loss = orc_fit_loss_grad(n, vol, nx, ny, nz, n_points, seed, step, t, gw, gs, g + ng, g + ng + nW, g, cdf,
+                                  cdf_res);
   int finite = isfinite(loss);
   for (size_t i = 0; i < ng + nW + nb && finite; ++i) finite = isfinite(g[i]);
   if (grads_out) memcpy(grads_out, g, sizeof(double) * (ng + nW + nb));
