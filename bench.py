@@ -212,6 +212,49 @@ def fit_cfg3(vol, pts, steps=FIT_STEPS, seed=0):
     return res
 
 
+def fit_adaptive(vol, pts, steps=FIT_STEPS, seed=0, every=50, res=128, spv=8):
+    """Section 6.2 adaptive resampling on the config-2 fit: the render
+    network fitted with uniform points and with points drawn in proportion
+    to the error grid (res^3 voxels, spv positions each, recomputed every
+    `every` steps; the first `every` steps are uniform).  Reports density
+    PSNR, the mean and 99th percentile of the final error grid, and the time
+    of the fit with the error-grid passes included."""
+    import torch
+    from paper_2112_01579_gb300 import srn, synth
+    out = {"workload": f"cfg2 fit, {steps} steps x {FIT_POINTS} points; error grid {res}^3 x {spv}, every {every}"}
+    E = torch.zeros(res ** 3, device=vol.device)
+    for mode in ("uniform", "adaptive"):
+        p = synth.init_params(R=32, F=16, m=14, layers=4, width=32, out_dim=1, act=synth.ACT_SNAKEALT, seed=seed)
+        net = srn.Network(p, precision=srn.SRN_PREC_FP16, max_fit_points=FIT_POINTS, adam=True)
+        loss = torch.zeros(1, device=vol.device)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        grid_ms = []
+        e0.record()
+        for s in range(steps):
+            if mode == "adaptive" and s > 0 and s % every == 0:
+                g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                g0.record()
+                srn.srn_error_grid(net.ctx, vol, res, spv, seed + s, E)
+                srn.srn_fit_set_sampling(net.ctx, E, res)
+                g1.record()
+                grid_ms.append((g0, g1))
+            srn.srn_fit_step(net.ctx, vol, FIT_POINTS, seed + 1, s, loss, lr_grid=1e-2, lr_net=5e-3)
+        e1.record()
+        torch.cuda.synchronize()
+        srn.srn_error_grid(net.ctx, vol, res, spv, seed + 99991, E)
+        torch.cuda.synchronize()
+        e_np = E.cpu().numpy()
+        srn.srn_sync_half(net.ctx)
+        out[mode] = {"fit_ms": e0.elapsed_time(e1), "final_loss": float(loss.item()),
+                     "density_psnr_db": density_psnr_network(net, vol, pts),
+                     "error_grid_mean": float(e_np.mean()), "error_grid_p99": float(np.percentile(e_np, 99)),
+                     "error_grid_max": float(e_np.max())}
+        if grid_ms:
+            out[mode]["error_grid_and_cdf_ms"] = float(np.median([a.elapsed_time(b) for a, b in grid_ms]))
+        net.close()
+    return out
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_2112_01579_gb300 import srn
@@ -656,6 +699,9 @@ def main():
                                                          ("ms_per_frame", "psnr_per_timestep_db")}
         del vols
         res["config"]["width_sweep"] = width_sweep()
+        pts = vertex_points(vol.shape[0])
+        res["config"]["adaptive_resampling"] = fit_adaptive(vol, pts, steps=args.fit_steps)
+        del pts
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(net.unpack_half(), None, tf, cams)
     if rank == 0:

@@ -74,7 +74,7 @@ typedef struct srn_config {
   int feat;        /* F: latent channels, a multiple of 4 (of 8 for FP16) */
   int n_fourier;   /* m: rows of the Fourier matrix */
   int layers;      /* l >= 2: number of linear layers */
-  int width;       /* c: hidden channels (32 for every implemented kernel) */
+  int width;       /* c: hidden channels: 32, 48 or 64 (the fused fit and backward: 32) */
   int out_dim;     /* D: 1 (density) or 4 (density + gradient head, Section 5) */
   int activation;  /* SRN_ACT_* */
   int precision;   /* SRN_PREC_*: arithmetic of srn_render (FP16 = tensor cores) */
@@ -237,6 +237,41 @@ srn_status srn_backward(srn_ctx* ctx, const float* pts_dev, int n, float time, c
 srn_status srn_fit_step(srn_ctx* ctx, const float* volume_dev, const int dims[3], int n_points, uint64_t seed,
                         int step, float time, float lr_grid, float lr_net, float grad_weight, float grad_scale,
                         float* loss_dev, void* stream);
+
+/*
+ * Section 6.2 adaptive resampling, step 1: the error grid.  err_dev
+ * receives res^3 floats ([z][y][x], x fastest): E_v = mean over
+ * samples_per_voxel positions in voxel v of |rho(p) - V(p)| (network output 0
+ * in FP32 against the trilinear volume; paper: res 128, 8 positions).
+ * Position i of voxel v = (vx, vy, vz): Philox4x32-10 of counter
+ * (v, i, 0x4552, 0), key (seed low, seed high); u_a = (word_a >> 8) 2^-24;
+ * p_a = (v_a + u_a) / res in FP32 round-to-nearest.  2 <= res <= 256,
+ * 1 <= samples_per_voxel <= 64.  Any width.
+ */
+srn_status srn_error_grid(srn_ctx* ctx, const float* volume_dev, const int dims[3], int res, int samples_per_voxel,
+                          uint64_t seed, float time, float* err_dev, void* stream);
+
+/*
+ * Section 6.2 adaptive resampling, step 2: later srn_fit_step calls draw
+ * their points with counts proportional to the error grid err_dev (res^3
+ * floats, e.g. from srn_error_grid; read now, not kept).  Weights
+ * q_v = floor(E_v * (65535 / max E)) in FP32; S = exclusive prefix sum of q
+ * (64-bit integers), Q = S[res^3].  Point j of n lies in the voxel v with
+ * S[v] <= floor((2j + 1) Q / (2n)) < S[v + 1] (voxel v receives
+ * round(n q_v / Q) points, +-1), at the offset the uniform sampler's Philox
+ * draw for (seed, step, j) gives inside the voxel: p_a = (v_a + u_a) / res as
+ * above.  err_dev = NULL, or a grid whose maximum is 0, returns to uniform
+ * sampling.  A negative or non-finite entry leaves the sampling unchanged and
+ * returns SRN_ERR_INVALID_ARG (the call synchronizes the stream to check).
+ * The distribution lives in context memory (allocated on the first call or
+ * when res grows).  2 <= res <= 256.
+ */
+srn_status srn_fit_set_sampling(srn_ctx* ctx, const float* err_dev, int res, void* stream);
+
+/* The n_points positions (float32 [n][3]) that srn_fit_step with the same
+ * (n_points, seed, step) draws under the current sampling (uniform or
+ * adaptive). */
+srn_status srn_fit_points(srn_ctx* ctx, int n_points, uint64_t seed, int step, float* pts_dev, void* stream);
 
 /* Mean squared difference of two float32 arrays of n values (densities):
  * PSNR = 10 log10(1 / MSE) for volumes normalised to [0,1] (Section 6

@@ -22,6 +22,13 @@ struct srn_ctx {
   unsigned int* status;       // device status word (SRN_OK / SRN_ERR_NONFINITE / SRN_ERR_INTERNAL)
   unsigned long long* ray_counter;  // persistent-render work counter (8-byte aligned)
   FitScratch fit;             // scratch of srn_fit_step / srn_backward
+  // Section 6.2 adaptive distribution (srn_fit_set_sampling)
+  unsigned long long* cdf = nullptr;   // [cdf_cap] exclusive prefix sums of the voxel weights
+  unsigned long long* cdf_bsum = nullptr;
+  unsigned int* cdf_flags = nullptr;   // [2] validity flag, maximum bits
+  size_t cdf_cap = 0;
+  int cdf_res = 0;
+  bool cdf_active = false;
 };
 
 namespace {
@@ -41,6 +48,13 @@ srn_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// (2n + 1) * Q < 2^64 for every adaptive distribution over res^3 voxels
+// (Q <= 65535 res^3), so the stratum midpoints stay exact in 64 bits.
+bool adaptive_fits(long long n, int res) {
+  const unsigned long long q = 65535ull * (unsigned)res * (unsigned)res * (unsigned)res;
+  return q <= ~0ull / (2ull * (unsigned long long)n + 1ull);
+}
 
 srn_status check_config(const srn_config* c) {
   if (!c) return fail(SRN_ERR_INVALID_ARG, "config is NULL");
@@ -203,6 +217,9 @@ srn_status srn_destroy(srn_ctx* ctx) {
   if (!ctx) return SRN_OK;
   cudaDeviceSynchronize();
   fit_scratch_free(ctx->fit);
+  if (ctx->cdf) cudaFree(ctx->cdf);
+  if (ctx->cdf_bsum) cudaFree(ctx->cdf_bsum);
+  if (ctx->cdf_flags) cudaFree(ctx->cdf_flags);
   if (ctx->status) cudaFree(ctx->status);
   delete ctx;
   return SRN_OK;
@@ -326,6 +343,8 @@ srn_status srn_fit_step(srn_ctx* ctx, const float* volume_dev, const int dims[3]
   if (ctx->cfg.out_dim == 4 && !(grad_scale == grad_scale && grad_weight >= 0.0f))
     return fail(SRN_ERR_INVALID_ARG, "grad_weight must be >= 0");
   if (!(lr_grid >= 0.0f) || !(lr_net >= 0.0f)) return fail(SRN_ERR_INVALID_ARG, "learning rates must be >= 0");
+  if (ctx->cdf_active && !adaptive_fits(n_points, ctx->cdf_res))
+    return fail(SRN_ERR_UNSUPPORTED, "n_points too large for 64-bit adaptive sampling at this resolution");
   srn_status st = use_device(ctx);
   if (st) return st;
   FitArgs a;
@@ -347,6 +366,8 @@ srn_status srn_fit_step(srn_ctx* ctx, const float* volume_dev, const int dims[3]
   a.grid = ctx->prm.grid;
   a.weights = ctx->prm.weights;
   a.biases = ctx->prm.biases;
+  a.cdf = ctx->cdf_active ? ctx->cdf : nullptr;
+  a.cdf_res = ctx->cdf_res;
   const NetDev net = make_net(ctx);
   cudaError_t e = launch_fit_step(ctx->fit, net, a, (cudaStream_t)stream);
   if (e == cudaSuccess && ctx->cfg.grid_u8)
@@ -499,6 +520,78 @@ srn_status srn_load(srn_ctx* ctx, const char* path, int* step_out) {
   }
   if (step_out) *step_out = h.step;
   return SRN_OK;
+}
+
+srn_status srn_error_grid(srn_ctx* ctx, const float* volume_dev, const int dims[3], int res, int samples_per_voxel,
+                          uint64_t seed, float time, float* err_dev, void* stream) {
+  if (!ctx) return fail(SRN_ERR_INVALID_ARG, "ctx is NULL");
+  if (!volume_dev || !dims || dims[0] < 2 || dims[1] < 2 || dims[2] < 2)
+    return fail(SRN_ERR_INVALID_ARG, "volume with dims >= 2 is required");
+  if (res < 2 || res > 256) return fail(SRN_ERR_INVALID_ARG, "res must be in [2, 256]");
+  if (samples_per_voxel < 1 || samples_per_voxel > 64)
+    return fail(SRN_ERR_INVALID_ARG, "samples_per_voxel must be in [1, 64]");
+  if (!err_dev) return fail(SRN_ERR_INVALID_ARG, "err_dev is required");
+  srn_status st = use_device(ctx);
+  if (st) return st;
+  cudaError_t e = launch_error_grid(make_net(ctx), VolDev{volume_dev, dims[0], dims[1], dims[2]}, res,
+                                    samples_per_voxel, seed, time, err_dev, (cudaStream_t)stream);
+  return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_error_grid");
+}
+
+srn_status srn_fit_set_sampling(srn_ctx* ctx, const float* err_dev, int res, void* stream) {
+  if (!ctx) return fail(SRN_ERR_INVALID_ARG, "ctx is NULL");
+  if (!err_dev) {
+    ctx->cdf_active = false;
+    return SRN_OK;
+  }
+  if (res < 2 || res > 256) return fail(SRN_ERR_INVALID_ARG, "res must be in [2, 256]");
+  srn_status st = use_device(ctx);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long n = (long long)res * res * res;
+  const long long nb = (n + kCdfBlock - 1) / kCdfBlock;
+  cudaError_t e = cudaSuccess;
+  if (!ctx->cdf_flags) e = cudaMalloc((void**)&ctx->cdf_flags, 2 * sizeof(unsigned int));
+  if (e == cudaSuccess) e = launch_error_max(err_dev, n, ctx->cdf_flags, s);
+  unsigned int flags[2] = {0u, 0u};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(flags, ctx->cdf_flags, sizeof(flags), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "srn_fit_set_sampling");
+  if (flags[0]) return fail(SRN_ERR_INVALID_ARG, "error grid has a negative or non-finite entry");
+  if (flags[1] == 0u) {
+    ctx->cdf_active = false;  // all zero: uniform sampling
+    return SRN_OK;
+  }
+  if ((size_t)(n + 1) > ctx->cdf_cap) {
+    if (ctx->cdf) cudaFree(ctx->cdf);
+    if (ctx->cdf_bsum) cudaFree(ctx->cdf_bsum);
+    ctx->cdf = nullptr;
+    ctx->cdf_bsum = nullptr;
+    ctx->cdf_cap = 0;
+    ctx->cdf_active = false;
+    e = cudaMalloc((void**)&ctx->cdf, sizeof(unsigned long long) * (size_t)(n + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->cdf_bsum, sizeof(unsigned long long) * (size_t)nb);
+    if (e != cudaSuccess) return cuda_fail(e, "srn_fit_set_sampling");
+    ctx->cdf_cap = (size_t)(n + 1);
+  }
+  e = launch_build_cdf(err_dev, n, ctx->cdf_flags, ctx->cdf, ctx->cdf_bsum, s);
+  if (e != cudaSuccess) return cuda_fail(e, "srn_fit_set_sampling");
+  ctx->cdf_res = res;
+  ctx->cdf_active = true;
+  return SRN_OK;
+}
+
+srn_status srn_fit_points(srn_ctx* ctx, int n_points, uint64_t seed, int step, float* pts_dev, void* stream) {
+  if (!ctx) return fail(SRN_ERR_INVALID_ARG, "ctx is NULL");
+  if (n_points < 0 || (n_points > 0 && !pts_dev)) return fail(SRN_ERR_INVALID_ARG, "bad n_points / pts_dev");
+  if (step < 0) return fail(SRN_ERR_INVALID_ARG, "step must be >= 0");
+  if (ctx->cdf_active && !adaptive_fits(n_points, ctx->cdf_res))
+    return fail(SRN_ERR_UNSUPPORTED, "n_points too large for 64-bit adaptive sampling at this resolution");
+  srn_status st = use_device(ctx);
+  if (st) return st;
+  cudaError_t e = launch_fit_points(ctx->cdf_active ? ctx->cdf : nullptr, ctx->cdf_res, seed, step, n_points,
+                                    pts_dev, (cudaStream_t)stream);
+  return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_fit_points");
 }
 
 srn_status srn_density_mse(const float* a_dev, const float* b_dev, long long n, double* mse_dev, void* stream) {

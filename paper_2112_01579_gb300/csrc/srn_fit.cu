@@ -3,7 +3,8 @@
 // backward of the network, FP32 throughout.
 //
 // Pipeline of one step (all on the caller's stream, no host sync):
-//   1. point kernel: Philox4x32-10 sample (counter = point, step), ground
+//   1. point kernel: Philox4x32-10 sample (counter = point, step; uniform or
+//      the Section 6.2 error-proportional distribution), ground
 //      truth, forward with stashed pre-activations, loss, backward through
 //      the layers.  Weight gradients: each CTA stages delta_i and v_i of its
 //      128 points in shared memory and accumulates dW_i = sum_p delta v^T for
@@ -23,6 +24,7 @@
 
 #include "srn_fit.h"
 #include "srn_net32.cuh"
+#include "srn_sample.cuh"
 
 namespace srn {
 namespace {
@@ -32,31 +34,6 @@ using namespace net32;
 constexpr int kFitThreads = 128;
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 2048;  // keys per sort block: 8 warps x 8 rounds x 32
-
-// ---------------------------------------------------------------- RNG
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011): ten rounds of the
-// Philox S-box with multipliers 0xD2511F53 / 0xCD9E8D57 and Weyl key
-// increments 0x9E3779B9 / 0xBB67AE85.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const unsigned int lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-    const unsigned int lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
-    k.x += 0x9E3779B9u;
-    k.y += 0xBB67AE85u;
-  }
-  return c;
-}
-
-// Training point j of a step: counter (j, step, 0x5352, 0), key (seed
-// low, seed high); each coordinate is (word >> 8) * 2^-24.
-__device__ __forceinline__ float3 sample_point(unsigned long long seed, int step, int j) {
-  uint4 o = philox4x32_10(make_uint4((unsigned)j, (unsigned)step, 0x5352u, 0u),
-                          make_uint2((unsigned)(seed & 0xffffffffull), (unsigned)(seed >> 32)));
-  const float s = 1.0f / 16777216.0f;
-  return make_float3((float)(o.x >> 8) * s, (float)(o.y >> 8) * s, (float)(o.z >> 8) * s);
-}
 
 __device__ __forceinline__ float sgnf(float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); }
 
@@ -70,6 +47,8 @@ struct PointArgs {
   float time;
   VolDev vol;
   float gw, gs;
+  const unsigned long long* cdf;  // Section 6.2 adaptive distribution (null: uniform)
+  int cdf_res;
   float* pts;   // scratch out
   float* dz;
   unsigned int* key;
@@ -127,7 +106,7 @@ __global__ void __launch_bounds__(kFitThreads) fit_point_kernel(const NetDev net
     float out[4] = {0.f, 0.f, 0.f, 0.f}, dout[4] = {0.f, 0.f, 0.f, 0.f};
     float hs[kMaxL][C];
     if (valid) {
-      if (a.mode == 0) p = sample_point(a.seed, a.step, j);
+      if (a.mode == 0) p = sample::fit_point(a.cdf, a.cdf_res, a.seed, a.step, j, a.n);
       else p = clamp_p(make_float3(a.pts_in[3 * j], a.pts_in[3 * j + 1], a.pts_in[3 * j + 2]));
       forward<C, true>(sm, L, net.act, lat, p, out, hs);
       if (a.mode == 0) {
@@ -755,6 +734,8 @@ cudaError_t launch_fit_step(FitScratch& s, const NetDev& net, const FitArgs& a, 
   pa.vol = a.vol;
   pa.gw = a.grad_weight;
   pa.gs = a.grad_scale;
+  pa.cdf = a.cdf;
+  pa.cdf_res = a.cdf_res;
   const size_t ng = s.n_grid, nW = net_weight_count(net), nb = net_bias_count(net);
   cudaError_t e = run_backward(s, net, pa, s.grads, s.grads + ng, s.grads + ng + nW, a.loss, st);
   if (e != cudaSuccess) return e;

@@ -42,6 +42,8 @@ struct FitArgs {
   __half* weights_h;
   float* adam_m;
   float* adam_v;
+  const unsigned long long* cdf;  // Section 6.2 adaptive distribution over cdf_res^3 voxels (null: uniform)
+  int cdf_res;
 };
 
 bool fit_supported(const NetDev& net);
@@ -50,5 +52,21 @@ void fit_scratch_free(FitScratch& s);
 cudaError_t launch_backward(FitScratch& s, const NetDev& net, const float* pts, int n, float time, const float* dout,
                             float* dgrid, float* dW, float* db, cudaStream_t st);
 cudaError_t launch_fit_step(FitScratch& s, const NetDev& net, const FitArgs& a, cudaStream_t st);
+
+// Section 6.2 adaptive resampling (srn_adaptive.cu).
+// Error grid E[res^3]: mean |net(p) - V(p)| over spv positions per voxel.
+cudaError_t launch_error_grid(const NetDev& net, const VolDev& vol, int res, int spv, unsigned long long seed,
+                              float time, float* E, cudaStream_t st);
+// Validity and maximum of E: flags[0] = 1 if an entry is negative or not
+// finite, flags[1] = bits of the maximum (E >= 0 orders like its bits).
+cudaError_t launch_error_max(const float* E, long long n, unsigned int* flags, cudaStream_t st);
+// Integer distribution S[n + 1] (exclusive prefix of the 16-bit weights)
+// from E and its maximum in flags[1]; bsum holds ceil(n / 2048) entries.
+cudaError_t launch_build_cdf(const float* E, long long n, const unsigned int* flags, unsigned long long* S,
+                             unsigned long long* bsum, cudaStream_t st);
+// The n points a fit step (seed, step) draws under S (null: uniform).
+cudaError_t launch_fit_points(const unsigned long long* S, int res, unsigned long long seed, int step, int n,
+                              float* pts, cudaStream_t st);
+constexpr int kCdfBlock = 2048;  // weights per block of the prefix sum
 
 }  // namespace srn

@@ -26,7 +26,8 @@ SRN_MAX_KEYFRAMES, SRN_MAX_TF_POINTS, SRN_MAX_VIEWS, SRN_MAX_TIMES = 32, 32, 64,
 EXPORTED = ["srn_version", "srn_last_error", "srn_create", "srn_destroy", "srn_set_params", "srn_sync_half",
             "srn_render", "srn_dvr_dense", "srn_eval", "srn_density_grad", "srn_backward", "srn_fit_step",
             "srn_sync_status", "srn_image_mse", "srn_backward_static", "srn_density_mse", "srn_resample",
-            "srn_lowpass_resample", "srn_save", "srn_load"]
+            "srn_lowpass_resample", "srn_save", "srn_load", "srn_error_grid", "srn_fit_set_sampling",
+            "srn_fit_points"]
 
 
 class SrnError(RuntimeError):
@@ -96,6 +97,9 @@ def lib():
         L.srn_lowpass_resample.argtypes = [vp, C.POINTER(C.c_int), i, vp, vp, vp]
         L.srn_save.argtypes = [vp, C.c_char_p, i]
         L.srn_load.argtypes = [vp, C.c_char_p, C.POINTER(C.c_int)]
+        L.srn_error_grid.argtypes = [vp, vp, C.POINTER(C.c_int), i, i, C.c_uint64, f, vp, vp]
+        L.srn_fit_set_sampling.argtypes = [vp, vp, i, vp]
+        L.srn_fit_points.argtypes = [vp, i, C.c_uint64, i, vp, vp]
         for name in EXPORTED[2:]:
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -204,6 +208,24 @@ def srn_backward_static(cfg, params, pts, dout, dgrid, dweights, dbiases, time=0
     allocate, e.g. while a stream is being captured into a CUDA graph."""
     _check(lib().srn_backward_static(C.byref(cfg), C.byref(params), _ptr(pts), pts.shape[0], float(time),
                                      _ptr(dout), _ptr(dgrid), _ptr(dweights), _ptr(dbiases), _stream(stream)))
+
+
+def srn_error_grid(ctx, volume, res, samples_per_voxel, seed, err, time=0.0, stream=None):
+    """Section 6.2 error grid: err float32 CUDA tensor of res^3 entries."""
+    nz, ny, nx = volume.shape
+    dims = (C.c_int * 3)(nx, ny, nz)
+    _check(lib().srn_error_grid(ctx, _ptr(volume), dims, int(res), int(samples_per_voxel), int(seed), float(time),
+                                _ptr(err), _stream(stream)))
+
+
+def srn_fit_set_sampling(ctx, err, res=0, stream=None):
+    """Draw later fit points in proportion to err (res^3 float32 CUDA
+    tensor); err=None returns to uniform sampling."""
+    _check(lib().srn_fit_set_sampling(ctx, None if err is None else _ptr(err), int(res), _stream(stream)))
+
+
+def srn_fit_points(ctx, n_points, seed, step, pts, stream=None):
+    _check(lib().srn_fit_points(ctx, int(n_points), int(seed), int(step), _ptr(pts), _stream(stream)))
 
 
 def srn_fit_step(ctx, volume, n_points, seed, step, loss, lr_grid=1e-2, lr_net=5e-3, time=0.0, grad_weight=0.0,
