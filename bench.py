@@ -509,7 +509,7 @@ def time_workload(fit_steps=FIT_STEPS, seed=0, time_input=0, vols=None):
             "trained_timesteps": train_t}
 
 
-def width_sweep(seed=0, size=512, step=1 / 256):
+def width_sweep(seed=0, size=1024, step=1 / 256):
     """Width / layer sweep of the network render (Section 4.1 performance
     figure): hidden width c in {32, 48, 64} x l in {2, 4, 6} layers, 32^3 x 16
     latent grid, m Fourier rows so the input is c + 16 wide, random
@@ -572,7 +572,7 @@ TRANSC_PER_SAMPLE = 3 * 32 + 2 * 14 + 1
 SMS, MUFU_PER_SM_CLK, FP32_PER_SM_CLK, MAX_SM_GHZ = 152, 16, 128, 2.07
 # DRAM bytes of one 1024^2 frame of the render kernel, from the ncu capture
 # summarised in profiles/ (null when the kernel changed after the capture).
-RENDER_DRAM_BYTES = 1145600
+RENDER_DRAM_BYTES = None
 
 
 def roofline(res):
