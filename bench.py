@@ -212,6 +212,37 @@ def fit_cfg3(vol, pts, steps=FIT_STEPS, seed=0):
     return res
 
 
+def point_eval(net, vol, n=1 << 20, seed=0):
+    """Random-access reconstruction (the paper's evaluation of 10^6 random
+    locations): 2^20 uniform points of the fitted render network, FP16
+    tensor-core eval, FP32 eval, and FP32 density + adjoint gradient; ms per
+    call (L2 flushed) and the density PSNR at the points against the
+    trilinear volume."""
+    import torch
+    from paper_2112_01579_gb300 import srn
+    g = torch.Generator(device=vol.device).manual_seed(seed)
+    pts = torch.rand((n, 3), device=vol.device, generator=g)
+    ref = torch.nn.functional.grid_sample(vol[None, None], (pts * 2 - 1).view(1, 1, 1, n, 3),
+                                          align_corners=True).view(-1).contiguous()
+    out = torch.empty((n, 1), device=vol.device)
+    grad = torch.empty((n, 3), device=vol.device)
+    rho = torch.empty(n, device=vol.device)
+    n32 = srn.Network(net.unpack(), precision=srn.SRN_PREC_FP32)
+    mse = torch.zeros(1, dtype=torch.float64, device=vol.device)
+    res = {"workload": f"{n} uniform random points of the fitted cfg2 network"}
+    for name, fn, o in (("eval_fp16_tensor", lambda: srn.srn_eval(net.ctx, pts, out), out),
+                        ("eval_fp32", lambda: srn.srn_eval(n32.ctx, pts, out), out),
+                        ("density_grad_fp32", lambda: srn.srn_density_grad(n32.ctx, pts, rho, grad), rho)):
+        ms = _time_frames(fn, n=5)
+        fn()
+        srn.srn_density_mse(o.reshape(-1).contiguous(), ref, mse)
+        torch.cuda.synchronize()
+        res[name] = {"ms": ms, "points_per_s": n / (ms / 1e3),
+                     "density_psnr_db": 10 * math.log10(1.0 / max(mse.item(), 1e-30))}
+    n32.close()
+    return res
+
+
 def fit_adaptive(vol, pts, steps=FIT_STEPS, seed=0, every=50, res=128, spv=8):
     """Section 6.2 adaptive resampling on the config-2 fit: the render
     network fitted with uniform points and with points drawn in proportion
@@ -698,6 +729,7 @@ def main():
         res["config"]["time_cfg5"]["direct_encoding"] = {k: direct[k] for k in
                                                          ("ms_per_frame", "psnr_per_timestep_db")}
         del vols
+        res["config"]["point_eval"] = point_eval(net, vol)
         res["config"]["width_sweep"] = width_sweep()
         pts = vertex_points(vol.shape[0])
         res["config"]["adaptive_resampling"] = fit_adaptive(vol, pts, steps=args.fit_steps)

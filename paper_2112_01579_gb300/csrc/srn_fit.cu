@@ -59,22 +59,34 @@ struct PointArgs {
 };
 
 // Adds the contribution of the CTA's points to the gradient entries of one
-// layer: W block (dout x din at woff) and bias block (dout at boff).
+// layer: W block (dout x din at woff) and bias block (dout at boff).  Each
+// sum over the CTA's points runs as four interleaved partial sums (points
+// p = 4q + r) combined at the end, a fixed order.
 __device__ __forceinline__ void accumulate_layer(float* sacc, const float* sdelta, int dstr_d, const float* svin,
                                                  int dstr_v, int dout, int din, int woff, int boff) {
   const int tid = threadIdx.x;
   for (int e = tid; e < dout * din; e += kFitThreads) {
     const int o = e / din, j = e - o * din;
-    float s = 0.f;
-#pragma unroll 8
-    for (int p = 0; p < kFitThreads; ++p) s = fmaf(sdelta[p * dstr_d + o], svin[p * dstr_v + j], s);
-    sacc[woff + e] += s;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll 4
+    for (int p = 0; p < kFitThreads; p += 4) {
+      s0 = fmaf(sdelta[p * dstr_d + o], svin[p * dstr_v + j], s0);
+      s1 = fmaf(sdelta[(p + 1) * dstr_d + o], svin[(p + 1) * dstr_v + j], s1);
+      s2 = fmaf(sdelta[(p + 2) * dstr_d + o], svin[(p + 2) * dstr_v + j], s2);
+      s3 = fmaf(sdelta[(p + 3) * dstr_d + o], svin[(p + 3) * dstr_v + j], s3);
+    }
+    sacc[woff + e] += (s0 + s1) + (s2 + s3);
   }
   for (int e = tid; e < dout; e += kFitThreads) {
-    float s = 0.f;
-#pragma unroll 8
-    for (int p = 0; p < kFitThreads; ++p) s += sdelta[p * dstr_d + e];
-    sacc[boff + e] += s;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll 4
+    for (int p = 0; p < kFitThreads; p += 4) {
+      s0 += sdelta[p * dstr_d + e];
+      s1 += sdelta[(p + 1) * dstr_d + e];
+      s2 += sdelta[(p + 2) * dstr_d + e];
+      s3 += sdelta[(p + 3) * dstr_d + e];
+    }
+    sacc[boff + e] += (s0 + s1) + (s2 + s3);
   }
 }
 
@@ -132,15 +144,19 @@ __global__ void __launch_bounds__(kFitThreads) fit_point_kernel(const NetDev net
         for (int dd = 0; dd < D; ++dd) dout[dd] = a.dout_in[(size_t)j * D + dd];
       }
     }
-    // ---- last layer (C -> D): delta = dout, input = act(h_{l-2})
-    float act_in[C];
+    // ---- last layer (C -> D): delta = dout, input = act(h_{l-2}); the
+    // activation and its derivative come from one sin/cos evaluation
+    float dact[C];
 #pragma unroll
-    for (int o = 0; o < C; ++o) act_in[o] = valid ? act_f(net.act, hs[l - 2][o]) : 0.f;
+    for (int o = 0; o < C; ++o) {
+      float av = 0.f, dv = 0.f;
+      if (valid) act_and_df(net.act, hs[l - 2][o], av, dv);
+      svin[tid * dstr_v + o] = av;
+      dact[o] = dv;
+    }
 #pragma unroll
     for (int dd = 0; dd < 4; ++dd)
       if (dd < D) sdelta[tid * dstr_d + dd] = dout[dd];
-#pragma unroll
-    for (int o = 0; o < C; ++o) svin[tid * dstr_v + o] = act_in[o];
     __syncthreads();
     accumulate_layer(sacc, sdelta, dstr_d, svin, dstr_v, D, C, nW - D * C, nW + (l - 1) * C);
     __syncthreads();
@@ -149,14 +165,17 @@ __global__ void __launch_bounds__(kFitThreads) fit_point_kernel(const NetDev net
     for (int jj = 0; jj < C; ++jj) {
       float g = 0.f;
       for (int dd = 0; dd < D; ++dd) g = fmaf(sm[L.oWl + dd * C + jj], dout[dd], g);
-      delta[jj] = valid ? g * act_df(net.act, hs[l - 2][jj]) : 0.f;
+      delta[jj] = g * dact[jj];
     }
     // ---- hidden layers i = l-2 .. 1 (C -> C)
     for (int i = l - 2; i >= 1; --i) {
 #pragma unroll
       for (int o = 0; o < C; ++o) {
+        float av = 0.f, dv = 0.f;
+        if (valid) act_and_df(net.act, hs[i - 1][o], av, dv);
         sdelta[tid * dstr_d + o] = delta[o];
-        svin[tid * dstr_v + o] = valid ? act_f(net.act, hs[i - 1][o]) : 0.f;
+        svin[tid * dstr_v + o] = av;
+        dact[o] = dv;
       }
       __syncthreads();
       accumulate_layer(sacc, sdelta, dstr_d, svin, dstr_v, C, C, C * d0 + (i - 1) * C * C, nW + i * C);
@@ -168,7 +187,7 @@ __global__ void __launch_bounds__(kFitThreads) fit_point_kernel(const NetDev net
 #pragma unroll
       for (int o = 0; o < C; ++o) axpy<C>(g, Wrm + o * C, delta[o]);
 #pragma unroll
-      for (int jj = 0; jj < C; ++jj) delta[jj] = valid ? g[jj] * act_df(net.act, hs[i - 1][jj]) : 0.f;
+      for (int jj = 0; jj < C; ++jj) delta[jj] = g[jj] * dact[jj];
     }
     // ---- layer 0 (d0 -> C): input [p, sin(Fp), cos(Fp), z]
 #pragma unroll
@@ -201,7 +220,12 @@ __global__ void __launch_bounds__(kFitThreads) fit_point_kernel(const NetDev net
     __syncthreads();
     if (valid) {
       const float* W0T = sm + L.oW0T;
-      for (int f = 0; f < L.F; ++f) a.dz[(size_t)j * L.F + f] = dotrow<C>(W0T + (3 + 2 * L.m + f) * C, delta);
+      float4* dzj = reinterpret_cast<float4*>(a.dz + (size_t)j * L.F);
+      for (int f = 0; f < L.F; f += 4) {
+        const float* r = W0T + (3 + 2 * L.m + f) * C;
+        dzj[f >> 2] = make_float4(dotrow<C>(r, delta), dotrow<C>(r + C, delta), dotrow<C>(r + 2 * C, delta),
+                                  dotrow<C>(r + 3 * C, delta));
+      }
       a.pts[3 * j] = p.x;
       a.pts[3 * j + 1] = p.y;
       a.pts[3 * j + 2] = p.z;
@@ -564,7 +588,8 @@ cudaError_t run_backward(FitScratch& s, const NetDev& net, PointArgs pa, float* 
   const int n = pa.n;
   const int nW = (int)(net_weight_count(net)), nb = (int)net_bias_count(net);
   Layout L = make_layout(net, true);
-  const int dstride = (net_d0(net) > net.c ? net_d0(net) : net.c) + 1;
+  // odd row stride: per-thread rows written at the same column hit distinct banks
+  const int dstride = ((net_d0(net) > net.c ? net_d0(net) : net.c) + 1) | 1;
   pa.dstride = dstride;
   pa.n_entries = nW + nb;
   pa.pts = s.pts;

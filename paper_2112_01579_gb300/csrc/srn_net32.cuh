@@ -97,6 +97,18 @@ __device__ __forceinline__ float act_f(int act, float x) {
   float s = sinf(x);
   return act == SRN_ACT_SNAKEALT ? fmaf(0.5f, x, s * s) : s;
 }
+// Activation value and derivative from one sin/cos evaluation.
+__device__ __forceinline__ void act_and_df(int act, float x, float& a, float& d) {
+  float s, c;
+  sincosf(x, &s, &c);
+  if (act == SRN_ACT_SNAKEALT) {
+    a = fmaf(0.5f, x, s * s);
+    d = 0.5f + 2.0f * s * c;
+  } else {
+    a = s;
+    d = c;
+  }
+}
 __device__ __forceinline__ float act_df(int act, float x) {
   if (act == SRN_ACT_SNAKEALT) {
     float s, c;
