@@ -459,8 +459,9 @@ def _psnr_imgs(S, a, b):
 def shaded_workload(fit_steps=FIT_STEPS, seed=0):
     """Config 4: 512^3 anisotropic blobs + noise; 64^3 x 16 FP16 grid, 4
     SnakeAlt layers; 1024^2 at step 1/1024 with headlight shading from the
-    adjoint gradient (FP32 kernels), central differences (FP16 tensor
-    cores, 6 extra evaluations) and the 4-output head (FP16 tensor cores),
+    adjoint gradient (FP32 kernels, and backward MMAs on the FP16 tensor
+    cores), central differences (FP16 tensor cores, 6 extra evaluations) and
+    the 4-output head (FP16 tensor cores),
     against dense DVR of the volume with one-voxel central differences."""
     import torch
     from paper_2112_01579_gb300 import srn, synth
@@ -481,6 +482,7 @@ def shaded_workload(fit_steps=FIT_STEPS, seed=0):
     ref = torch.zeros((1, H_IMG, W_IMG, 4), device="cuda")
     n32 = srn.Network(nets[1].unpack(), precision=srn.SRN_PREC_FP32)
     modes = [("none_fp16", nets[1], srn.SRN_SHADE_NONE), ("adjoint_fp32", n32, srn.SRN_SHADE_ADJOINT),
+             ("adjoint_fp16", nets[1], srn.SRN_SHADE_ADJOINT),
              ("fd_fp16", nets[1], srn.SRN_SHADE_FD), ("head_fp16", nets[4], srn.SRN_SHADE_HEAD)]
     for name, net, sh in modes:
         desc = srn.render_desc(W_IMG, H_IMG, 1 / 1024, ET, sh, 1 / 511)
@@ -491,7 +493,8 @@ def shaded_workload(fit_steps=FIT_STEPS, seed=0):
     desc = srn.render_desc(W_IMG, H_IMG, 1 / 1024, ET, srn.SRN_SHADE_FD)
     res["dense_fd_ms_per_frame"] = _time_frames(lambda: srn.srn_dvr_dense(vol, cams[:1], tf, desc, ref), n=3)
     res["ratio_fd_over_head"] = res["fd_fp16"]["ms_per_frame"] / res["head_fp16"]["ms_per_frame"]
-    res["ratio_adjoint_over_head"] = res["adjoint_fp32"]["ms_per_frame"] / res["head_fp16"]["ms_per_frame"]
+    res["ratio_adjoint_over_head"] = res["adjoint_fp16"]["ms_per_frame"] / res["head_fp16"]["ms_per_frame"]
+    res["ratio_adjoint_fp32_over_head"] = res["adjoint_fp32"]["ms_per_frame"] / res["head_fp16"]["ms_per_frame"]
     for n in list(nets.values()) + [n32]:
         n.close()
     del vol

@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_hist_kernel(const unsigned 
 constexpr int kScanThreads = 1024, kScanPer = 8, kScanTile = kScanThreads * kScanPer;
 __global__ void __launch_bounds__(kScanThreads) scan_kernel(unsigned int* __restrict__ a, int m) {
   __shared__ unsigned int tile[kScanTile + kScanTile / 32];  // padded: 8-strided reads stay conflict-free
-  __shared__ unsigned int part[kScanThreads];
+  __shared__ unsigned int part[32];
   __shared__ unsigned int carry_s;
   const int tid = threadIdx.x;
   if (tid == 0) carry_s = 0;
@@ -305,15 +305,29 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(unsigned int* __rest
       v[k] = tile[i + i / 32];
       s += v[k];
     }
-    part[tid] = s;
-    __syncthreads();
-    for (int off = 1; off < kScanThreads; off <<= 1) {
-      const unsigned int t = tid >= off ? part[tid - off] : 0u;
-      __syncthreads();
-      part[tid] += t;
-      __syncthreads();
+    // block-wide inclusive scan of the thread sums: warp shuffles, then the
+    // 32 warp totals by warp 0
+    const int lane = tid & 31, warp = tid >> 5;
+    unsigned int x = s;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xffffffffu, x, off);
+      if (lane >= off) x += y;
     }
-    unsigned int run = carry_s + part[tid] - s;
+    if (lane == 31) part[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      unsigned int w = part[lane];
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xffffffffu, w, off);
+        if (lane >= off) w += y;
+      }
+      part[lane] = w;
+    }
+    __syncthreads();
+    const unsigned int incl = (warp > 0 ? part[warp - 1] : 0u) + x;
+    unsigned int run = carry_s + incl - s;
 #pragma unroll
     for (int k = 0; k < kScanPer; ++k) {
       const int i = tid * kScanPer + k;
@@ -325,7 +339,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(unsigned int* __rest
       const int g = base + i;
       if (g < m) a[g] = tile[i + i / 32];
     }
-    if (tid == kScanThreads - 1) carry_s += part[tid];
+    if (tid == kScanThreads - 1) carry_s += incl;
     __syncthreads();
   }
 }

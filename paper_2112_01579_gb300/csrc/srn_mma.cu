@@ -18,21 +18,27 @@ cudaError_t dispatch_shading(const NetDev& net, const BatchDev& b, unsigned long
   switch (b.shading) {
     case SRN_SHADE_NONE: return launch_t<C, M, F, ACT, SRN_SHADE_NONE, 0, 0>(net, b, PointsDev{}, ctr, st, s);
     case SRN_SHADE_FD: return launch_t<C, M, F, ACT, SRN_SHADE_FD, 0, 0>(net, b, PointsDev{}, ctr, st, s);
+    case SRN_SHADE_ADJOINT: return launch_t<C, M, F, ACT, SRN_SHADE_ADJOINT, 0, 0>(net, b, PointsDev{}, ctr, st, s);
     default: return launch_t<C, M, F, ACT, SRN_SHADE_HEAD, 0, 0>(net, b, PointsDev{}, ctr, st, s);
   }
 }
 
-// Shared memory the kernel needs for this network (0: the shape is not tiled).
-int mma_smem_bytes(const NetDev& n) {
+// Shared memory the kernel needs for this network and shading (0: the shape
+// is not tiled).
+int mma_smem_bytes(const NetDev& n, int shading) {
   if (n.c != 32 && n.c != 48 && n.c != 64) return 0;
-  return mma::make_plan(n, n.c, mma::wgs_for(n.c)).total;
+  const int sh = shading == SRN_SHADE_ADJOINT ? SRN_SHADE_ADJOINT : SRN_SHADE_NONE;  // the most warpgroups otherwise
+  return mma::make_plan(n, n.c, mma::wgs_for(n.c, sh), sh == SRN_SHADE_ADJOINT).total;
 }
 
 }  // namespace
 
 bool render_mma_supported(const NetDev& n, int shading) {
   if (n.l < 2 || n.l > 8) return false;
-  if (shading == SRN_SHADE_ADJOINT) return false;
+  // adjoint: backward MMAs at width 32, density output, at most four layers
+  // (two stashed derivative blocks in TMEM), no time input, FP16 grid
+  if (shading == SRN_SHADE_ADJOINT && !(n.c == 32 && n.D == 1 && n.l <= mma::kAdjMaxLayers && !n.ti && !n.gq))
+    return false;
   if (shading == SRN_SHADE_HEAD && n.D != 4) return false;
   if (n.ti && !(n.c == 32 && n.m == 14 && n.F == 16 && n.act == SRN_ACT_SNAKEALT && shading == SRN_SHADE_NONE))
     return false;
@@ -44,7 +50,7 @@ bool render_mma_supported(const NetDev& n, int shading) {
   const bool shape_c = n.c == 48 && n.m == 22 && n.F == 16 && n.act == SRN_ACT_SNAKEALT && shading == SRN_SHADE_NONE;
   const bool shape_d = n.c == 64 && n.m == 30 && n.F == 16 && n.act == SRN_ACT_SNAKEALT && shading == SRN_SHADE_NONE;
   if (!shape_a && !shape_b && !shape_c && !shape_d) return false;
-  const int smem = mma_smem_bytes(n);
+  const int smem = mma_smem_bytes(n, shading);
   if (smem == 0 || smem > 227 * 1024) return false;
   if ((size_t)n.nkey * n.R * n.R * n.R * n.F >= (size_t)1 << 31) return false;
   return n.act == SRN_ACT_SINE || n.act == SRN_ACT_SNAKEALT;

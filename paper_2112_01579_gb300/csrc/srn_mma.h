@@ -9,11 +9,21 @@ namespace srn {
 namespace mma {
 
 
-// Warpgroups per CTA for hidden width C (one CTA per SM): what the shared
-// memory of the A tiles and weight tiles allows.
-constexpr int wgs_for(int C) { return C == 32 ? 6 : (C == 48 ? 4 : 3); }
+// Warpgroups per CTA for hidden width C and shading mode SH (one CTA per
+// SM): what the shared memory of the A tiles and weight tiles and the
+// register file allow.  Width 32 runs 7 (72 registers a thread), except the
+// finite-difference variant, whose extra state needs the 80 registers of 6.
+constexpr int wgs_for(int C, int SH) {
+  return C == 32 ? (SH == SRN_SHADE_FD ? 6 : (SH == SRN_SHADE_ADJOINT ? 4 : 7)) : (C == 48 ? 4 : 3);
+}
+// TMEM columns a CTA allocates, and the columns of one warpgroup: the
+// adjoint variant keeps a 64-column accumulator (the input-gradient MMA has
+// N = 64) plus two 32-column stashes of activation derivatives.
+constexpr int tmem_cols_for(int SH) { return SH == SRN_SHADE_ADJOINT ? 512 : 256; }
+constexpr int tmem_wg_cols(int C, int SH) { return SH == SRN_SHADE_ADJOINT ? 128 : C; }
+constexpr int kAdjMaxLayers = 4;  // layers of the networks the tensor-core adjoint takes
 constexpr int kTile = 128 * 128;       // one A K-atom: 128 rows x 128 B (64 fp16)
-constexpr int kTmemCols = 256;         // >= warpgroups x C FP32 accumulator columns, power of two
+
 constexpr long long kWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
 constexpr int kPoints = 4;             // kernel mode: network output at given points (no ray march)
 
@@ -27,13 +37,13 @@ struct PointsDev {
 
 // ---------------------------------------------------------------- layout
 struct SmemPlan {
-  int oA, oOne, oB0, oBh, oBb, oWl, oTF, oTFinv, oFm, oQp, oMbar, oMisc, total;
+  int oA, oOne, oB0, oBh, oBb, oBhT, oB0T, oWl, oTF, oTFinv, oFm, oQp, oMbar, oMisc, total;
 };
 
 // Shared memory for hidden width C and WGS warpgroups.  An operand row spans
 // ceil(K / 64) K-atoms of 64 FP16 columns; atoms of an A tile are kTile
 // bytes apart, atoms of a B tile C * 128 bytes apart.
-inline SmemPlan make_plan(const NetDev& n, int C, int WGS) {
+inline SmemPlan make_plan(const NetDev& n, int C, int WGS, bool adjoint = false) {
   const int D0 = net_d0(n);
   const int K0 = ((D0 + 2 + 15) / 16) * 16;
   const int NA0 = (K0 + 63) / 64, NAH = (2 * C + 63) / 64, NA = NA0 > NAH ? NA0 : NAH;
@@ -46,6 +56,8 @@ inline SmemPlan make_plan(const NetDev& n, int C, int WGS) {
   s.oB0 = o; o += NA0 * BT;                 // layer 0
   s.oBh = o; o += (n.l - 2) * NAH * BT;     // hidden layers: [W | W]
   s.oBb = o; o += NBB * BT;                 // hidden biases, one 16-column K-block per layer
+  s.oBhT = o; if (adjoint) o += (n.l - 2) * NAH * BT;      // adjoint: [W_h^T | W_h^T] of the hidden layers
+  s.oB0T = o; if (adjoint) o += NAH * (NA0 * 64) * 128;    // adjoint: [W_0^T | W_0^T], K0 rows
   s.oWl = o; o += (n.D * C + 4) * 4;
   o = (o + 15) & ~15;
   s.oTF = o; o += (int)sizeof(TFDev);

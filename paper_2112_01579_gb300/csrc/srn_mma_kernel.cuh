@@ -3,9 +3,9 @@
 //
 // Design (GB300-first restatement of the fused TensorCore network of
 // Section 4.1):
-// * A CTA holds 6, 4 or 3 warpgroups for hidden width 32, 48 or 64 (what
-//   shared memory allows).  Each warpgroup owns a tile of 128 rays, one per
-//   thread; thread i of the warpgroup is row i of the MMA operand A and
+// * A CTA holds 7 (6 with finite-difference shading), 4 or 3 warpgroups for
+//   hidden width 32, 48 or 64 (what shared memory and registers allow).  Each
+//   warpgroup owns a tile of 128 rays, one per thread; thread i of the warpgroup is row i of the MMA operand A and
 //   TMEM lane i of the accumulator, so the per-ray work (ray stepping,
 //   latent-grid trilinear fetch, Fourier features, transfer function,
 //   compositing, early termination) stays one thread per ray as in the paper,
@@ -383,11 +383,71 @@ __device__ __forceinline__ void tmem_ld_row(uint32_t taddr, float (&v)[C]) {
   if constexpr (C % 32 != 0) tmem_ld16(taddr + (C - 16), v + (C - 16));
 }
 
+// Thread's TMEM lane, 32 consecutive FP32 columns written, store waited for.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+      "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};\n\t"
+      "tcgen05.wait::st.sync.aligned;"
+      ::"r"(taddr), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]),
+        "f"(v[8]), "f"(v[9]), "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15]),
+        "f"(v[16]), "f"(v[17]), "f"(v[18]), "f"(v[19]), "f"(v[20]), "f"(v[21]), "f"(v[22]), "f"(v[23]),
+        "f"(v[24]), "f"(v[25]), "f"(v[26]), "f"(v[27]), "f"(v[28]), "f"(v[29]), "f"(v[30]), "f"(v[31])
+      : "memory");
+}
+
+// Gradient with respect to p of sum_c gz[c] z_c(p), z the latent vector
+// (trilinear in p inside the cell chosen by cell_coord, time-blended):
+// sum over corners and keyframes of w_time (gz . g_corner) grad w_corner(p),
+// with d f / d p = R - 1 per axis.
+template <int F>
+__device__ __forceinline__ float3 latent_grad_h(const __half* __restrict__ G, int R, const RayLat& rl, float3 p,
+                                                const float* gz) {
+  int ix, iy, iz;
+  float fx, fy, fz;
+  cell_coord(p.x, R, ix, fx);
+  cell_coord(p.y, R, iy, fy);
+  cell_coord(p.z, R, iz, fz);
+  const int sx = F, sy = R * F, sz = R * R * F;
+  const int base = iz * sz + iy * sy + ix * sx;
+  float3 g = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+    const float wx = dx ? fx : 1.0f - fx, wy = dy ? fy : 1.0f - fy, wz = dz ? fz : 1.0f - fz;
+    const int off = base + dx * sx + dy * sy + dz * sz;
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+      const int gb = kk ? rl.g1 : rl.g0;
+      if (kk && gb < 0) break;
+      float dot = 0.0f;
+#pragma unroll
+      for (int c = 0; c < F; c += 8) {
+        uint4 q = __ldg(reinterpret_cast<const uint4*>(G + gb + off + c));
+        const __half2* h = reinterpret_cast<const __half2*>(&q);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float2 v = __half22float2(h[e]);
+          dot = fmaf(gz[c + 2 * e], v.x, dot);
+          dot = fmaf(gz[c + 2 * e + 1], v.y, dot);
+        }
+      }
+      dot *= kk ? rl.w1 : rl.w0;
+      g.x = fmaf(dot, (dx ? wy : -wy) * wz, g.x);
+      g.y = fmaf(dot, wx * (dy ? wz : -wz), g.y);
+      g.z = fmaf(dot, wx * (dz ? wy : -wy), g.z);
+    }
+  }
+  const float s = (float)(R - 1);
+  return make_float3(s * g.x, s * g.y, s * g.z);
+}
+
 template <int C, int M, int F, int ACT, int SH, int TI, int GQ>
-__global__ void __launch_bounds__(128 * wgs_for(C), 1)
+__global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
     render_mma_kernel(const NetDev net, const BatchDev b, const PointsDev pd, const SmemPlan plan,
                       unsigned long long* __restrict__ ray_counter, unsigned int* __restrict__ status) {
-  constexpr int WGS = wgs_for(C), THREADS = 128 * WGS;
+  constexpr int WGS = wgs_for(C, SH), THREADS = 128 * WGS;
   constexpr int D0 = 3 + 2 * M + F + TI;
   constexpr int K0 = ((D0 + 2 + 15) / 16) * 16;  // inputs + two bias columns
   constexpr int NA0 = (K0 + 63) / 64, NAH = (2 * C + 63) / 64;
@@ -397,6 +457,9 @@ __global__ void __launch_bounds__(128 * wgs_for(C), 1)
   constexpr int NP = SH == SRN_SHADE_FD ? 7 : 1;  // network passes per sample
   constexpr bool POINTS = SH == kPoints;
   constexpr bool SNAKE = ACT == SRN_ACT_SNAKEALT;
+  constexpr bool ADJ = SH == SRN_SHADE_ADJOINT;  // input gradient by backward MMAs (Section 5 "adjoint")
+  constexpr int TMC = tmem_cols_for(SH);
+  static_assert(!ADJ || (C == 32 && K0 <= 64 && TI == 0 && GQ == 0), "tensor-core adjoint: width 32, K0 <= 64");
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -404,6 +467,8 @@ __global__ void __launch_bounds__(128 * wgs_for(C), 1)
   uint8_t* B0 = sm + plan.oB0;
   uint8_t* Bh = sm + plan.oBh;
   uint8_t* Bb = sm + plan.oBb;
+  uint8_t* BhT = sm + plan.oBhT;
+  uint8_t* B0T = sm + plan.oB0T;
   float* wl = reinterpret_cast<float*>(sm + plan.oWl);
   TFDev& tf = *reinterpret_cast<TFDev*>(sm + plan.oTF);
   float* tfinv = reinterpret_cast<float*>(sm + plan.oTFinv);
@@ -479,6 +544,41 @@ __global__ void __launch_bounds__(128 * wgs_for(C), 1)
       *reinterpret_cast<uint4*>(Bb + ((cg + 1) >> 3) * BT + sw_off(o, (cg + 1) & 7)) = make_uint4(0u, 0u, 0u, 0u);
     }
   }
+  if constexpr (ADJ) {
+    // backward B tiles, unscaled FP16 weights, K = 2C (hi and lo halves of
+    // the adjoint row): hidden layer h (1 <= h <= l-2): row n = input n of
+    // the layer, column c -> W_h[c mod C][n]; layer 0: row n = tile input
+    // column n (same order as the forward tile; zero for the bias columns and
+    // the padding), column c -> W_0[c mod C][src(n)].
+    const int rows = (L - 2) * C + K0;
+    for (int it = tid; it < rows; it += THREADS) {
+      const bool in0 = it >= (L - 2) * C;
+      const int h = in0 ? 0 : 1 + it / C;
+      const int n = in0 ? it - (L - 2) * C : it - (h - 1) * C;
+      int src = n;
+      if (in0) {
+        if (n < 2 * M) src = (n & 1) ? 3 + M + (n >> 1) : 3 + (n >> 1);
+        else if (n < 2 * M + 3) src = n - 2 * M;
+        else if (n >= D0) src = -1;
+      }
+      const int din = in0 ? D0 : C;
+      const __half* Wsrc = net.W_h + (in0 ? 0 : (size_t)C * D0 + (size_t)(h - 1) * C * C);
+      uint8_t* Wt = in0 ? B0T : BhT + (h - 1) * NAH * BT;
+      const int atom = in0 ? K0 * 128 : BT;  // bytes of one K-atom of this tile
+      for (int cg = 0; cg < 2 * C / 8; ++cg) {
+        uint32_t w[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int c0 = (8 * cg + 2 * e) % C, c1 = (8 * cg + 2 * e + 1) % C;
+          const __half v0 = src >= 0 ? Wsrc[(size_t)c0 * din + src] : __float2half_rn(0.0f);
+          const __half v1 = src >= 0 ? Wsrc[(size_t)c1 * din + src] : __float2half_rn(0.0f);
+          __half2 hh = __halves2half2(v0, v1);
+          w[e] = *reinterpret_cast<uint32_t*>(&hh);
+        }
+        *reinterpret_cast<uint4*>(Wt + (cg >> 3) * atom + sw_off(n, cg & 7)) = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+    }
+  }
   {
     // last layer on the CUDA cores: folded like the hidden layers
     const __half* Wl = net.W_h + (size_t)C * D0 + (size_t)(L - 2) * C * C;
@@ -514,7 +614,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C), 1)
     misc[4 + wg] = 0;
   }
   if (tid < 32) {
-    tmem_alloc(smem_u32((const void*)&misc[0]), kTmemCols);
+    tmem_alloc(smem_u32((const void*)&misc[0]), TMC);
     tmem_relinquish();
   }
   fence_proxy_async();
@@ -538,11 +638,12 @@ __global__ void __launch_bounds__(128 * wgs_for(C), 1)
   __syncthreads();
   const bool nerf = misc[1] != 0;
   const uint32_t tmem = (uint32_t)misc[0];
-  const uint32_t d_tmem = tmem + (uint32_t)(wg * C);
+  const uint32_t d_tmem = tmem + (uint32_t)(wg * tmem_wg_cols(C, SH));
   const uint32_t t_row = d_tmem + ((uint32_t)((row >> 5) * 32) << 16);  // warp's lane quarter
   uint8_t* A = Aall + wg * NA * kTile;
   const uint32_t a_addr = smem_u32(A), b0_addr = smem_u32(B0), bh_addr = smem_u32(Bh), bb_addr = smem_u32(Bb);
   const uint32_t one_addr = smem_u32(sm + plan.oOne);
+  const uint32_t bht_addr = smem_u32(BhT), b0t_addr = smem_u32(B0T);
   const uint32_t mb = smem_u32(&mbar[wg]);
   const int bar_id = 1 + wg;
 
@@ -623,6 +724,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C), 1)
 
     // ---- layer-0 input of this pass
     float len = 0.f;
+    float3 qs = make_float3(0.f, 0.f, 0.f);  // sample position of this pass
     if (POINTS && active && !failed) {
       write_input_row<M, F, K0, TI, GQ>(A, row, ppos, nerf, fm, net.grid_h, net.grid_q, qp, net.R, rl);
     } else if (active && !failed) {
@@ -640,6 +742,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C), 1)
         if (ax == 2) q.z = clamp01f(q.z + h);
       }
       write_input_row<M, F, K0, TI, GQ>(A, row, q, nerf, fm, net.grid_h, net.grid_q, qp, net.R, rl);
+      qs = q;
     }
     fence_proxy_async();
     tc_fence_before();
@@ -657,6 +760,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C), 1)
 
     // ---- layers: wait, read the accumulator row, activation, next MMA
     float out[4] = {0.f, 0.f, 0.f, 0.f};
+    float dl[C];  // adjoint variant: d out / d (pre-activation) of the current layer
     bool stop = false;
     for (int layer = 0; layer < L - 1; ++layer) {
       // the failure decision is warp-uniform so tcgen05.ld stays convergent;
@@ -686,6 +790,14 @@ __global__ void __launch_bounds__(128 * wgs_for(C), 1)
             }
             *reinterpret_cast<uint4*>(A + a_off(row, j)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
             *reinterpret_cast<uint4*>(A + a_off(row, C / 8 + j)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+          }
+          if constexpr (ADJ) {
+            // activation derivative of this hidden layer, kept in TMEM for the
+            // backward: SnakeAlt' = 0.5 + sin(2x) (the accumulator holds 2x); sin' = cos
+            float dv[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) dv[j] = SNAKE ? 0.5f + __sinf(x[j]) : __cosf(x[j]);
+            tmem_st32(t_row + 64 + 32 * layer, dv);
           }
         }
         fence_proxy_async();
@@ -718,9 +830,117 @@ __global__ void __launch_bounds__(128 * wgs_for(C), 1)
             out[dd] = sacc;
           }
         }
+        if constexpr (ADJ) {
+          // d out / d x of the last hidden layer; wl holds W / 2 for SnakeAlt
+#pragma unroll
+          for (int j = 0; j < C; ++j) dl[j] = SNAKE ? wl[j] * fmaf(2.0f, __sinf(x[j]), 1.0f) : wl[j] * __cosf(x[j]);
+        }
       }
     }
     if (stop) break;
+
+    // ---- adjoint input gradient (Section 5): backward through the hidden
+    // layers and layer 0 on the tensor cores, the adjoint row split into FP16
+    // hi + lo like the activations; then the Fourier and latent Jacobians.
+    float3 gadj = make_float3(0.f, 0.f, 0.f);
+    if constexpr (ADJ) {
+      for (int h = L - 2; h >= 0; --h) {
+        if (!failed) {
+#pragma unroll
+          for (int j = 0; j < C / 8; ++j) {
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float a0 = dl[8 * j + 2 * e], a1 = dl[8 * j + 2 * e + 1];
+              const __half2 hh = __floats2half2_rn(a0, a1);
+              const float2 hb = __half22float2(hh);
+              hi[e] = *reinterpret_cast<const uint32_t*>(&hh);
+              lo[e] = pack_h2(a0 - hb.x, a1 - hb.y);
+            }
+            *reinterpret_cast<uint4*>(A + a_off(row, j)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4*>(A + a_off(row, C / 8 + j)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+          }
+        }
+        fence_proxy_async();
+        tc_fence_before();
+        bar_sync(bar_id, 128);
+        if (misc[4 + wg]) { stop = true; break; }
+        if (row == 0) {
+          tc_fence_after();
+#pragma unroll
+          for (int kk = 0; kk < 2 * C / 16; ++kk) {
+            const uint32_t ka = ((16 * kk) >> 6), kb = ((16 * kk) & 63) * 2;
+            const uint64_t ad = sw128_desc(a_addr + ka * kTile + kb);
+            if (h >= 1)
+              mma_f16(d_tmem, ad, sw128_desc(bht_addr + (h - 1) * NAH * BT + ka * BT + kb), IDESC, kk > 0);
+            else
+              mma_f16(d_tmem, ad, sw128_desc(b0t_addr + ka * (K0 * 128) + kb), idesc_n(K0), kk > 0);
+          }
+          mma_commit(mb);
+        }
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(mb, phase))) {
+          failed = true;
+          misc[4 + wg] = 1;
+        }
+        phase ^= 1u;
+        tc_fence_after();
+        if (failed) continue;
+        if (h >= 1) {
+          float g[32], dv[32];
+          tmem_ld32(t_row, g);
+          tmem_ld32(t_row + 64 + 32 * (h - 1), dv);
+#pragma unroll
+          for (int j = 0; j < C; ++j) dl[j] = g[j] * dv[j];
+        } else {
+          float gv[64];
+          tmem_ld32(t_row, *reinterpret_cast<float(*)[32]>(gv));
+          tmem_ld32(t_row + 32, *reinterpret_cast<float(*)[32]>(gv + 32));
+          if (active) {
+            // position columns, then the Fourier features (d sin e = cos e F_k,
+            // d cos e = -sin e F_k), then the latent vector
+            float3 gp = make_float3(gv[2 * M], gv[2 * M + 1], gv[2 * M + 2]);
+            if (nerf) {
+              constexpr int kReseed = M > 15 ? 4 : 64;
+              constexpr float kW = 6.28318548202514648f, kWErr = 1.74845560252379070e-7f;
+              float sn[3], cs[3];
+              float ga[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+              for (int kq = 0; kq < M; ++kq) {
+                const int a = kq % 3, j = kq / 3;
+                const float pa = a == 0 ? qs.x : (a == 1 ? qs.y : qs.z);
+                if (j % kReseed == 0) {
+                  const float xx = pa * (float)(1 << j);
+                  const float r = rintf(xx);
+                  __sincosf(fmaf(kW, xx - r, kWErr * r), &sn[a], &cs[a]);
+                } else {
+                  const float ss = sn[a], cc = cs[a];
+                  sn[a] = 2.0f * ss * cc;
+                  cs[a] = (cc - ss) * (cc + ss);
+                }
+                ga[a] = fmaf(fm[3 * kq + a], gv[2 * kq] * cs[a] - gv[2 * kq + 1] * sn[a], ga[a]);
+              }
+              gp.x += ga[0];
+              gp.y += ga[1];
+              gp.z += ga[2];
+            } else {
+#pragma unroll
+              for (int kq = 0; kq < M; ++kq) {
+                const float e = fm[3 * kq] * qs.x + fm[3 * kq + 1] * qs.y + fm[3 * kq + 2] * qs.z;
+                float sv, cv;
+                sincosf(e, &sv, &cv);
+                const float coef = gv[2 * kq] * cv - gv[2 * kq + 1] * sv;
+                gp.x = fmaf(coef, fm[3 * kq], gp.x);
+                gp.y = fmaf(coef, fm[3 * kq + 1], gp.y);
+                gp.z = fmaf(coef, fm[3 * kq + 2], gp.z);
+              }
+            }
+            const float3 gl = latent_grad_h<F>(net.grid_h, net.R, rl, qs, gv + 2 * M + 3);
+            gadj = make_float3(gp.x + gl.x, gp.y + gl.y, gp.z + gl.z);
+          }
+        }
+      }
+      if (stop) break;
+    }
 
     if (POINTS) {
       if (active && !failed) {
@@ -748,6 +968,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C), 1)
       } else {
         rho_c = out[0];
         if (SH == SRN_SHADE_HEAD) g = make_float3(out[1], out[2], out[3]);
+        if (ADJ) g = gadj;
       }
       if (sample_done) {
         ++ns;
@@ -775,13 +996,13 @@ __global__ void __launch_bounds__(128 * wgs_for(C), 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (tid < 32) tmem_dealloc(tmem, kTmemCols);
+  if (tid < 32) tmem_dealloc(tmem, TMC);
 }
 
 template <int C, int M, int F, int ACT, int SH, int TI, int GQ>
 cudaError_t launch_t(const NetDev& net, const BatchDev& b, const PointsDev& pd, unsigned long long* ctr,
                      unsigned int* status, cudaStream_t s) {
-  SmemPlan plan = make_plan(net, C, wgs_for(C));
+  SmemPlan plan = make_plan(net, C, wgs_for(C, SH), SH == SRN_SHADE_ADJOINT);
   auto k = render_mma_kernel<C, M, F, ACT, SH, TI, GQ>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total);
   if (e != cudaSuccess) return e;
@@ -791,7 +1012,7 @@ cudaError_t launch_t(const NetDev& net, const BatchDev& b, const PointsDev& pd, 
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  k<<<sms, 128 * wgs_for(C), plan.total, s>>>(net, b, pd, plan, ctr, status);
+  k<<<sms, 128 * wgs_for(C, SH), plan.total, s>>>(net, b, pd, plan, ctr, status);
   return cudaGetLastError();
 }
 

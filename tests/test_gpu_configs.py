@@ -33,10 +33,10 @@ def _render(S, net, cams, tf, W, Hh, step, et, shading=0, fd_h=0.0, times=None):
     return out
 
 
-@pytest.mark.parametrize("shading,precision", [(1, 0), (2, 1), (3, 1)])
+@pytest.mark.parametrize("shading,precision", [(1, 0), (1, 1), (2, 1), (3, 1)])
 def test_shaded_workload_full_size(srn, shading, precision):
     """64^3 x 16 latent grid, 4 SnakeAlt layers of width 32, 1024^2 at step
-    1/1024, headlight Blinn-Phong from the adjoint (FP32 path), central
+    1/1024, headlight Blinn-Phong from the adjoint (FP32 or FP16 path), central
     differences with a one-voxel step of the 512^3 volume (FP16 path) or the
     4-output head (FP16 path)."""
     S = srn

@@ -113,7 +113,7 @@ def test_mma_matches_fp32_path_sample_count(srn):
     assert np.abs(a - b).max() <= H.TOL_FP16_IMG
 
 
-@pytest.mark.parametrize("shading", [2, 3])
+@pytest.mark.parametrize("shading", [1, 2, 3])
 def test_mma_shading(srn, shading):
     S = srn
     net, q = _net16(S, H.cfg2_params(seed=26, R=16, out_dim=4 if shading == 3 else 1))
@@ -123,9 +123,45 @@ def test_mma_shading(srn, shading):
     ref, _, _ = oracle.render(oracle.OracleNet(q), cams, H.oracle_tf(tf), 32, 24, 1 / 64, 2.0, shading=shading,
                               fd_h=1 / 64)
     err = np.abs(got[0] - ref[0]).max()
-    # FD divides FP16-path density differences by 2h: its error scales by 1/h
+    # FD divides FP16-path density differences by 2h: its error scales by 1/h;
+    # the adjoint normal carries the FP16 rounding of the layer-0 inputs into
+    # the specular term (exponent 32)
     tol = H.TOL_FP16_IMG if shading == 3 else 5 * H.TOL_FP16_IMG
     assert err <= tol, err
+
+
+@pytest.mark.parametrize("shape", ["cfg1_sine_l2", "snake_l3"])
+def test_mma_adjoint_shapes(srn, shape):
+    """The tensor-core adjoint (backward MMAs through W_h^T and W_0^T) on the
+    other instantiated shapes: 12 Fourier rows / 8 channels with sine and two
+    layers (no hidden backward), and three SnakeAlt layers (one)."""
+    S = srn
+    if shape == "cfg1_sine_l2":
+        p = H.cfg1_params(seed=27)
+    else:
+        p = synth.random_params(R=12, F=16, m=14, layers=3, width=32, act=synth.ACT_SNAKEALT, seed=28,
+                                grid_std=0.5, bias_std=0.2)
+    net, q = _net16(S, p)
+    tf = synth.tf_preset(8)
+    cams = synth.orbit_cameras(2)
+    got, _ = _render(S, net, cams, tf, 40, 28, 1 / 64, 2.0, shading=1)
+    ref, _, _ = oracle.render(oracle.OracleNet(q), cams, H.oracle_tf(tf), 40, 28, 1 / 64, 2.0, shading=1)
+    err = np.abs(got[0] - ref[0]).max()
+    assert err <= 5 * H.TOL_FP16_IMG, err
+
+
+def test_mma_adjoint_limits(srn):
+    """Five layers (three stashed derivative blocks) or a 4-output network:
+    the tensor-core adjoint refuses with SRN_ERR_UNSUPPORTED."""
+    import torch
+    S = srn
+    out = torch.zeros((1, 1, 8, 8, 4), device="cuda")
+    for p in (synth.random_params(R=8, F=16, m=14, layers=5, width=32, act=synth.ACT_SNAKEALT, seed=29),
+              H.cfg2_params(seed=30, R=8, out_dim=4)):
+        net, _ = _net16(S, p)
+        with pytest.raises(S.SrnError) as e:
+            S.srn_render(net.ctx, synth.orbit_cameras(1), synth.tf_preset(4), S.render_desc(8, 8, 0.01, 2.0, 1), out)
+        assert e.value.status == S.SRN_ERR_UNSUPPORTED
 
 
 def test_mma_time_batch(srn):
