@@ -91,7 +91,7 @@ __device__ __forceinline__ void accumulate_layer(float* sacc, const float* sdelt
 }
 
 template <int C>
-__global__ void __launch_bounds__(kFitThreads) fit_point_kernel(const NetDev net, const PointArgs a, const Layout L) {
+__global__ void __launch_bounds__(kFitThreads, 4) fit_point_kernel(const NetDev net, const PointArgs a, const Layout L) {
   extern __shared__ float4 smem4[];
   float* sm = reinterpret_cast<float*>(smem4);
   const int dstr_d = C + 1, dstr_v = a.dstride;

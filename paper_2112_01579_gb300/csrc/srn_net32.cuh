@@ -93,14 +93,21 @@ __device__ __forceinline__ float dotrow(const float* __restrict__ row, const flo
 }
 
 // Eq. 3 SnakeAlt(x) = 0.5 x + sin^2 x, or sin(x); and their derivatives.
+// Out-of-line sin / cos: the accurate functions carry a large argument-
+// reduction path, and inlined once per hidden unit of the unrolled layers
+// they overflow the instruction cache (the fit kernel stalled mostly on
+// instruction fetch).
+static __device__ __noinline__ void sincos_call(float x, float* s, float* c) { sincosf(x, s, c); }
+static __device__ __noinline__ float sin_call(float x) { return sinf(x); }
+
 __device__ __forceinline__ float act_f(int act, float x) {
-  float s = sinf(x);
+  float s = sin_call(x);
   return act == SRN_ACT_SNAKEALT ? fmaf(0.5f, x, s * s) : s;
 }
 // Activation value and derivative from one sin/cos evaluation.
 __device__ __forceinline__ void act_and_df(int act, float x, float& a, float& d) {
   float s, c;
-  sincosf(x, &s, &c);
+  sincos_call(x, &s, &c);
   if (act == SRN_ACT_SNAKEALT) {
     a = fmaf(0.5f, x, s * s);
     d = 0.5f + 2.0f * s * c;
