@@ -251,34 +251,41 @@ __global__ void __launch_bounds__(kFitThreads, 4) fit_point_kernel(const NetDev 
 }
 
 // ---------------------------------------------------------------- radix sort
+// Digit counts of one sort block (8 warps x 8 rounds x 32 keys) per warp:
+// equal digits within a round are grouped with __match_any_sync.  NB bins.
+template <int NB>
 __device__ __forceinline__ void warp_digit_counts(const unsigned int* __restrict__ keys, int n, int shift,
-                                                  unsigned int (*cnt)[256]) {
+                                                  unsigned int (*cnt)[NB]) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int base = blockIdx.x * kSortItems + w * 256;
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
     const int i = base + r * 32 + lane;
     const bool valid = i < n;
-    const unsigned int d = valid ? (keys[i] >> shift) & 255u : 0xFFFFFFFFu;
+    const unsigned int d = valid ? (keys[i] >> shift) & (unsigned)(NB - 1) : 0xFFFFFFFFu;
     const unsigned int peers = __match_any_sync(0xffffffffu, d);
     if (valid && lane == __ffs(peers) - 1) cnt[w][d] += __popc(peers);
     __syncwarp();
   }
 }
 
+// hist[d * nblocks + block] = count of digit d in the block (digit-major, so
+// one exclusive scan gives every (digit, block) its output offset).
+template <int NB>
 __global__ void __launch_bounds__(kSortThreads) sort_hist_kernel(const unsigned int* __restrict__ keys, int n,
                                                                  int shift, unsigned int* __restrict__ hist,
                                                                  int nblocks) {
-  __shared__ unsigned int cnt[8][256];
-  for (int i = threadIdx.x; i < 8 * 256; i += kSortThreads) (&cnt[0][0])[i] = 0;
+  __shared__ unsigned int cnt[8][NB];
+  for (int i = threadIdx.x; i < 8 * NB; i += kSortThreads) (&cnt[0][0])[i] = 0;
   __syncthreads();
-  warp_digit_counts(keys, n, shift, cnt);
+  warp_digit_counts<NB>(keys, n, shift, cnt);
   __syncthreads();
-  const int d = threadIdx.x;
-  unsigned int t = 0;
+  for (int d = threadIdx.x; d < NB; d += kSortThreads) {
+    unsigned int t = 0;
 #pragma unroll
-  for (int w = 0; w < 8; ++w) t += cnt[w][d];
-  hist[(size_t)d * nblocks + blockIdx.x] = t;
+    for (int w = 0; w < 8; ++w) t += cnt[w][d];
+    hist[(size_t)d * nblocks + blockIdx.x] = t;
+  }
 }
 
 // Exclusive scan of m counts in place by one block: tiles of 8192 values are
@@ -344,19 +351,19 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(unsigned int* __rest
   }
 }
 
+template <int NB>
 __global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(const unsigned int* __restrict__ kin,
                                                                     const unsigned int* __restrict__ vin,
                                                                     unsigned int* __restrict__ kout,
                                                                     unsigned int* __restrict__ vout, int n, int shift,
                                                                     const unsigned int* __restrict__ scanned,
                                                                     int nblocks) {
-  __shared__ unsigned int cnt[8][256];
-  for (int i = threadIdx.x; i < 8 * 256; i += kSortThreads) (&cnt[0][0])[i] = 0;
+  __shared__ unsigned int cnt[8][NB];
+  for (int i = threadIdx.x; i < 8 * NB; i += kSortThreads) (&cnt[0][0])[i] = 0;
   __syncthreads();
-  warp_digit_counts(kin, n, shift, cnt);
+  warp_digit_counts<NB>(kin, n, shift, cnt);
   __syncthreads();
-  {
-    const int d = threadIdx.x;
+  for (int d = threadIdx.x; d < NB; d += kSortThreads) {
     unsigned int base = scanned[(size_t)d * nblocks + blockIdx.x];
 #pragma unroll
     for (int w = 0; w < 8; ++w) {
@@ -373,7 +380,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(const unsign
     const int i = base + r * 32 + lane;
     const bool valid = i < n;
     const unsigned int k = valid ? kin[i] : 0u;
-    const unsigned int d = valid ? (k >> shift) & 255u : 0xFFFFFFFFu;
+    const unsigned int d = valid ? (k >> shift) & (unsigned)(NB - 1) : 0xFFFFFFFFu;
     const unsigned int peers = __match_any_sync(0xffffffffu, d);
     const unsigned int rank = __popc(peers & ((1u << lane) - 1u));
     if (valid) {
@@ -628,10 +635,20 @@ cudaError_t run_backward(FitScratch& s, const NetDev& net, PointArgs pa, float* 
   int bits = 1;
   while (((size_t)1 << bits) < s.n_cells) ++bits;
   const int nblocks = (n + kSortItems - 1) / kSortItems;
-  for (int shift = 0; shift < bits && n > 0; shift += 8) {
-    sort_hist_kernel<<<nblocks, kSortThreads, 0, st>>>(k_in, n, shift, s.hist, nblocks);
-    scan_kernel<<<1, kScanThreads, 0, st>>>(s.hist, 256 * nblocks);
-    sort_scatter_kernel<<<nblocks, kSortThreads, 0, st>>>(k_in, v_in, k_out, v_out, n, shift, s.hist, nblocks);
+  // 9-bit digits when the cell index fits one (one pass for grids up to 8^3
+  // cells), else 8-bit digits
+  const int dbits = s.radix_bins == 512 && bits <= 9 ? 9 : 8;
+  for (int shift = 0; shift < bits && n > 0; shift += dbits) {
+    if (dbits == 9) {
+      sort_hist_kernel<512><<<nblocks, kSortThreads, 0, st>>>(k_in, n, shift, s.hist, nblocks);
+      scan_kernel<<<1, kScanThreads, 0, st>>>(s.hist, 512 * nblocks);
+      sort_scatter_kernel<512><<<nblocks, kSortThreads, 0, st>>>(k_in, v_in, k_out, v_out, n, shift, s.hist, nblocks);
+    } else {
+      sort_hist_kernel<256><<<nblocks, kSortThreads, 0, st>>>(k_in, n, shift, s.hist, nblocks);
+      scan_kernel<<<1, kScanThreads, 0, st>>>(s.hist, 256 * nblocks);
+      sort_scatter_kernel<256><<<nblocks, kSortThreads, 0, st>>>(k_in, v_in, k_out, v_out, n, shift, s.hist,
+                                                                 nblocks);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     std::swap(k_in, k_out);
     std::swap(v_in, v_out);
@@ -729,7 +746,8 @@ cudaError_t fit_scratch_alloc(FitScratch& s, const NetDev& net, int max_points) 
   alloc((void**)&s.key_alt, sizeof(unsigned int) * n);
   alloc((void**)&s.idx, sizeof(unsigned int) * n);
   alloc((void**)&s.idx_alt, sizeof(unsigned int) * n);
-  alloc((void**)&s.hist, sizeof(unsigned int) * 256 * nsb);
+  s.radix_bins = sort_bins(s.n_cells);
+  alloc((void**)&s.hist, sizeof(unsigned int) * s.radix_bins * nsb);
   alloc((void**)&s.cell_start, sizeof(unsigned int) * (s.n_cells + 1));
   alloc((void**)&s.part, sizeof(float) * (size_t)s.max_cta * (s.n_entries + 1));
   alloc((void**)&s.grads, sizeof(float) * (s.n_grid + s.n_entries));
@@ -745,6 +763,8 @@ void fit_scratch_free(FitScratch& s) {
     if (p) cudaFree(p);
   memset(&s, 0, sizeof(s));
 }
+
+int sort_bins(size_t n_cells) { return n_cells <= 512 ? 512 : 256; }
 
 bool fit_supported(const NetDev& net) {
   return net.c == 32 && (net.F == 4 || net.F == 8 || net.F == 16 || net.F == 32) && net.l <= kMaxL;

@@ -12,6 +12,7 @@ struct FitScratch {
   size_t n_cells;          // (R-1)^3 latent-grid cells
   size_t n_entries;        // weights + biases
   size_t n_grid;           // latent-grid entries over all keyframes
+  int radix_bins;          // 256 (8-bit digits) or 512 (one 9-bit pass for up to 512 cells)
   float* pts;              // [n][3] positions (clamped) of the current step
   float* dz;               // [n][F] adjoint of the latent vector
   unsigned int* key;       // [n] cell of each point, and radix ping-pong
@@ -47,6 +48,8 @@ struct FitArgs {
 };
 
 bool fit_supported(const NetDev& net);
+// Radix bins of the cell sort: 512 (one 9-bit pass) for up to 512 cells, else 256.
+int sort_bins(size_t n_cells);
 cudaError_t fit_scratch_alloc(FitScratch& s, const NetDev& net, int max_points);
 void fit_scratch_free(FitScratch& s);
 cudaError_t launch_backward(FitScratch& s, const NetDev& net, const float* pts, int n, float time, const float* dout,
