@@ -288,21 +288,45 @@ __global__ void __launch_bounds__(kSortThreads) sort_hist_kernel(const unsigned 
   }
 }
 
-// Exclusive scan of m counts in place by one block: tiles of 8192 values are
-// staged coalesced in shared memory, each thread scans 8 consecutive values,
-// and a block-wide scan of the thread sums plus a running carry links the
-// tiles.  Fixed order, so deterministic.
+// Exclusive scan of m counts in place, in segments of `seg` values, one block
+// per segment: tiles of 8192 values are staged coalesced in shared memory,
+// each thread scans 8 consecutive values, and a block-wide scan of the thread
+// sums plus a running carry links the tiles.  Segment b starts from
+// carry_in[b] (the exclusive scan of the segment sums; 0 when carry_in is
+// null).  Integer sums in a fixed order, so deterministic.
 constexpr int kScanThreads = 1024, kScanPer = 8, kScanTile = kScanThreads * kScanPer;
-__global__ void __launch_bounds__(kScanThreads) scan_kernel(unsigned int* __restrict__ a, int m) {
+
+// sums[b] = sum of segment b of a.
+__global__ void __launch_bounds__(kScanThreads) seg_sum_kernel(const unsigned int* __restrict__ a, int m, int seg,
+                                                               unsigned int* __restrict__ sums) {
+  __shared__ unsigned int wsum[32];
+  const int b0 = blockIdx.x * seg, b1 = min(m, b0 + seg);
+  unsigned int t = 0;
+  for (int i = b0 + threadIdx.x; i < b1; i += kScanThreads) t += a[i];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    unsigned int w = wsum[threadIdx.x];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) w += __shfl_xor_sync(0xffffffffu, w, off);
+    if (threadIdx.x == 0) sums[blockIdx.x] = w;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_kernel(unsigned int* __restrict__ a, int m, int seg,
+                                                            const unsigned int* __restrict__ carry_in) {
   __shared__ unsigned int tile[kScanTile + kScanTile / 32];  // padded: 8-strided reads stay conflict-free
   __shared__ unsigned int part[32];
   __shared__ unsigned int carry_s;
   const int tid = threadIdx.x;
-  if (tid == 0) carry_s = 0;
-  for (int base = 0; base < m; base += kScanTile) {
+  const int s0 = blockIdx.x * seg, s1 = min(m, s0 + seg);
+  if (tid == 0) carry_s = carry_in ? carry_in[blockIdx.x] : 0u;
+  for (int base = s0; base < s1; base += kScanTile) {
     for (int i = tid; i < kScanTile; i += kScanThreads) {
       const int g = base + i;
-      tile[i + i / 32] = g < m ? a[g] : 0u;
+      tile[i + i / 32] = g < s1 ? a[g] : 0u;
     }
     __syncthreads();
     unsigned int v[kScanPer], s = 0;
@@ -344,7 +368,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(unsigned int* __rest
     __syncthreads();
     for (int i = tid; i < kScanTile; i += kScanThreads) {
       const int g = base + i;
-      if (g < m) a[g] = tile[i + i / 32];
+      if (g < s1) a[g] = tile[i + i / 32];
     }
     if (tid == kScanThreads - 1) carry_s += incl;
     __syncthreads();
@@ -638,17 +662,24 @@ cudaError_t run_backward(FitScratch& s, const NetDev& net, PointArgs pa, float* 
   // 9-bit digits when the cell index fits one (one pass for grids up to 8^3
   // cells), else 8-bit digits
   const int dbits = s.radix_bins == 512 && bits <= 9 ? 9 : 8;
+  const int hist_m = (1 << dbits) * nblocks;
+  const int nseg = (hist_m + kScanTile - 1) / kScanTile;  // one 8192-value tile per scan block
+  unsigned int* seg_sums = s.hist + (size_t)s.radix_bins * (size_t)((s.max_points + kSortItems - 1) / kSortItems);
   for (int shift = 0; shift < bits && n > 0; shift += dbits) {
-    if (dbits == 9) {
-      sort_hist_kernel<512><<<nblocks, kSortThreads, 0, st>>>(k_in, n, shift, s.hist, nblocks);
-      scan_kernel<<<1, kScanThreads, 0, st>>>(s.hist, 512 * nblocks);
-      sort_scatter_kernel<512><<<nblocks, kSortThreads, 0, st>>>(k_in, v_in, k_out, v_out, n, shift, s.hist, nblocks);
+    if (dbits == 9) sort_hist_kernel<512><<<nblocks, kSortThreads, 0, st>>>(k_in, n, shift, s.hist, nblocks);
+    else sort_hist_kernel<256><<<nblocks, kSortThreads, 0, st>>>(k_in, n, shift, s.hist, nblocks);
+    if (nseg > 1) {
+      seg_sum_kernel<<<nseg, kScanThreads, 0, st>>>(s.hist, hist_m, kScanTile, seg_sums);
+      scan_kernel<<<1, kScanThreads, 0, st>>>(seg_sums, nseg, nseg, nullptr);
+      scan_kernel<<<nseg, kScanThreads, 0, st>>>(s.hist, hist_m, kScanTile, seg_sums);
     } else {
-      sort_hist_kernel<256><<<nblocks, kSortThreads, 0, st>>>(k_in, n, shift, s.hist, nblocks);
-      scan_kernel<<<1, kScanThreads, 0, st>>>(s.hist, 256 * nblocks);
+      scan_kernel<<<1, kScanThreads, 0, st>>>(s.hist, hist_m, hist_m, nullptr);
+    }
+    if (dbits == 9)
+      sort_scatter_kernel<512><<<nblocks, kSortThreads, 0, st>>>(k_in, v_in, k_out, v_out, n, shift, s.hist, nblocks);
+    else
       sort_scatter_kernel<256><<<nblocks, kSortThreads, 0, st>>>(k_in, v_in, k_out, v_out, n, shift, s.hist,
                                                                  nblocks);
-    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     std::swap(k_in, k_out);
     std::swap(v_in, v_out);
@@ -747,7 +778,8 @@ cudaError_t fit_scratch_alloc(FitScratch& s, const NetDev& net, int max_points) 
   alloc((void**)&s.idx, sizeof(unsigned int) * n);
   alloc((void**)&s.idx_alt, sizeof(unsigned int) * n);
   s.radix_bins = sort_bins(s.n_cells);
-  alloc((void**)&s.hist, sizeof(unsigned int) * s.radix_bins * nsb);
+  // radix histograms, then the per-segment sums of their scan
+  alloc((void**)&s.hist, sizeof(unsigned int) * (s.radix_bins * nsb + (s.radix_bins * nsb) / 8192 + 1));
   alloc((void**)&s.cell_start, sizeof(unsigned int) * (s.n_cells + 1));
   alloc((void**)&s.part, sizeof(float) * (size_t)s.max_cta * (s.n_entries + 1));
   alloc((void**)&s.grads, sizeof(float) * (s.n_grid + s.n_entries));
