@@ -21,6 +21,7 @@ import csv
 import json
 import math
 import os
+import platform
 import re
 import subprocess
 import sys
@@ -594,8 +595,33 @@ def cpu_baseline(params, vol_np, tf, cams, budget_rows=16):
     _, _, ns = oracle.render(on, cams[:1], otf, W_IMG, H_IMG, STEP, ET, pixels=pix)
     dt = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": ns / dt, "unit": "network samples/s", "cores": cores, "kind": "oracle",
-            "sample": f"{len(rows)} of {H_IMG} rows of one {W_IMG}x{H_IMG} frame ({ns} samples, {dt:.1f} s)"}
+    res = {"value": ns / dt, "unit": "network samples/s", "cores": cores, "kind": "oracle",
+           "sample": f"{len(rows)} of {H_IMG} rows of one {W_IMG}x{H_IMG} frame ({ns} samples, {dt:.1f} s)",
+           "cpu": _cpu_model()}
+    # one thread on two of those rows (OpenMP team size set through the runtime the oracle links)
+    try:
+        import ctypes
+        gomp = ctypes.CDLL("libgomp.so.1")
+        gomp.omp_set_num_threads(1)
+        t0 = time.perf_counter()
+        _, _, ns1 = oracle.render(on, cams[:1], otf, W_IMG, H_IMG, STEP, ET, pixels=pix[:2 * W_IMG])
+        res["single_thread_value"] = ns1 / (time.perf_counter() - t0)
+        gomp.omp_set_num_threads(cores)
+    except OSError:
+        res["single_thread_value"] = None
+    return res
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "hardware", "cpu part"):
+                    return f"{platform.machine()} {line.split(':', 1)[1].strip()}"
+    except OSError:
+        pass
+    return platform.machine()
 
 
 # Algorithmic work of one network sample of the render network (47 -> 32 ->

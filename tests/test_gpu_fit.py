@@ -29,13 +29,18 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-30))
 
 
-@pytest.mark.parametrize("shape", ["cfg1", "cfg2", "head", "time", "dense_cells"])
+@pytest.mark.parametrize("shape", ["cfg1", "cfg2", "head", "time", "dense_cells", "large_9bit", "large_8bit"])
 def test_backward_matches_oracle(srn, shape):
     import torch
     S = srn
     t = 0.0
     n = 3001  # ragged against the 128-point CTAs and the 2048-key sort blocks
-    if shape == "dense_cells":
+    if shape in ("large_9bit", "large_8bit"):
+        # 100,003 points: the histogram scan runs in several blocks; 7^3 cells
+        # sort in one 9-bit pass, 15^3 cells in two 8-bit passes
+        p = H.cfg1_params(seed=37) if shape == "large_9bit" else H.cfg2_params(seed=38, R=16)
+        n = 100003
+    elif shape == "dense_cells":
         # >= 32 points per cell: the (cell, corner)-parallel latent-gradient pass
         p = synth.random_params(R=6, F=16, m=14, layers=3, width=32, act=synth.ACT_SNAKEALT, seed=36,
                                 grid_std=0.5, n_keyframes=2, key_times=[0.0, 1.0])
