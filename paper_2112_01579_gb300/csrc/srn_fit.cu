@@ -629,7 +629,7 @@ int sm_count() {
 // (all keyframes) to dgrid, weights / biases to dW / db, the loss (fit) to
 // loss.
 cudaError_t run_backward(FitScratch& s, const NetDev& net, PointArgs pa, float* dgrid, float* dW, float* db,
-                         float* loss, cudaStream_t st) {
+                         float* loss, cudaStream_t st, unsigned int* mma_status = nullptr) {
   const int n = pa.n;
   const int nW = (int)(net_weight_count(net)), nb = (int)net_bias_count(net);
   Layout L = make_layout(net, true);
@@ -642,12 +642,20 @@ cudaError_t run_backward(FitScratch& s, const NetDev& net, PointArgs pa, float* 
   pa.key = s.key;
   pa.idx = s.idx;
   pa.part = s.part;
-  const int n_cta = std::min(s.max_cta, (n + kFitThreads - 1) / kFitThreads);
+  int n_cta = std::min(s.max_cta, (n + kFitThreads - 1) / kFitThreads);
   size_t smem = sizeof(float) * ((size_t)L.total + kFitThreads * (net.c + 1) + (size_t)kFitThreads * dstride +
                                  ((pa.n_entries + 3) & ~3) + kFitThreads);
   cudaError_t e = cudaMemsetAsync(s.flag, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return e;
-  if (n_cta > 0) {
+  if (pa.mode == 0 && n > 0 && mma_status && fit_mma_supported(net) && s.max_cta >= fit_mma_rows_per_cta()) {
+    // tensor-core point kernel: one partial row per warpgroup
+    const int rows = fit_mma_rows_per_cta();
+    const int grid = std::max(1, std::min({sm_count(), s.max_cta / rows, (n + 128 * rows - 1) / (128 * rows)}));
+    PointArgsMma ma{n, pa.seed, pa.step, pa.time, pa.vol, pa.cdf, pa.cdf_res, s.pts, s.dz, s.key, s.idx, s.part};
+    e = launch_fit_mma(net, ma, grid, mma_status, st);
+    if (e != cudaSuccess) return e;
+    n_cta = grid * rows;
+  } else if (n_cta > 0) {
     auto k = fit_point_kernel<32>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -828,7 +836,7 @@ cudaError_t launch_fit_step(FitScratch& s, const NetDev& net, const FitArgs& a, 
   pa.cdf = a.cdf;
   pa.cdf_res = a.cdf_res;
   const size_t ng = s.n_grid, nW = net_weight_count(net), nb = net_bias_count(net);
-  cudaError_t e = run_backward(s, net, pa, s.grads, s.grads + ng, s.grads + ng + nW, a.loss, st);
+  cudaError_t e = run_backward(s, net, pa, s.grads, s.grads + ng, s.grads + ng + nW, a.loss, st, a.status);
   if (e != cudaSuccess) return e;
   const size_t n = ng + nW + nb;
   unsigned int blocks = (unsigned int)std::min<size_t>((n + 255) / 256, (size_t)sm_count() * 8);

@@ -56,6 +56,27 @@ cudaError_t launch_backward(FitScratch& s, const NetDev& net, const float* pts, 
                             float* dgrid, float* dW, float* db, cudaStream_t st);
 cudaError_t launch_fit_step(FitScratch& s, const NetDev& net, const FitArgs& a, cudaStream_t st);
 
+// Tensor-core point kernel of the fit (srn_fit_mma.cu): arguments, support
+// (width 32, two layers, density output, no time input, 12 Fourier rows / 8
+// channels or 14 / 16), partial rows written per CTA.
+struct PointArgsMma {
+  int n;
+  unsigned long long seed;
+  int step;
+  float time;
+  VolDev vol;
+  const unsigned long long* cdf;
+  int cdf_res;
+  float* pts;
+  float* dz;
+  unsigned int* key;
+  unsigned int* idx;
+  float* part;
+};
+bool fit_mma_supported(const NetDev& n);
+int fit_mma_rows_per_cta();
+cudaError_t launch_fit_mma(const NetDev& n, const PointArgsMma& a, int grid, unsigned int* status, cudaStream_t st);
+
 // Section 6.2 adaptive resampling (srn_adaptive.cu).
 // Error grid E[res^3]: mean |net(p) - V(p)| over spv positions per voxel.
 cudaError_t launch_error_grid(const NetDev& net, const VolDev& vol, int res, int spv, unsigned long long seed,

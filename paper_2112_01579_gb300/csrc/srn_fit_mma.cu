@@ -1,0 +1,461 @@
+// Tensor-core point kernel of the fit (Section 5 world-space training) for
+// two-layer networks of width 32 with a density output: forward, loss,
+// backward and the layer-0 weight gradient on tcgen05 MMAs; the rest of the
+// fit step (cell sort, latent-grid gradient, reductions, Adam) is shared with
+// the FP32 path in srn_fit.cu.
+//
+// A warpgroup takes 128 points at a time, one per thread (thread = MMA row =
+// TMEM lane), from a fixed, static assignment of point tiles:
+// * forward: the thread writes its layer-0 input row v0 = [sin/cos, p, z, 1, 1]
+//   as FP16 blocks [v hi | v lo | v hi] (v = hi + lo to ~2^-22); one MMA
+//   against [W hi | W hi | W lo] (the FP32 master weights split the same
+//   way) gives x1 = W0 v0 + b0 in TMEM, FP32-accurate (the bias as FP16
+//   hi + lo weights of the two constant columns);
+// * the thread reads x1, applies the activation and its derivative (MUFU
+//   sin/cos), evaluates the last layer and the L1 loss in FP32, and forms
+//   delta = dL/dx1 = sign(r)/n * w_last * a'(x1);
+// * backward to the latent vector: dz = W0_z^T delta in FP32 on the CUDA
+//   cores (it feeds the latent-grid gradient, a sum with strong
+//   cancellation, so it keeps FP32 accuracy), overlapping the MMA below;
+// * weight gradient of layer 0: dW0^T = sum over points of v0 delta^T is an
+//   MMA with K = points: the thread also writes its v0 (hi, lo) and delta
+//   (hi, lo) as columns of two transposed tiles, and one M = 128 (v0 hi rows,
+//   v0 lo rows) x N = 64 (delta hi, delta lo) MMA per tile accumulates all
+//   four products in TMEM across the warpgroup's tiles.  The bias gradient
+//   of layer 0 is the row of the constant-1 column.
+// * last-layer gradients and the loss are warp reductions in a fixed order.
+// Each warpgroup writes one partial row [W | b | loss], reduced with the FP32
+// path's rows by the same fixed-order kernel: the step is deterministic.
+#include "srn_fit.h"
+#include "srn_mma_kernel.cuh"
+#include "srn_net32.cuh"
+#include "srn_sample.cuh"
+
+namespace srn {
+namespace {
+
+using namespace mma;
+
+constexpr int kFitWGS = 2;              // warpgroups per CTA (shared memory: ~222 KB)
+constexpr int kFitTmemCols = 256;       // per warpgroup: 64 forward / dz + 64 dW0 accumulator columns
+constexpr int kFitWgCols = 128;
+
+struct FitPlan {
+  int oAf, oAt, oBt, oB0, oWz, oWl, oFm, oSlot, oMbar, oMisc, total;
+};
+
+FitPlan fit_plan(int m, int F) {
+  FitPlan p;
+  int o = 0;
+  p.oAf = o; o += kFitWGS * 3 * kTile;          // input rows [hi | lo | hi] (128 x 192 FP16)
+  p.oAt = o; o += kFitWGS * 2 * kTile;          // v0^T: 128 rows (hi, lo features) x 128 points
+  p.oBt = o; o += kFitWGS * 2 * 64 * 128;       // delta^T: 64 rows (hi, lo) x 128 points
+  p.oB0 = o; o += 3 * 32 * 128;                 // [W hi | W hi | W lo]: 32 rows x 192 columns
+  p.oWz = o; o += F * 32 * 4;                    // FP32 latent columns of W0, [F][32]
+  p.oWl = o; o += 64 * 4;
+  p.oFm = o; o += ((3 * m + 3) & ~3) * 4 + 16;
+  p.oSlot = o; o += kFitWGS * 4 * 34 * 4;       // per warp: dW_last[32], db_last, spare
+  o = (o + 7) & ~7;
+  p.oMbar = o; o += 8 * kFitWGS;
+  p.oMisc = o; o += 16 * 4;
+  p.total = o + 1024;
+  return p;
+}
+
+__device__ __forceinline__ uint32_t h16(float v) {
+  const __half h = __float2half_rn(v);
+  return (uint32_t)__half_as_ushort(h);
+}
+
+// K-major, 128B-swizzled tile element (row r, column k) byte offset; atoms of
+// 64 columns are `atom` bytes apart.
+__device__ __forceinline__ uint32_t kel(int r, int k, int atom) {
+  return (uint32_t)((k >> 6) * atom) + sw_off(r, (k & 63) >> 3) + (uint32_t)((k & 7) * 2);
+}
+
+template <int M, int F, int ACT>
+__global__ void __launch_bounds__(128 * kFitWGS, 1)
+    fit_mma_kernel(const NetDev net, const PointArgsMma a, const FitPlan plan, unsigned int* __restrict__ status) {
+  constexpr int C = 32;
+  constexpr int D0 = 3 + 2 * M + F;
+  static_assert(D0 + 2 <= 64, "layer-0 input (with the two bias columns) must fit 64 columns");
+  constexpr bool SNAKE = ACT == SRN_ACT_SNAKEALT;
+  constexpr int ATOM_T = 64 * 128;  // bytes of a delta^T K-atom (64 rows)
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  float* wl = reinterpret_cast<float*>(sm + plan.oWl);
+  float* fm = reinterpret_cast<float*>(sm + plan.oFm);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + plan.oMbar);
+  volatile int* misc = reinterpret_cast<volatile int*>(sm + plan.oMisc);  // [0] tmem base, [1] nerf, [4+wg] fail
+
+  const int tid = threadIdx.x;
+  const int wg = tid >> 7, row = tid & 127, lane = tid & 31, warp = row >> 5;
+  uint8_t* Af = sm + plan.oAf + wg * 3 * kTile;
+  uint8_t* At = sm + plan.oAt + wg * 2 * kTile;
+  uint8_t* Bt = sm + plan.oBt + wg * 2 * ATOM_T;
+  uint8_t* B0 = sm + plan.oB0;
+  float* wz = reinterpret_cast<float*>(sm + plan.oWz);
+  float* slot = reinterpret_cast<float*>(sm + plan.oSlot) + (wg * 4 + warp) * 34;
+  float* ex = reinterpret_cast<float*>(Af);  // after the last tile: exchange rows (64 x 33) + 4 loss words
+
+  // ---- stage the FP32 master weights of layer 0 split into FP16 hi + lo.
+  // B0 row o: blocks [W hi | W hi | W lo] of 64 columns in the input tile's
+  // order; block 0 also carries the bias hi / lo in columns D0, D0+1.
+  for (int r = tid; r < C; r += 128 * kFitWGS) {
+    for (int cg = 0; cg < 24; ++cg) {
+      uint32_t w[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        uint32_t hh[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int col = 8 * cg + 2 * e + q;
+          const int blk = col >> 6, c = col & 63;
+          int src = -1;
+          if (c < 2 * M) src = (c & 1) ? 3 + M + (c >> 1) : 3 + (c >> 1);
+          else if (c < 2 * M + 3) src = c - 2 * M;
+          else if (c < D0) src = c;
+          float v = 0.0f;
+          if (src >= 0) {
+            const float wv = net.W[(size_t)r * D0 + src];
+            const float wh = __half2float(__float2half_rn(wv));
+            v = blk < 2 ? wh : wv - wh;
+          }
+          if (blk == 0 && (c == D0 || c == D0 + 1)) {
+            const float bias = net.b[r];
+            const float bh = __half2float(__float2half_rn(bias));
+            v = c == D0 ? bh : bias - bh;
+          }
+          hh[q] = h16(v);
+        }
+        w[e] = hh[0] | (hh[1] << 16);
+      }
+      *reinterpret_cast<uint4*>(B0 + (cg >> 3) * (32 * 128) + sw_off(r, cg & 7)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+  for (int i = tid; i < F * C; i += 128 * kFitWGS) {
+    const int f = i / C, o = i - f * C;
+    wz[i] = net.W[(size_t)o * D0 + 3 + 2 * M + f];
+  }
+  for (int i = tid; i < C; i += 128 * kFitWGS) wl[i] = net.W[(size_t)C * D0 + i];  // FP32 last layer
+  if (tid == 0) wl[C] = net.b[C];
+  for (int i = tid; i < 3 * M; i += 128 * kFitWGS) fm[i] = net.fourier[i];
+  for (int i = row; i < 4 * 34; i += 128) reinterpret_cast<float*>(sm + plan.oSlot)[wg * 4 * 34 + i] = 0.0f;
+  if (row == 0) {
+    mbar_init(smem_u32(&mbar[wg]), 1);
+    misc[4 + wg] = 0;
+  }
+  if (tid < 32) {
+    tmem_alloc(smem_u32((const void*)&misc[0]), kFitTmemCols);
+    tmem_relinquish();
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+
+  const uint32_t tmem = (uint32_t)misc[0];
+  const uint32_t d_acc = tmem + (uint32_t)(wg * kFitWgCols);  // forward / dz accumulator (64 columns)
+  const uint32_t d_dw = d_acc + 64;                           // dW0 accumulator (64 columns)
+  const uint32_t t_row = d_acc + ((uint32_t)(warp * 32) << 16);
+  const uint32_t t_dw = d_dw + ((uint32_t)(warp * 32) << 16);
+  const uint32_t af_addr = smem_u32(Af), at_addr = smem_u32(At), bt_addr = smem_u32(Bt);
+  const uint32_t b0_addr = smem_u32(B0);
+  const uint32_t mb = smem_u32(&mbar[wg]);
+  const int bar_id = 1 + wg;
+  uint32_t phase = 0;
+  bool failed = false;
+
+  const net32::Latent lat = net32::make_latent(net, a.time);
+  const float inv_n = 1.0f / (float)a.n;
+  const int nchunks = (a.n + 127) / 128;
+  const int wg_global = blockIdx.x * kFitWGS + wg, n_wg = gridDim.x * kFitWGS;
+  float loss_acc = 0.0f;
+  bool first = true;
+
+  for (int chunk = wg_global; chunk < nchunks; chunk += n_wg) {
+    const int j = chunk * 128 + row;
+    const bool valid = j < a.n;
+    float3 p = make_float3(0.5f, 0.5f, 0.5f);
+    if (valid) p = sample::fit_point(a.cdf, a.cdf_res, a.seed, a.step, j, a.n);
+    const float y = valid ? vol_sample(a.vol, p) : 0.0f;
+
+    // ---- layer-0 input v0 in the tile's column order, FP16 hi + lo
+    float v[64];
+#pragma unroll
+    for (int c = 0; c < 64; ++c) v[c] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      float s, c;
+      net32::fourier_sincos(fm + 3 * k, p, s, c);
+      v[2 * k] = s;
+      v[2 * k + 1] = c;
+    }
+    v[2 * M] = p.x;
+    v[2 * M + 1] = p.y;
+    v[2 * M + 2] = p.z;
+    {
+      const net32::Cell cell = net32::make_cell(lat, p);
+#pragma unroll
+      for (int f = 0; f < F; f += 4) {
+        const float4 z = net32::latent4(lat, cell, f);
+        v[2 * M + 3 + f] = z.x;
+        v[2 * M + 4 + f] = z.y;
+        v[2 * M + 5 + f] = z.z;
+        v[2 * M + 6 + f] = z.w;
+      }
+    }
+    v[D0] = 1.0f;
+    v[D0 + 1] = 1.0f;
+#pragma unroll
+    for (int cg = 0; cg < 8; ++cg) {
+      uint32_t hi[4], lo[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float a0 = v[8 * cg + 2 * e], a1 = v[8 * cg + 2 * e + 1];
+        const __half2 h = __floats2half2_rn(a0, a1);
+        const float2 hb = __half22float2(h);
+        hi[e] = *reinterpret_cast<const uint32_t*>(&h);
+        lo[e] = pack_h2(a0 - hb.x, a1 - hb.y);
+        // the transposed copy for the weight gradient: rows f (hi) and 64 + f (lo), column = point
+        const int f0 = 8 * cg + 2 * e;
+        *reinterpret_cast<uint16_t*>(At + kel(f0, row, kTile)) = (uint16_t)(hi[e] & 0xffffu);
+        *reinterpret_cast<uint16_t*>(At + kel(f0 + 1, row, kTile)) = (uint16_t)(hi[e] >> 16);
+        *reinterpret_cast<uint16_t*>(At + kel(64 + f0, row, kTile)) = (uint16_t)(lo[e] & 0xffffu);
+        *reinterpret_cast<uint16_t*>(At + kel(65 + f0, row, kTile)) = (uint16_t)(lo[e] >> 16);
+      }
+      *reinterpret_cast<uint4*>(Af + a_off(row, cg)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<uint4*>(Af + a_off(row, 8 + cg)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      *reinterpret_cast<uint4*>(Af + a_off(row, 16 + cg)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    bar_sync(bar_id, 128);
+    if (misc[4 + wg]) break;
+    if (row == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int kk = 0; kk < 12; ++kk) {
+        const uint32_t ka = kk >> 2, kb = (kk & 3) * 32;
+        mma_f16(d_acc, sw128_desc(af_addr + ka * kTile + kb), sw128_desc(b0_addr + ka * (32 * 128) + kb),
+                idesc_n(32), kk > 0);
+      }
+      mma_commit(mb);
+    }
+    if (!__all_sync(0xffffffffu, mbar_wait_bounded(mb, phase))) {
+      failed = true;
+      misc[4 + wg] = 1;
+    }
+    phase ^= 1u;
+    tc_fence_after();
+
+    // ---- activation, last layer, loss, delta = dL/dx1
+    float x[32];
+    if (!failed) tmem_ld32(t_row, x);
+    float out = wl[C];
+    float dact[32];
+#pragma unroll
+    for (int o = 0; o < C; ++o) {
+      float s, c;
+      __sincosf(x[o], &s, &c);
+      const float av = SNAKE ? fmaf(0.5f, x[o], s * s) : s;
+      dact[o] = SNAKE ? fmaf(2.0f * s, c, 0.5f) : c;
+      x[o] = av;  // x now holds the activation
+      out = fmaf(wl[o], av, out);
+    }
+    const float r = out - y;
+    const float dout = valid ? (r > 0.f ? inv_n : (r < 0.f ? -inv_n : 0.f)) : 0.0f;
+    if (valid) loss_acc += fabsf(r);
+    // last-layer gradients: reduce-scatter dout * a over the warp, lane o keeps output o
+    {
+      float g[32];
+#pragma unroll
+      for (int o = 0; o < C; ++o) g[o] = dout * x[o];
+#pragma unroll
+      for (int w = 16; w > 0; w >>= 1) {
+        const bool upper = (lane & w) != 0;
+#pragma unroll
+        for (int o = 0; o < w; ++o) {
+          const float send = upper ? g[o] : g[o + w];
+          const float keep = upper ? g[o + w] : g[o];
+          g[o] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+        }
+      }
+      slot[lane] += g[0];
+      float ds = dout;
+#pragma unroll
+      for (int w = 16; w > 0; w >>= 1) ds += __shfl_xor_sync(0xffffffffu, ds, w);
+      if (lane == 0) slot[32] += ds;
+    }
+    float delta[32];
+#pragma unroll
+    for (int o = 0; o < C; ++o) delta[o] = dout * wl[o] * dact[o];
+
+    // ---- delta as columns of the transposed tile (weight gradient)
+#pragma unroll
+    for (int cg = 0; cg < 4; ++cg) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float a0 = delta[8 * cg + 2 * e], a1 = delta[8 * cg + 2 * e + 1];
+        const __half2 h = __floats2half2_rn(a0, a1);
+        const float2 hb = __half22float2(h);
+        const uint32_t hi = *reinterpret_cast<const uint32_t*>(&h);
+        const uint32_t lo = pack_h2(a0 - hb.x, a1 - hb.y);
+        const int o0 = 8 * cg + 2 * e;
+        *reinterpret_cast<uint16_t*>(Bt + kel(o0, row, ATOM_T)) = (uint16_t)(hi & 0xffffu);
+        *reinterpret_cast<uint16_t*>(Bt + kel(o0 + 1, row, ATOM_T)) = (uint16_t)(hi >> 16);
+        *reinterpret_cast<uint16_t*>(Bt + kel(32 + o0, row, ATOM_T)) = (uint16_t)(lo & 0xffffu);
+        *reinterpret_cast<uint16_t*>(Bt + kel(33 + o0, row, ATOM_T)) = (uint16_t)(lo >> 16);
+      }
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    bar_sync(bar_id, 128);
+    if (misc[4 + wg]) break;
+    if (row == 0) {
+      tc_fence_after();
+      // dW0^T += v0^T delta over this tile's points (M = 128 v0 rows, N = 64 delta rows, K = 128 points)
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+        const uint32_t ka = kk >> 2, kb = (kk & 3) * 32;
+        mma_f16(d_dw, sw128_desc(at_addr + ka * kTile + kb), sw128_desc(bt_addr + ka * ATOM_T + kb), idesc_n(64),
+                (first && kk == 0) ? 0u : 1u);
+      }
+      mma_commit(mb);
+    }
+    first = false;
+    // ---- while it runs: latent adjoint dz = W0_z^T delta (FP32), point, cell key
+    if (valid) {
+      float4* dzj = reinterpret_cast<float4*>(a.dz + (size_t)j * F);
+#pragma unroll
+      for (int f = 0; f < F; f += 4) {
+        float zz[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float4* wr = reinterpret_cast<const float4*>(wz + (f + q) * C);
+          float acc = 0.0f;
+#pragma unroll
+          for (int o4 = 0; o4 < C / 4; ++o4) {
+            const float4 w4 = wr[o4];
+            acc = fmaf(w4.x, delta[4 * o4], acc);
+            acc = fmaf(w4.y, delta[4 * o4 + 1], acc);
+            acc = fmaf(w4.z, delta[4 * o4 + 2], acc);
+            acc = fmaf(w4.w, delta[4 * o4 + 3], acc);
+          }
+          zz[q] = acc;
+        }
+        dzj[f >> 2] = make_float4(zz[0], zz[1], zz[2], zz[3]);
+      }
+      a.pts[3 * (size_t)j] = p.x;
+      a.pts[3 * (size_t)j + 1] = p.y;
+      a.pts[3 * (size_t)j + 2] = p.z;
+      int ix, iy, iz;
+      float fx, fy, fz;
+      cell_coord(p.x, lat.R, ix, fx);
+      cell_coord(p.y, lat.R, iy, fy);
+      cell_coord(p.z, lat.R, iz, fz);
+      a.key[j] = (unsigned)((iz * (lat.R - 1) + iy) * (lat.R - 1) + ix);
+      a.idx[j] = (unsigned)j;
+    }
+    // the weight-gradient MMA reads this tile's transposed rows: wait before
+    // the next tile overwrites them
+    if (!__all_sync(0xffffffffu, mbar_wait_bounded(mb, phase))) {
+      failed = true;
+      misc[4 + wg] = 1;
+    }
+    phase ^= 1u;
+    tc_fence_after();
+  }
+
+  // ---- the warpgroup's partial row [W | b | loss]
+  const int nW = C * D0 + C, n_entries = nW + C + 1;
+  float* prow = a.part + (size_t)wg_global * (n_entries + 1);
+  const bool any_tile = wg_global < nchunks;
+  bar_sync(bar_id, 128);
+  if (!failed && !misc[4 + wg]) {
+    // dW0^T rows: lane f of warps 0-1 holds v0-hi feature f, warps 2-3 the lo
+    // feature f - 64; columns: delta hi (0..31), delta lo (32..63)
+    float h0[32], h1[32];
+    if (any_tile) {
+      tmem_ld32(t_dw, h0);
+      tmem_ld32(t_dw + 32, h1);
+    } else {
+#pragma unroll
+      for (int o = 0; o < 32; ++o) h0[o] = h1[o] = 0.0f;
+    }
+#pragma unroll
+    for (int o = 0; o < 32; ++o) h0[o] += h1[o];
+    if (row >= 64) {
+#pragma unroll
+      for (int o = 0; o < 32; ++o) ex[(row - 64) * 33 + o] = h0[o];
+    }
+    bar_sync(bar_id, 128);
+    if (row < 64) {
+      const int f = row;
+      int src = -1;
+      if (f < 2 * M) src = (f & 1) ? 3 + M + (f >> 1) : 3 + (f >> 1);
+      else if (f < 2 * M + 3) src = f - 2 * M;
+      else if (f < D0) src = f;
+#pragma unroll
+      for (int o = 0; o < 32; ++o) {
+        const float g = h0[o] + ex[f * 33 + o];
+        if (src >= 0) prow[o * D0 + src] = g;
+        if (f == D0) prow[nW + o] = g;  // the constant-1 column: bias of layer 0
+      }
+    }
+    // last layer and loss: the four warps' slots in order
+    if (row < 32) {
+      const float* s0 = reinterpret_cast<float*>(sm + plan.oSlot) + wg * 4 * 34;
+      prow[C * D0 + row] = ((s0[row] + s0[34 + row]) + s0[68 + row]) + s0[102 + row];
+      if (row == 0) prow[nW + C] = ((s0[32] + s0[66]) + s0[100]) + s0[134];
+    }
+    // loss: fixed tree over the warpgroup's threads
+    float l = loss_acc;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) l += __shfl_xor_sync(0xffffffffu, l, w);
+    if (lane == 0) ex[64 * 33 + warp] = l;  // words past the exchange rows
+    bar_sync(bar_id, 128);
+    if (row == 0) {
+      const float* q = ex + 64 * 33;
+      prow[n_entries] = ((q[0] + q[1]) + q[2]) + q[3];
+    }
+  }
+  if (failed || misc[4 + wg]) {
+    if (row == 0) atomicExch(status, (unsigned int)SRN_ERR_TIMEOUT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (tid < 32) tmem_dealloc(tmem, kFitTmemCols);
+}
+
+template <int M, int F, int ACT>
+cudaError_t fit_mma_t(const NetDev& net, const PointArgsMma& a, int grid, unsigned int* status, cudaStream_t st) {
+  const FitPlan plan = fit_plan(M, F);
+  auto k = fit_mma_kernel<M, F, ACT>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total);
+  if (e != cudaSuccess) return e;
+  k<<<grid, 128 * kFitWGS, plan.total, st>>>(net, a, plan, status);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int fit_mma_rows_per_cta() { return kFitWGS; }
+
+bool fit_mma_supported(const NetDev& n) {
+  if (n.c != 32 || n.l != 2 || n.D != 1 || n.ti) return false;
+  if (n.act != SRN_ACT_SINE && n.act != SRN_ACT_SNAKEALT) return false;
+  return (n.m == 12 && n.F == 8) || (n.m == 14 && n.F == 16);
+}
+
+cudaError_t launch_fit_mma(const NetDev& n, const PointArgsMma& a, int grid, unsigned int* status, cudaStream_t st) {
+  if (n.m == 12 && n.F == 8)
+    return n.act == SRN_ACT_SNAKEALT ? fit_mma_t<12, 8, SRN_ACT_SNAKEALT>(n, a, grid, status, st)
+                                     : fit_mma_t<12, 8, SRN_ACT_SINE>(n, a, grid, status, st);
+  return n.act == SRN_ACT_SNAKEALT ? fit_mma_t<14, 16, SRN_ACT_SNAKEALT>(n, a, grid, status, st)
+                                   : fit_mma_t<14, 16, SRN_ACT_SINE>(n, a, grid, status, st);
+}
+
+}  // namespace srn
