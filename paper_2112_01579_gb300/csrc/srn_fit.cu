@@ -484,40 +484,60 @@ __global__ void grid_grad_kernel(const float* __restrict__ pts, const float* __r
   }
 }
 
-// Dense cells (many points per cell): one warp per (cell, corner) sums
-// w_corner(p) * dz over the cell's points (sorted order, lane-strided, fixed
-// butterfly) into part[cell][corner][F]; vertex_gather_kernel then adds the
-// <= 8 partials of each vertex in a fixed order.
+// Dense cells (many points per cell): one block of 8 warps per cell, warp c
+// sums w_corner_c(p) * dz over the cell's points (sorted order, lane-strided,
+// fixed butterfly) into part[cell][c][F]; vertex_gather_kernel then adds the
+// <= 8 partials of each vertex in a fixed order.  The block stages the cell's
+// points (position, dz) in shared memory 256 at a time, so each point is
+// gathered from global memory once instead of once per corner; lane l still
+// takes points l, l + 32, ... in order, so the sums are those of a warp
+// reading global memory directly.
 template <int F>
-__global__ void cell_corner_kernel(const float* __restrict__ pts, const float* __restrict__ dz,
-                                   const unsigned int* __restrict__ sidx, const unsigned int* __restrict__ start,
-                                   int R, long long n_cells, float* __restrict__ part) {
-  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (wid >= n_cells * 8) return;
-  const long long cell = wid >> 3;
-  const int c = (int)(wid & 7);
+__global__ void __launch_bounds__(256) cell_corner_kernel(const float* __restrict__ pts,
+                                                          const float* __restrict__ dz,
+                                                          const unsigned int* __restrict__ sidx,
+                                                          const unsigned int* __restrict__ start, int R,
+                                                          long long n_cells, float* __restrict__ part) {
+  constexpr int kChunk = 256;
+  __shared__ float sp[kChunk][3];
+  __shared__ float4 sz[kChunk][F / 4];
+  const long long cell = blockIdx.x;
+  if (cell >= n_cells) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = warp;
   const int dx = c & 1, dy = (c >> 1) & 1, dzz = c >> 2;
   float acc[F];
 #pragma unroll
   for (int f = 0; f < F; ++f) acc[f] = 0.f;
   const int s0 = (int)start[cell], s1 = (int)start[cell + 1];
-  for (int s = s0 + lane; s < s1; s += 32) {
-    const int j = (int)sidx[s];
-    int ix, iy, iz;
-    float fx, fy, fz;
-    cell_coord(pts[3 * j], R, ix, fx);
-    cell_coord(pts[3 * j + 1], R, iy, fy);
-    cell_coord(pts[3 * j + 2], R, iz, fz);
-    const float w = (dx ? fx : 1.0f - fx) * (dy ? fy : 1.0f - fy) * (dzz ? fz : 1.0f - fz);
-    const float4* zz = reinterpret_cast<const float4*>(dz + (size_t)j * F);
+  for (int base = s0; base < s1; base += kChunk) {
+    const int cnt = min(kChunk, s1 - base);
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt; i += 256) {
+      const int j = (int)sidx[base + i];
+      sp[i][0] = pts[3 * (size_t)j];
+      sp[i][1] = pts[3 * (size_t)j + 1];
+      sp[i][2] = pts[3 * (size_t)j + 2];
+      const float4* zz = reinterpret_cast<const float4*>(dz + (size_t)j * F);
 #pragma unroll
-    for (int f = 0; f < F; f += 4) {
-      const float4 q = zz[f / 4];
-      acc[f] = fmaf(w, q.x, acc[f]);
-      acc[f + 1] = fmaf(w, q.y, acc[f + 1]);
-      acc[f + 2] = fmaf(w, q.z, acc[f + 2]);
-      acc[f + 3] = fmaf(w, q.w, acc[f + 3]);
+      for (int f = 0; f < F / 4; ++f) sz[i][f] = zz[f];
+    }
+    __syncthreads();
+    for (int i = lane; i < cnt; i += 32) {
+      int ix, iy, iz;
+      float fx, fy, fz;
+      cell_coord(sp[i][0], R, ix, fx);
+      cell_coord(sp[i][1], R, iy, fy);
+      cell_coord(sp[i][2], R, iz, fz);
+      const float w = (dx ? fx : 1.0f - fx) * (dy ? fy : 1.0f - fy) * (dzz ? fz : 1.0f - fz);
+#pragma unroll
+      for (int f = 0; f < F; f += 4) {
+        const float4 q = sz[i][f / 4];
+        acc[f] = fmaf(w, q.x, acc[f]);
+        acc[f + 1] = fmaf(w, q.y, acc[f + 1]);
+        acc[f + 2] = fmaf(w, q.z, acc[f + 2]);
+        acc[f + 3] = fmaf(w, q.w, acc[f + 3]);
+      }
     }
   }
 #pragma unroll
@@ -526,7 +546,7 @@ __global__ void cell_corner_kernel(const float* __restrict__ pts, const float* _
     for (int off = 16; off > 0; off >>= 1) acc[f] += __shfl_xor_sync(0xffffffffu, acc[f], off);
   if (lane == 0) {
 #pragma unroll
-    for (int f = 0; f < F; ++f) part[(size_t)wid * F + f] = acc[f];
+    for (int f = 0; f < F; ++f) part[((size_t)cell * 8 + c) * F + f] = acc[f];
   }
 }
 
