@@ -185,6 +185,10 @@ srn_status srn_sync_half(srn_ctx* ctx, void* stream);
  * density samples taken is ADDED to *samples_dev (uint64).  Allocates
  * nothing (Section 6: fV-SRN decodes without temporary memory).
  * precision FP32: CUDA-core FP32; FP16: tensor-core MMA with FP32 accumulate.
+ * FP16 operands hold magnitudes up to 65504: a network whose inputs or
+ * activations exceed that renders non-finite densities, which the FP16 path
+ * records as SRN_ERR_NONFINITE (reported by srn_sync_status); the FP32 path
+ * evaluates such networks.
  */
 srn_status srn_render(srn_ctx* ctx, const srn_camera* cams, int n_views, const float* times, int n_times,
                       const srn_tf* tf, const srn_render_desc* desc, float* rgba_dev,
@@ -341,7 +345,7 @@ srn_status srn_save(srn_ctx* ctx, const char* path, int step);
 srn_status srn_load(srn_ctx* ctx, const char* path, int* step_out);
 
 /* Synchronize `stream` and return (then clear) the device status word:
- * SRN_OK, SRN_ERR_NONFINITE or SRN_ERR_INTERNAL. */
+ * SRN_OK, SRN_ERR_NONFINITE, SRN_ERR_TIMEOUT or SRN_ERR_INTERNAL. */
 srn_status srn_sync_status(srn_ctx* ctx, void* stream);
 
 /* Mean squared error over the RGB channels of n RGBA float32 pixels, the

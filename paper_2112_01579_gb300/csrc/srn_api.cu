@@ -385,7 +385,8 @@ srn_status srn_sync_status(srn_ctx* ctx, void* stream) {
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->status, 0, sizeof(unsigned int), s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "srn_sync_status");
-  if (word == SRN_ERR_NONFINITE) return fail(SRN_ERR_NONFINITE, "a fit step produced a non-finite loss or gradient");
+  if (word == SRN_ERR_NONFINITE)
+    return fail(SRN_ERR_NONFINITE, "a fit step produced a non-finite loss or gradient, or the FP16 path a non-finite output");
   if (word == SRN_ERR_TIMEOUT) return fail(SRN_ERR_TIMEOUT, "a bounded device wait gave up");
   if (word != 0) return fail(SRN_ERR_INTERNAL, "device status word %u", word);
   return SRN_OK;

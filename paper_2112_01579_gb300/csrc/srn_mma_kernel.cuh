@@ -34,6 +34,8 @@
 //   its pixel and takes the next ray, so tiles stay full.
 // * Every mbarrier wait is bounded; on timeout the warpgroup stops, records
 //   SRN_ERR_TIMEOUT in the status word and the CTA frees its TMEM.
+// * A non-finite network output (an input or activation beyond the FP16
+//   range, 65504) is recorded as SRN_ERR_NONFINITE.
 #pragma once
 #include <string.h>
 
@@ -653,6 +655,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
   const long long n_rays = POINTS ? pd.n : tpf * 32 * b.n_views * b.n_times;
   const size_t gsz = (size_t)net.R * net.R * net.R * net.F;
   bool active = false, exhausted = false, failed = false;
+  bool overflow = false;  // a non-finite network output (FP16 range exceeded)
   long long pix = 0;
   float3 o = make_float3(0.f, 0.f, 0.f), d = o;
   float t0 = 0.f, t1 = 0.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, Acc = 0.f;
@@ -945,6 +948,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
     if (POINTS) {
       if (active && !failed) {
         for (int dd = 0; dd < D; ++dd) pd.out[pix * D + dd] = out[dd];
+        overflow |= !(fabsf(out[0]) < INFINITY);
         ++ns;
         active = false;
       }
@@ -972,6 +976,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
       }
       if (sample_done) {
         ++ns;
+        overflow |= !(fabsf(rho_c) < INFINITY);
         float4 c = tf_eval_inv(tf, tfinv, rho_c);
         const float alpha = 1.0f - __expf(-c.w * tf.opacity_scale * len);
         if (SH != SRN_SHADE_NONE) shade(c, g, d);
@@ -991,6 +996,10 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
 
   if (failed || misc[4 + wg]) {
     if (row == 0) atomicExch(status, (unsigned int)SRN_ERR_TIMEOUT);
+  } else if (__any_sync(0xffffffffu, overflow) && lane == 0) {
+    // an input or activation outside the FP16 range made the output
+    // non-finite; the FP32 path evaluates such networks
+    atomicCAS(status, (unsigned int)SRN_OK, (unsigned int)SRN_ERR_NONFINITE);
   }
   if (!POINTS) add_samples(b.samples, ns);
   tc_fence_before();

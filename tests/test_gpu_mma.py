@@ -180,6 +180,31 @@ def test_mma_time_batch(srn):
     assert r["ok"], r
 
 
+def test_mma_fp16_overflow_is_reported(srn):
+    """A latent grid beyond the FP16 range (1e5) overflows the FP16 operands:
+    the tensor-core render reports SRN_ERR_NONFINITE; the FP32 path renders
+    the same network with finite values; a normal network leaves the status
+    at SRN_OK."""
+    import torch
+    S = srn
+    p = H.cfg2_params(seed=29, R=8)
+    p["grid"] = (p["grid"] * 2e5).astype(np.float32)
+    tf, cams = synth.tf_preset(8), synth.orbit_cameras(1)
+    out = torch.zeros((1, 1, 16, 16, 4), device="cuda")
+    n16 = S.Network(p, precision=S.SRN_PREC_FP16)  # the device's FP16 copy rounds 1e5 to infinity
+    S.srn_render(n16.ctx, cams, tf, S.render_desc(16, 16, 1 / 64, 2.0), out)
+    st, _ = S.srn_sync_status(n16.ctx)
+    assert st == S.SRN_ERR_NONFINITE
+    assert S.srn_sync_status(n16.ctx)[0] == S.SRN_OK  # reading clears it
+    n32 = S.Network(p, precision=S.SRN_PREC_FP32)
+    S.srn_render(n32.ctx, cams, tf, S.render_desc(16, 16, 1 / 64, 2.0), out)
+    assert S.srn_sync_status(n32.ctx)[0] == S.SRN_OK
+    assert torch.isfinite(out).all()
+    ok = S.Network(synth.to_half_exact(H.cfg2_params(seed=30, R=8)), precision=S.SRN_PREC_FP16)
+    S.srn_render(ok.ctx, cams, tf, S.render_desc(16, 16, 1 / 64, 2.0), out)
+    assert S.srn_sync_status(ok.ctx)[0] == S.SRN_OK
+
+
 def test_mma_rejects_unsupported(srn):
     S = srn
     p = synth.random_params(R=8, F=12, m=10, layers=3, width=32, seed=28)
