@@ -92,13 +92,16 @@ def test_uniform_points_and_invalid_grids(srn):
         assert torch.equal(pts, before)
 
 
-def test_adaptive_fit_steps_match_oracle(srn):
+@pytest.mark.parametrize("layers", [3, 2])
+def test_adaptive_fit_steps_match_oracle(srn, layers):
     """Error grid from the GPU, then two fit steps drawing from it: loss and
-    updated weights against the oracle given the same FP32 error values."""
+    updated weights against the oracle given the same FP32 error values
+    (three layers: the FP32 fit kernels; two: the tensor-core point kernel,
+    whose weight gradients carry the wider hi/lo bound)."""
     import torch
     S = srn
     vol = synth.blobs_volume(40, 6, seed=604).numpy()
-    p = synth.init_params(R=8, F=16, m=14, layers=3, width=32, act=synth.ACT_SNAKEALT, seed=605)
+    p = synth.init_params(R=8, F=16, m=14, layers=layers, width=32, act=synth.ACT_SNAKEALT, seed=605)
     net = S.Network(p, max_fit_points=4000, adam=True)
     vol_d = torch.tensor(vol, device="cuda")
     E = torch.zeros(16 ** 3, device="cuda")
@@ -118,4 +121,5 @@ def test_adaptive_fit_steps_match_oracle(srn):
     Wg = np.concatenate([w.ravel() for w in got["weights"]])
     g = grads[on.grid.size:on.grid.size + on.W.size]
     big = np.abs(g) > 1e-2 * np.abs(g).max()
-    assert np.abs(Wg - on.W)[big].max() <= 5e-3 * 5e-3 + 1e-7
+    scale = 10.0 if layers == 2 else 1.0  # tensor-core fit: 2e-4 instead of 2e-5 of the block maximum
+    assert np.abs(Wg - on.W)[big].max() <= scale * 5e-3 * 5e-3 + 1e-7
