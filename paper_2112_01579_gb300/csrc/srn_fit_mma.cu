@@ -37,7 +37,7 @@ namespace {
 using namespace mma;
 
 constexpr int kFitWGS = 2;              // warpgroups per CTA (shared memory: ~222 KB)
-constexpr int kFitTmemCols = 256;       // per warpgroup: 64 forward / dz + 64 dW0 accumulator columns
+constexpr int kFitTmemCols = 256;       // per warpgroup: 64 forward + 64 dW0 accumulator columns
 constexpr int kFitWgCols = 128;
 
 struct FitPlan {
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
   float* wl = reinterpret_cast<float*>(sm + plan.oWl);
   float* fm = reinterpret_cast<float*>(sm + plan.oFm);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(sm + plan.oMbar);
-  volatile int* misc = reinterpret_cast<volatile int*>(sm + plan.oMisc);  // [0] tmem base, [1] nerf, [4+wg] fail
+  volatile int* misc = reinterpret_cast<volatile int*>(sm + plan.oMisc);  // [0] tmem base, [4+wg] fail
 
   const int tid = threadIdx.x;
   const int wg = tid >> 7, row = tid & 127, lane = tid & 31, warp = row >> 5;
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
   tc_fence_after();
 
   const uint32_t tmem = (uint32_t)misc[0];
-  const uint32_t d_acc = tmem + (uint32_t)(wg * kFitWgCols);  // forward / dz accumulator (64 columns)
+  const uint32_t d_acc = tmem + (uint32_t)(wg * kFitWgCols);  // forward accumulator (32 of 64 columns)
   const uint32_t d_dw = d_acc + 64;                           // dW0 accumulator (64 columns)
   const uint32_t t_row = d_acc + ((uint32_t)(warp * 32) << 16);
   const uint32_t t_dw = d_dw + ((uint32_t)(warp * 32) << 16);
