@@ -21,19 +21,23 @@ def srn():
     return S
 
 
-@pytest.mark.parametrize("width,res,spv", [(32, 12, 8), (48, 7, 3)])
-def test_error_grid_matches_oracle(srn, width, res, spv):
+@pytest.mark.parametrize("width,res,spv,timed", [(32, 12, 8, False), (48, 7, 3, False), (32, 9, 5, True)])
+def test_error_grid_matches_oracle(srn, width, res, spv, timed):
+    """Error grid against the oracle; the timed case has three keyframes and
+    the direct time input, evaluated between keyframes."""
     import torch
     S = srn
     m = synth.fourier_rows_for_width(width)
+    kw = dict(n_keyframes=3, key_times=[0.0, 1.0, 3.0], time_input=1) if timed else {}
     p = synth.random_params(R=8, F=16, m=m, layers=3, width=width, act=synth.ACT_SNAKEALT, seed=600 + width,
-                            grid_std=0.5, bias_std=0.2)
+                            grid_std=0.5, bias_std=0.2, **kw)
+    t = 1.75 if timed else 0.0
     vol = synth.blobs_volume(24, 5, seed=601).numpy()
     net = S.Network(p)
     E = torch.full((res ** 3,), -1.0, device="cuda")
-    S.srn_error_grid(net.ctx, torch.tensor(vol, device="cuda"), res, spv, 77, E)
+    S.srn_error_grid(net.ctx, torch.tensor(vol, device="cuda"), res, spv, 77, E, time=t)
     torch.cuda.synchronize()
-    ref = oracle.error_grid(oracle.OracleNet(p), vol, res, spv, 77).reshape(-1)
+    ref = oracle.error_grid(oracle.OracleNet(p), vol, res, spv, 77, t).reshape(-1)
     got = E.cpu().numpy().astype(np.float64)
     assert np.abs(got - ref).max() <= H.TOL_FP32_RHO * max(1.0, np.abs(ref).max())
 
