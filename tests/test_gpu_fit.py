@@ -22,8 +22,19 @@ TOL_GRAD = 2e-5
 TOL_GRAD_MMA = 2e-4
 
 
+def _spread(vol):
+    """The volume mapped to [-10, 10]: residuals r = rho - y then lie far from
+    zero for almost every point, so the L1 gradient's sign(r) is not decided
+    by rounding.  (With targets in [0, 1] a network fitted loosely leaves a
+    few of 10^4 points within the tensor-core forward's ~1e-6 of r = 0; their
+    sign may differ from the FP64 oracle's, a legitimate ambiguity of the L1
+    subgradient that moves the last bias by 2/n per point.)"""
+    return (20.0 * (np.asarray(vol) - 0.5)).astype(np.float32)
+
+
 def _mma_fit(p):
-    """True when the fit step of this network runs the tensor-core point kernel."""
+    """True when the fit step of this network runs the tensor-core point
+    kernel (width 32, two layers, density output, no time input)."""
     W = p["weights"]
     m, F = p["fourier"].shape[0], p["grid"].shape[-1]
     return (len(W) == 2 and W[0].shape[0] == 32 and W[1].shape[0] == 1 and not p.get("time_input", 0)
@@ -160,6 +171,8 @@ def test_fit_step_matches_oracle(srn, shape):
         p = synth.init_params(R=8, F=8, m=12, layers=2, width=32, act=synth.ACT_SINE, seed=37)
     else:
         p = synth.init_params(R=16, F=16, m=14, layers=4, width=32, act=synth.ACT_SNAKEALT, seed=38)
+    if _mma_fit(p):
+        vol = _spread(vol)
     net, on, losses, grads = _fit_pair(S, p, vol, 5000, 2)
     for lg, lo in losses:
         assert abs(lg - lo) <= 1e-5 * max(abs(lo), 1e-3), losses
@@ -181,6 +194,7 @@ def test_tensor_core_fit_gradients(srn, shape):
     else:
         p = synth.random_params(R=10, F=16, m=14, layers=2, width=32, act=synth.ACT_SNAKEALT, seed=44, grid_std=0.3)
     assert _mma_fit(p)
+    vol = _spread(vol)
     n = 20011
     net = S.Network(p, max_fit_points=n, adam=True)
     loss = torch.zeros(1, device="cuda")
@@ -206,7 +220,7 @@ def test_fit_head_and_keyframes(srn):
     _check_params(net, on, grads, 1e-2, 5e-3)
     p = synth.init_params(R=6, F=8, m=12, layers=2, width=32, act=synth.ACT_SINE, seed=41, n_keyframes=3,
                           key_times=[0.0, 2.0, 3.0])
-    net, on, losses, grads = _fit_pair(S, p, vol, 2000, 2, t=2.25)
+    net, on, losses, grads = _fit_pair(S, p, _spread(vol) if _mma_fit(p) else vol, 2000, 2, t=2.25)
     for lg, lo in losses:
         assert abs(lg - lo) <= 1e-5 * max(abs(lo), 1e-3), losses
     _check_params(net, on, grads, 1e-2, 5e-3, TOL_GRAD_MMA if _mma_fit(p) else TOL_GRAD)
