@@ -237,6 +237,11 @@ srn_status srn_backward(srn_ctx* ctx, const float* pts_dev, int n, float time, c
  * loss_dev.  If the loss or any gradient is not finite the parameters are
  * left unchanged and the context records SRN_ERR_NONFINITE, reported by
  * srn_sync_status.  Also refreshes the FP16 copies when they exist.
+ * Two-layer width-32 density networks (12 Fourier rows / 8 channels or
+ * 14 / 16, no time input) run the per-point forward and the layer-0 weight
+ * gradient on the tensor cores from FP16 hi + lo splits of FP32 values
+ * (weight gradients within ~2e-4 of each block's maximum); every other shape
+ * runs FP32 kernels.  Either way the step is deterministic.
  */
 srn_status srn_fit_step(srn_ctx* ctx, const float* volume_dev, const int dims[3], int n_points, uint64_t seed,
                         int step, float time, float lr_grid, float lr_net, float grad_weight, float grad_scale,
