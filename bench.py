@@ -136,8 +136,7 @@ def setup_scene(device="cuda", fit_steps=FIT_STEPS, seed=0):
     loss = torch.zeros(1, device=device)
     try:
         t0 = time.time()
-        for s in range(fit_steps):
-            srn.srn_fit_step(net.ctx, vol, FIT_POINTS, seed + 1, s, loss, lr_grid=1e-2, lr_net=5e-3)
+        srn.srn_fit_steps(net.ctx, vol, FIT_POINTS, seed + 1, 0, fit_steps, loss, lr_grid=1e-2, lr_net=5e-3)
         torch.cuda.synchronize()
         fit_info = {"steps": fit_steps, "final_loss": float(loss.item()), "wall_s": time.time() - t0}
     except srn.SrnError as e:
@@ -185,30 +184,51 @@ def lowpass_baseline(vol, R, F):
 
 def fit_cfg3(vol, pts, steps=FIT_STEPS, seed=0):
     """Config 3: the plain-workload network (8^3 x 8 grid, m = 12, 2 sine
-    layers) fitted to the volume, 2^18 points per step.  Returns steps/s
-    (device time of all steps), final loss and density PSNR."""
+    layers) fitted to the volume, 2^18 points per step.  The same fit runs
+    twice from the same initial state: one srn_fit_step call per step, then
+    srn_fit_steps (one captured step replayed as a CUDA graph), whose final
+    state must equal the first's bit for bit.  Returns steps/s of both (device
+    time of all steps), final loss and density PSNR."""
     import torch
     from paper_2112_01579_gb300 import srn, synth
     p = synth.init_params(R=8, F=8, m=12, layers=2, width=32, act=synth.ACT_SINE, seed=seed)
     net = srn.Network(p, precision=srn.SRN_PREC_FP32, max_fit_points=FIT_POINTS, adam=True)
     loss = torch.zeros(1, device=vol.device)
-    for s in range(3):  # warm-up on throw-away steps of a copy
-        srn.srn_fit_step(net.ctx, vol, FIT_POINTS, seed + 7, s, loss, lr_grid=0.0, lr_net=0.0)
-    net.adam_m.zero_()
-    net.adam_v.zero_()
-    torch.cuda.synchronize()
+    init = [t.clone() for t in (net.grid, net.weights, net.biases)]
+
+    def reset():
+        for t, t0 in zip((net.grid, net.weights, net.biases), init):
+            t.copy_(t0)
+        net.adam_m.zero_()
+        net.adam_v.zero_()
+        torch.cuda.synchronize()
+
+    # warm-up with the timed arguments (this also captures the graph), then back to the initial state
+    for s in range(3):
+        srn.srn_fit_step(net.ctx, vol, FIT_POINTS, seed + 1, s, loss, lr_grid=1e-2, lr_net=5e-3)
+    srn.srn_fit_steps(net.ctx, vol, FIT_POINTS, seed + 1, 0, 3, loss, lr_grid=1e-2, lr_net=5e-3)
+    reset()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for s in range(steps):
         srn.srn_fit_step(net.ctx, vol, FIT_POINTS, seed + 1, s, loss, lr_grid=1e-2, lr_net=5e-3)
     e1.record()
     torch.cuda.synchronize()
+    single_sps = steps / (e0.elapsed_time(e1) / 1e3)
+    single = [t.clone() for t in (net.grid, net.weights, net.biases, loss)]
+    reset()
+    e0.record()
+    srn.srn_fit_steps(net.ctx, vol, FIT_POINTS, seed + 1, 0, steps, loss, lr_grid=1e-2, lr_net=5e-3)
+    e1.record()
+    torch.cuda.synchronize()
     st, msg = srn.srn_sync_status(net.ctx)
     sps = steps / (e0.elapsed_time(e1) / 1e3)
+    same = all(torch.equal(a, b) for a, b in zip(single, (net.grid, net.weights, net.biases, loss)))
     M, _, lp_psnr = lowpass_baseline(vol, 8, 8)
-    res = {"steps": steps, "points_per_step": FIT_POINTS, "steps_per_s": sps, "final_loss": float(loss.item()),
-           "density_psnr_db": density_psnr_network(net, vol, pts), "lowpass_grid": M,
-           "lowpass_density_psnr_db": lp_psnr, "status": st}
+    res = {"steps": steps, "points_per_step": FIT_POINTS, "steps_per_s": sps, "api": "srn_fit_steps (graph replay)",
+           "steps_per_s_single_calls": single_sps, "graph_equals_single_calls": same,
+           "final_loss": float(loss.item()), "density_psnr_db": density_psnr_network(net, vol, pts),
+           "lowpass_grid": M, "lowpass_density_psnr_db": lp_psnr, "status": st}
     net.close()
     return res
 
@@ -262,15 +282,16 @@ def fit_adaptive(vol, pts, steps=FIT_STEPS, seed=0, every=50, res=128, spv=8):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         grid_ms = []
         e0.record()
-        for s in range(steps):
-            if mode == "adaptive" and s > 0 and s % every == 0:
+        for s in range(0, steps, every):
+            if mode == "adaptive" and s > 0:
                 g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 g0.record()
                 srn.srn_error_grid(net.ctx, vol, res, spv, seed + s, E)
                 srn.srn_fit_set_sampling(net.ctx, E, res)
                 g1.record()
                 grid_ms.append((g0, g1))
-            srn.srn_fit_step(net.ctx, vol, FIT_POINTS, seed + 1, s, loss, lr_grid=1e-2, lr_net=5e-3)
+            srn.srn_fit_steps(net.ctx, vol, FIT_POINTS, seed + 1, s, min(every, steps - s), loss, lr_grid=1e-2,
+                              lr_net=5e-3)
         e1.record()
         torch.cuda.synchronize()
         srn.srn_error_grid(net.ctx, vol, res, spv, seed + 99991, E)
@@ -474,9 +495,8 @@ def shaded_workload(fit_steps=FIT_STEPS, seed=0):
         p = synth.init_params(R=64, F=16, m=14, layers=4, width=32, out_dim=D, act=synth.ACT_SNAKEALT, seed=seed)
         net = srn.Network(p, precision=srn.SRN_PREC_FP16, max_fit_points=FIT_POINTS, adam=True)
         loss = torch.zeros(1, device="cuda")
-        for st in range(fit_steps):
-            # head targets: central differences of the volume scaled by 1/100 (|grad V| reaches ~100 per unit)
-            srn.srn_fit_step(net.ctx, vol, FIT_POINTS, seed + 11, st, loss, grad_weight=gw, grad_scale=0.01)
+        # head targets: central differences of the volume scaled by 1/100 (|grad V| reaches ~100 per unit)
+        srn.srn_fit_steps(net.ctx, vol, FIT_POINTS, seed + 11, 0, fit_steps, loss, grad_weight=gw, grad_scale=0.01)
         srn.srn_sync_half(net.ctx)
         nets[D] = net
     out = torch.zeros((1, 1, H_IMG, W_IMG, 4), device="cuda")

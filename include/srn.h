@@ -248,6 +248,24 @@ srn_status srn_fit_step(srn_ctx* ctx, const float* volume_dev, const int dims[3]
                         float* loss_dev, void* stream);
 
 /*
+ * n_steps training steps first_step, first_step + 1, ... with the same
+ * arguments: the same results, bit for bit, as that many srn_fit_step calls
+ * (loss_dev holds the last step's loss), without the per-step launch cost.
+ * One step is captured once as a CUDA graph on a stream the context owns
+ * and replayed n_steps times on `stream`; the step index is kept in device
+ * memory and advanced by the graph.  The graph is captured again when any
+ * argument other than first_step / n_steps, the parameter arrays
+ * (srn_set_params) or the adaptive distribution's storage changes (the
+ * distribution's values are read at replay time).  n_steps >= 0 (0: nothing
+ * happens), first_step >= 0, first_step + n_steps <= INT_MAX.  Validation and
+ * error reporting as srn_fit_step; a non-finite step is skipped and
+ * recorded, and the following steps run.
+ */
+srn_status srn_fit_steps(srn_ctx* ctx, const float* volume_dev, const int dims[3], int n_points, uint64_t seed,
+                         int first_step, int n_steps, float time, float lr_grid, float lr_net, float grad_weight,
+                         float grad_scale, float* loss_dev, void* stream);
+
+/*
  * Section 6.2 adaptive resampling, step 1: the error grid.  err_dev
  * receives res^3 floats ([z][y][x], x fastest): E_v = mean over
  * samples_per_voxel positions in voxel v of |rho(p) - V(p)| (network output 0

@@ -1,6 +1,7 @@
 // C ABI of the library (include/srn.h): argument validation, context
 // management and kernel dispatch.  No computation happens here: every step
 // of the render / eval / fit path runs in the library's CUDA kernels.
+#include <limits.h>
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -29,6 +30,11 @@ struct srn_ctx {
   size_t cdf_cap = 0;
   int cdf_res = 0;
   bool cdf_active = false;
+  // srn_fit_steps: one fit step captured as a CUDA graph, replayed per step;
+  // the step index lives in status[1] and the graph advances it.
+  cudaStream_t graph_stream = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  srn::FitArgs graph_key;  // the arguments baked into graph_exec
 };
 
 namespace {
@@ -220,6 +226,8 @@ srn_status srn_destroy(srn_ctx* ctx) {
   if (ctx->cdf) cudaFree(ctx->cdf);
   if (ctx->cdf_bsum) cudaFree(ctx->cdf_bsum);
   if (ctx->cdf_flags) cudaFree(ctx->cdf_flags);
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  if (ctx->graph_stream) cudaStreamDestroy(ctx->graph_stream);
   if (ctx->status) cudaFree(ctx->status);
   delete ctx;
   return SRN_OK;
@@ -328,9 +336,14 @@ srn_status srn_backward(srn_ctx* ctx, const float* pts_dev, int n, float time, c
   return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_backward");
 }
 
-srn_status srn_fit_step(srn_ctx* ctx, const float* volume_dev, const int dims[3], int n_points, uint64_t seed,
-                        int step, float time, float lr_grid, float lr_net, float grad_weight, float grad_scale,
-                        float* loss_dev, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// Validation and argument set shared by srn_fit_step and srn_fit_steps.
+srn_status make_fit_args(srn_ctx* ctx, const float* volume_dev, const int dims[3], int n_points, uint64_t seed,
+                         int step, float time, float lr_grid, float lr_net, float grad_weight, float grad_scale,
+                         float* loss_dev, FitArgs* out) {
   if (!ctx) return fail(SRN_ERR_INVALID_ARG, "ctx is NULL");
   if (!volume_dev || !dims || dims[0] < 2 || dims[1] < 2 || dims[2] < 2)
     return fail(SRN_ERR_INVALID_ARG, "volume with dims >= 2 is required");
@@ -345,9 +358,7 @@ srn_status srn_fit_step(srn_ctx* ctx, const float* volume_dev, const int dims[3]
   if (!(lr_grid >= 0.0f) || !(lr_net >= 0.0f)) return fail(SRN_ERR_INVALID_ARG, "learning rates must be >= 0");
   if (ctx->cdf_active && !adaptive_fits(n_points, ctx->cdf_res))
     return fail(SRN_ERR_UNSUPPORTED, "n_points too large for 64-bit adaptive sampling at this resolution");
-  srn_status st = use_device(ctx);
-  if (st) return st;
-  FitArgs a;
+  FitArgs a{};
   a.vol = VolDev{volume_dev, dims[0], dims[1], dims[2]};
   a.n = n_points;
   a.seed = seed;
@@ -368,12 +379,96 @@ srn_status srn_fit_step(srn_ctx* ctx, const float* volume_dev, const int dims[3]
   a.biases = ctx->prm.biases;
   a.cdf = ctx->cdf_active ? ctx->cdf : nullptr;
   a.cdf_res = ctx->cdf_res;
+  a.step_ptr = nullptr;
+  *out = a;
+  return SRN_OK;
+}
+
+// One fit step (Section 5.2 loss, Adam update) plus the 8-bit grid refresh.
+cudaError_t enqueue_fit_step(srn_ctx* ctx, const FitArgs& a, cudaStream_t st) {
   const NetDev net = make_net(ctx);
-  cudaError_t e = launch_fit_step(ctx->fit, net, a, (cudaStream_t)stream);
+  cudaError_t e = launch_fit_step(ctx->fit, net, a, st);
   if (e == cudaSuccess && ctx->cfg.grid_u8)
     e = launch_quantize_grid(net.grid, net_grid_count(net) / net.F, net.F, (uint8_t*)ctx->prm.grid_q,
-                             ctx->prm.grid_qp, (cudaStream_t)stream);
+                             ctx->prm.grid_qp, st);
+  return e;
+}
+
+// Every field the graph bakes in, the step excepted (it is read from device memory).
+bool same_graph_args(const FitArgs& x, const FitArgs& y) {
+  return x.vol.vol == y.vol.vol && x.vol.nx == y.vol.nx && x.vol.ny == y.vol.ny && x.vol.nz == y.vol.nz &&
+         x.n == y.n && x.seed == y.seed && memcmp(&x.time, &y.time, sizeof(float)) == 0 &&
+         memcmp(&x.lr_grid, &y.lr_grid, sizeof(float)) == 0 && memcmp(&x.lr_net, &y.lr_net, sizeof(float)) == 0 &&
+         memcmp(&x.grad_weight, &y.grad_weight, sizeof(float)) == 0 &&
+         memcmp(&x.grad_scale, &y.grad_scale, sizeof(float)) == 0 && x.loss == y.loss && x.grid_h == y.grid_h &&
+         x.weights_h == y.weights_h && x.adam_m == y.adam_m && x.adam_v == y.adam_v && x.grid == y.grid &&
+         x.weights == y.weights && x.biases == y.biases && x.cdf == y.cdf && x.cdf_res == y.cdf_res;
+}
+
+// Captures one step (fit step, grid refresh, step counter += 1) on the
+// context's own stream into ctx->graph_exec.
+cudaError_t capture_fit_graph(srn_ctx* ctx, const FitArgs& a) {
+  if (ctx->graph_exec) {
+    cudaGraphExecDestroy(ctx->graph_exec);
+    ctx->graph_exec = nullptr;
+  }
+  cudaError_t e = cudaSuccess;
+  if (!ctx->graph_stream) e = cudaStreamCreateWithFlags(&ctx->graph_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  // relaxed: the launchers set kernel attributes (shared-memory size) while capturing
+  e = cudaStreamBeginCapture(ctx->graph_stream, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return e;
+  cudaError_t le = enqueue_fit_step(ctx, a, ctx->graph_stream);
+  if (le == cudaSuccess) le = launch_step_counter(const_cast<int*>(a.step_ptr), 0, 1, ctx->graph_stream);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(ctx->graph_stream, &g);  // always ends the capture
+  if (le != cudaSuccess) e = le;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e == cudaSuccess) ctx->graph_key = a;
+  else ctx->graph_exec = nullptr;
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+srn_status srn_fit_step(srn_ctx* ctx, const float* volume_dev, const int dims[3], int n_points, uint64_t seed,
+                        int step, float time, float lr_grid, float lr_net, float grad_weight, float grad_scale,
+                        float* loss_dev, void* stream) {
+  FitArgs a;
+  srn_status st = make_fit_args(ctx, volume_dev, dims, n_points, seed, step, time, lr_grid, lr_net, grad_weight,
+                                grad_scale, loss_dev, &a);
+  if (st) return st;
+  st = use_device(ctx);
+  if (st) return st;
+  cudaError_t e = enqueue_fit_step(ctx, a, (cudaStream_t)stream);
   return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_fit_step");
+}
+
+srn_status srn_fit_steps(srn_ctx* ctx, const float* volume_dev, const int dims[3], int n_points, uint64_t seed,
+                         int first_step, int n_steps, float time, float lr_grid, float lr_net, float grad_weight,
+                         float grad_scale, float* loss_dev, void* stream) {
+  FitArgs a;
+  srn_status st = make_fit_args(ctx, volume_dev, dims, n_points, seed, first_step, time, lr_grid, lr_net,
+                                grad_weight, grad_scale, loss_dev, &a);
+  if (st) return st;
+  if (n_steps < 0 || first_step > INT_MAX - n_steps)
+    return fail(SRN_ERR_INVALID_ARG, "n_steps must be >= 0 and first_step + n_steps must fit an int");
+  if (n_steps == 0) return SRN_OK;
+  st = use_device(ctx);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  int* step_dev = reinterpret_cast<int*>(ctx->status + 1);
+  a.step_ptr = step_dev;
+  cudaError_t e = cudaSuccess;
+  // capturing records the launches without running them: nothing executes
+  // before the replays below, which are ordered on `stream`
+  if (!ctx->graph_exec || !same_graph_args(a, ctx->graph_key)) e = capture_fit_graph(ctx, a);
+  if (e == cudaSuccess) e = launch_step_counter(step_dev, first_step, 0, s);
+  for (int i = 0; i < n_steps && e == cudaSuccess; ++i) e = cudaGraphLaunch(ctx->graph_exec, s);
+  return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_fit_steps");
 }
 
 srn_status srn_sync_status(srn_ctx* ctx, void* stream) {

@@ -49,6 +49,7 @@ struct PointArgs {
   float gw, gs;
   const unsigned long long* cdf;  // Section 6.2 adaptive distribution (null: uniform)
   int cdf_res;
+  const int* step_ptr;            // step index in device memory (graph replay), else `step`
   float* pts;   // scratch out
   float* dz;
   unsigned int* key;
@@ -101,6 +102,7 @@ __global__ void __launch_bounds__(kFitThreads, 4) fit_point_kernel(const NetDev 
   float* sred = sacc + ((a.n_entries + 3) & ~3);
   load_net<C>(sm, L, net);
   const int tid = threadIdx.x;
+  const int step = a.step_ptr ? *a.step_ptr : a.step;
   for (int e = tid; e < a.n_entries; e += kFitThreads) sacc[e] = 0.f;
 
   // packed offsets of each layer's weights / biases in [W | b]
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(kFitThreads, 4) fit_point_kernel(const NetDev 
     float out[4] = {0.f, 0.f, 0.f, 0.f}, dout[4] = {0.f, 0.f, 0.f, 0.f};
     float hs[kMaxL][C];
     if (valid) {
-      if (a.mode == 0) p = sample::fit_point(a.cdf, a.cdf_res, a.seed, a.step, j, a.n);
+      if (a.mode == 0) p = sample::fit_point(a.cdf, a.cdf_res, a.seed, step, j, a.n);
       else p = clamp_p(make_float3(a.pts_in[3 * j], a.pts_in[3 * j + 1], a.pts_in[3 * j + 2]));
       forward<C, true>(sm, L, net.act, lat, p, out, hs);
       if (a.mode == 0) {
@@ -607,15 +609,18 @@ __global__ void __launch_bounds__(256) reduce_parts_kernel(const float* __restri
 // when the step produced a non-finite loss or gradient.
 __global__ void adam_kernel(float* __restrict__ grid, float* __restrict__ W, float* __restrict__ b,
                             const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v, size_t ng,
-                            size_t nW, size_t nb, float lr_grid, float lr_net, int step,
-                            const unsigned int* __restrict__ flag, unsigned int* __restrict__ status,
-                            __half* __restrict__ grid_h, __half* __restrict__ W_h) {
+                            size_t nW, size_t nb, float lr_grid, float lr_net, int step_arg,
+                            const int* __restrict__ step_ptr, const unsigned int* __restrict__ flag,
+                            unsigned int* __restrict__ status, __half* __restrict__ grid_h,
+                            __half* __restrict__ W_h) {
+  const int step = step_ptr ? *step_ptr : step_arg;
   if (*flag) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(status, (unsigned int)SRN_ERR_NONFINITE);
     return;
   }
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-  const float bc1 = 1.0f - powf(b1, (float)(step + 1)), bc2 = 1.0f - powf(b2, (float)(step + 1));
+  const float t1 = (float)step + 1.0f;  // exact below 2^24; no int overflow at INT_MAX
+  const float bc1 = 1.0f - powf(b1, t1), bc2 = 1.0f - powf(b2, t1);
   const size_t n = ng + nW + nb;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const float gi = g[i];
@@ -671,7 +676,8 @@ cudaError_t run_backward(FitScratch& s, const NetDev& net, PointArgs pa, float* 
     // tensor-core point kernel: one partial row per warpgroup
     const int rows = fit_mma_rows_per_cta();
     const int grid = std::max(1, std::min({sm_count(), s.max_cta / rows, (n + 128 * rows - 1) / (128 * rows)}));
-    PointArgsMma ma{n, pa.seed, pa.step, pa.time, pa.vol, pa.cdf, pa.cdf_res, s.pts, s.dz, s.key, s.idx, s.part};
+    PointArgsMma ma{n,      pa.seed, pa.step, pa.time, pa.vol, pa.cdf,   pa.cdf_res,
+                    pa.step_ptr, s.pts,  s.dz,    s.key,  s.idx,  s.part};
     e = launch_fit_mma(net, ma, grid, mma_status, st);
     if (e != cudaSuccess) return e;
     n_cta = grid * rows;
@@ -855,13 +861,25 @@ cudaError_t launch_fit_step(FitScratch& s, const NetDev& net, const FitArgs& a, 
   pa.gs = a.grad_scale;
   pa.cdf = a.cdf;
   pa.cdf_res = a.cdf_res;
+  pa.step_ptr = a.step_ptr;
   const size_t ng = s.n_grid, nW = net_weight_count(net), nb = net_bias_count(net);
   cudaError_t e = run_backward(s, net, pa, s.grads, s.grads + ng, s.grads + ng + nW, a.loss, st, a.status);
   if (e != cudaSuccess) return e;
   const size_t n = ng + nW + nb;
   unsigned int blocks = (unsigned int)std::min<size_t>((n + 255) / 256, (size_t)sm_count() * 8);
   adam_kernel<<<blocks, 256, 0, st>>>(a.grid, a.weights, a.biases, s.grads, a.adam_m, a.adam_v, ng, nW, nb, a.lr_grid,
-                                      a.lr_net, a.step, s.flag, a.status, a.grid_h, a.weights_h);
+                                      a.lr_net, a.step, a.step_ptr, s.flag, a.status, a.grid_h, a.weights_h);
+  return cudaGetLastError();
+}
+
+namespace {
+__global__ void step_counter_kernel(int* step, int value, int delta) {
+  *step = delta ? (int)((unsigned)*step + (unsigned)delta) : value;
+}
+}  // namespace
+
+cudaError_t launch_step_counter(int* step, int value, int delta, cudaStream_t st) {
+  step_counter_kernel<<<1, 1, 0, st>>>(step, value, delta);
   return cudaGetLastError();
 }
 

@@ -168,6 +168,7 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
   bool failed = false;
 
   const net32::Latent lat = net32::make_latent(net, a.time);
+  const int step = a.step_ptr ? *a.step_ptr : a.step;
   const float inv_n = 1.0f / (float)a.n;
   const int nchunks = (a.n + 127) / 128;
   const int wg_global = blockIdx.x * kFitWGS + wg, n_wg = gridDim.x * kFitWGS;
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
     const int j = chunk * 128 + row;
     const bool valid = j < a.n;
     float3 p = make_float3(0.5f, 0.5f, 0.5f);
-    if (valid) p = sample::fit_point(a.cdf, a.cdf_res, a.seed, a.step, j, a.n);
+    if (valid) p = sample::fit_point(a.cdf, a.cdf_res, a.seed, step, j, a.n);
     const float y = valid ? vol_sample(a.vol, p) : 0.0f;
 
     // ---- layer-0 input v0 in the tile's column order, FP16 hi + lo

@@ -27,7 +27,7 @@ EXPORTED = ["srn_version", "srn_last_error", "srn_create", "srn_destroy", "srn_s
             "srn_render", "srn_dvr_dense", "srn_eval", "srn_density_grad", "srn_backward", "srn_fit_step",
             "srn_sync_status", "srn_image_mse", "srn_backward_static", "srn_density_mse", "srn_resample",
             "srn_lowpass_resample", "srn_save", "srn_load", "srn_error_grid", "srn_fit_set_sampling",
-            "srn_fit_points"]
+            "srn_fit_points", "srn_fit_steps"]
 
 
 class SrnError(RuntimeError):
@@ -100,6 +100,7 @@ def lib():
         L.srn_error_grid.argtypes = [vp, vp, C.POINTER(C.c_int), i, i, C.c_uint64, f, vp, vp]
         L.srn_fit_set_sampling.argtypes = [vp, vp, i, vp]
         L.srn_fit_points.argtypes = [vp, i, C.c_uint64, i, vp, vp]
+        L.srn_fit_steps.argtypes = [vp, vp, C.POINTER(C.c_int), i, C.c_uint64, i, i, f, f, f, f, f, vp, vp]
         for name in EXPORTED[2:]:
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -235,6 +236,15 @@ def srn_fit_step(ctx, volume, n_points, seed, step, loss, lr_grid=1e-2, lr_net=5
     _check(lib().srn_fit_step(ctx, _ptr(volume), dims, int(n_points), int(seed), int(step), float(time),
                               float(lr_grid), float(lr_net), float(grad_weight), float(grad_scale), _ptr(loss),
                               _stream(stream)))
+
+
+def srn_fit_steps(ctx, volume, n_points, seed, first_step, n_steps, loss, lr_grid=1e-2, lr_net=5e-3, time=0.0,
+                  grad_weight=0.0, grad_scale=1.0, stream=None):
+    nz, ny, nx = volume.shape
+    dims = (C.c_int * 3)(nx, ny, nz)
+    _check(lib().srn_fit_steps(ctx, _ptr(volume), dims, int(n_points), int(seed), int(first_step), int(n_steps),
+                               float(time), float(lr_grid), float(lr_net), float(grad_weight), float(grad_scale),
+                               _ptr(loss), _stream(stream)))
 
 
 def srn_sync_status(ctx, stream=None):
