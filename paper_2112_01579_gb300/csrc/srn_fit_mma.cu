@@ -18,11 +18,12 @@
 //   cores (it feeds the latent-grid gradient, a sum with strong
 //   cancellation, so it keeps FP32 accuracy), overlapping the MMA below;
 // * weight gradient of layer 0: dW0^T = sum over points of v0 delta^T is an
-//   MMA with K = points: the thread also writes its v0 (hi, lo) and delta
-//   (hi, lo) as columns of two transposed tiles, and one M = 128 (v0 hi rows,
-//   v0 lo rows) x N = 64 (delta hi, delta lo) MMA per tile accumulates all
-//   four products in TMEM across the warpgroup's tiles.  The bias gradient
-//   of layer 0 is the row of the constant-1 column.
+//   MMA with K = points.  Both operands are read MN-major (one 128-byte row
+//   per point): A is the input tile itself (its v hi and v lo blocks, M =
+//   128 features), B a tile of the points' delta rows (hi, lo; N = 64), which
+//   every thread writes with vector stores.  One MMA per tile accumulates
+//   all four hi/lo products in TMEM across the warpgroup's tiles.  The bias
+//   gradient of layer 0 is the row of the constant-1 column.
 // * last-layer gradients and the loss are warp reductions in a fixed order.
 // Each warpgroup writes one partial row [W | b | loss], reduced with the FP32
 // path's rows by the same fixed-order kernel: the step is deterministic.
@@ -36,20 +37,19 @@ namespace {
 
 using namespace mma;
 
-constexpr int kFitWGS = 2;              // warpgroups per CTA (shared memory: ~222 KB)
+constexpr int kFitWGS = 2;              // warpgroups per CTA (registers: 255 per thread)
 constexpr int kFitTmemCols = 256;       // per warpgroup: 64 forward + 64 dW0 accumulator columns
 constexpr int kFitWgCols = 128;
 
 struct FitPlan {
-  int oAf, oAt, oBt, oB0, oWz, oWl, oFm, oSlot, oMbar, oMisc, total;
+  int oAf, oBt, oB0, oWz, oWl, oFm, oSlot, oMbar, oMisc, total;
 };
 
 FitPlan fit_plan(int m, int F) {
   FitPlan p;
   int o = 0;
-  p.oAf = o; o += kFitWGS * 3 * kTile;          // input rows [hi | lo | hi] (128 x 192 FP16)
-  p.oAt = o; o += kFitWGS * 2 * kTile;          // v0^T: 128 rows (hi, lo features) x 128 points
-  p.oBt = o; o += kFitWGS * 2 * 64 * 128;       // delta^T: 64 rows (hi, lo) x 128 points
+  p.oAf = o; o += kFitWGS * 2 * kTile;          // input rows [hi | lo] (128 points x 128 FP16)
+  p.oBt = o; o += kFitWGS * kTile;              // delta rows [hi | lo] (128 points x 64 FP16)
   p.oB0 = o; o += 3 * 32 * 128;                 // [W hi | W hi | W lo]: 32 rows x 192 columns
   p.oWz = o; o += F * 32 * 4;                    // FP32 latent columns of W0, [F][32]
   p.oWl = o; o += 64 * 4;
@@ -67,11 +67,21 @@ __device__ __forceinline__ uint32_t h16(float v) {
   return (uint32_t)__half_as_ushort(h);
 }
 
-// K-major, 128B-swizzled tile element (row r, column k) byte offset; atoms of
-// 64 columns are `atom` bytes apart.
-__device__ __forceinline__ uint32_t kel(int r, int k, int atom) {
-  return (uint32_t)((k >> 6) * atom) + sw_off(r, (k & 63) >> 3) + (uint32_t)((k & 7) * 2);
+// MN-major shared-memory descriptor, 128-byte swizzle: one 128-byte row of
+// 64 M (or N) elements per K index, 8-row groups 1024 bytes apart (SBO),
+// 64-element M blocks `lbo` bytes apart (LBO).
+__device__ __forceinline__ uint64_t sw128_mn_desc(uint32_t saddr, uint32_t lbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1u << 46;  // descriptor version
+  d |= (uint64_t)2u << 61;  // SWIZZLE_128B
+  return d;
 }
+
+// Weight-gradient MMA: M = 128, N = 64, A and B both MN-major (transpose bits).
+constexpr uint32_t kIdescGrad = idesc_n(64) | (1u << 15) | (1u << 16);
 
 template <int M, int F, int ACT>
 __global__ void __launch_bounds__(128 * kFitWGS, 1)
@@ -80,7 +90,6 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
   constexpr int D0 = 3 + 2 * M + F;
   static_assert(D0 + 2 <= 64, "layer-0 input (with the two bias columns) must fit 64 columns");
   constexpr bool SNAKE = ACT == SRN_ACT_SNAKEALT;
-  constexpr int ATOM_T = 64 * 128;  // bytes of a delta^T K-atom (64 rows)
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -91,9 +100,8 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
 
   const int tid = threadIdx.x;
   const int wg = tid >> 7, row = tid & 127, lane = tid & 31, warp = row >> 5;
-  uint8_t* Af = sm + plan.oAf + wg * 3 * kTile;
-  uint8_t* At = sm + plan.oAt + wg * 2 * kTile;
-  uint8_t* Bt = sm + plan.oBt + wg * 2 * ATOM_T;
+  uint8_t* Af = sm + plan.oAf + wg * 2 * kTile;
+  uint8_t* Bt = sm + plan.oBt + wg * kTile;
   uint8_t* B0 = sm + plan.oB0;
   float* wz = reinterpret_cast<float*>(sm + plan.oWz);
   float* slot = reinterpret_cast<float*>(sm + plan.oSlot) + (wg * 4 + warp) * 34;
@@ -160,7 +168,7 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
   const uint32_t d_dw = d_acc + 64;                           // dW0 accumulator (64 columns)
   const uint32_t t_row = d_acc + ((uint32_t)(warp * 32) << 16);
   const uint32_t t_dw = d_dw + ((uint32_t)(warp * 32) << 16);
-  const uint32_t af_addr = smem_u32(Af), at_addr = smem_u32(At), bt_addr = smem_u32(Bt);
+  const uint32_t af_addr = smem_u32(Af), bt_addr = smem_u32(Bt);
   const uint32_t b0_addr = smem_u32(B0);
   const uint32_t mb = smem_u32(&mbar[wg]);
   const int bar_id = 1 + wg;
@@ -219,16 +227,9 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
         const float2 hb = __half22float2(h);
         hi[e] = *reinterpret_cast<const uint32_t*>(&h);
         lo[e] = pack_h2(a0 - hb.x, a1 - hb.y);
-        // the transposed copy for the weight gradient: rows f (hi) and 64 + f (lo), column = point
-        const int f0 = 8 * cg + 2 * e;
-        *reinterpret_cast<uint16_t*>(At + kel(f0, row, kTile)) = (uint16_t)(hi[e] & 0xffffu);
-        *reinterpret_cast<uint16_t*>(At + kel(f0 + 1, row, kTile)) = (uint16_t)(hi[e] >> 16);
-        *reinterpret_cast<uint16_t*>(At + kel(64 + f0, row, kTile)) = (uint16_t)(lo[e] & 0xffffu);
-        *reinterpret_cast<uint16_t*>(At + kel(65 + f0, row, kTile)) = (uint16_t)(lo[e] >> 16);
       }
       *reinterpret_cast<uint4*>(Af + a_off(row, cg)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
       *reinterpret_cast<uint4*>(Af + a_off(row, 8 + cg)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-      *reinterpret_cast<uint4*>(Af + a_off(row, 16 + cg)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
     }
     fence_proxy_async();
     tc_fence_before();
@@ -236,11 +237,12 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
     if (misc[4 + wg]) break;
     if (row == 0) {
       tc_fence_after();
+      // K blocks [v hi | v lo | v hi] x [W hi | W hi | W lo]: the third A block is the first
 #pragma unroll
       for (int kk = 0; kk < 12; ++kk) {
         const uint32_t ka = kk >> 2, kb = (kk & 3) * 32;
-        mma_f16(d_acc, sw128_desc(af_addr + ka * kTile + kb), sw128_desc(b0_addr + ka * (32 * 128) + kb),
-                idesc_n(32), kk > 0);
+        mma_f16(d_acc, sw128_desc(af_addr + (ka == 2 ? 0u : ka) * kTile + kb),
+                sw128_desc(b0_addr + ka * (32 * 128) + kb), idesc_n(32), kk > 0);
       }
       mma_commit(mb);
     }
@@ -293,22 +295,20 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
 #pragma unroll
     for (int o = 0; o < C; ++o) delta[o] = dout * wl[o] * dact[o];
 
-    // ---- delta as columns of the transposed tile (weight gradient)
+    // ---- the point's delta row [hi (32) | lo (32)] (weight gradient, MN-major B)
 #pragma unroll
     for (int cg = 0; cg < 4; ++cg) {
+      uint32_t hi[4], lo[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const float a0 = delta[8 * cg + 2 * e], a1 = delta[8 * cg + 2 * e + 1];
         const __half2 h = __floats2half2_rn(a0, a1);
         const float2 hb = __half22float2(h);
-        const uint32_t hi = *reinterpret_cast<const uint32_t*>(&h);
-        const uint32_t lo = pack_h2(a0 - hb.x, a1 - hb.y);
-        const int o0 = 8 * cg + 2 * e;
-        *reinterpret_cast<uint16_t*>(Bt + kel(o0, row, ATOM_T)) = (uint16_t)(hi & 0xffffu);
-        *reinterpret_cast<uint16_t*>(Bt + kel(o0 + 1, row, ATOM_T)) = (uint16_t)(hi >> 16);
-        *reinterpret_cast<uint16_t*>(Bt + kel(32 + o0, row, ATOM_T)) = (uint16_t)(lo & 0xffffu);
-        *reinterpret_cast<uint16_t*>(Bt + kel(33 + o0, row, ATOM_T)) = (uint16_t)(lo >> 16);
+        hi[e] = *reinterpret_cast<const uint32_t*>(&h);
+        lo[e] = pack_h2(a0 - hb.x, a1 - hb.y);
       }
+      *reinterpret_cast<uint4*>(Bt + sw_off(row, cg)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<uint4*>(Bt + sw_off(row, 4 + cg)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
     fence_proxy_async();
     tc_fence_before();
@@ -316,12 +316,12 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
     if (misc[4 + wg]) break;
     if (row == 0) {
       tc_fence_after();
-      // dW0^T += v0^T delta over this tile's points (M = 128 v0 rows, N = 64 delta rows, K = 128 points)
+      // dW0^T += v0^T delta over this tile's points (M = 128: v hi, v lo features; N = 64: delta hi,
+      // delta lo; K = 128 points, 16 rows = 2048 bytes per MMA)
 #pragma unroll
       for (int kk = 0; kk < 8; ++kk) {
-        const uint32_t ka = kk >> 2, kb = (kk & 3) * 32;
-        mma_f16(d_dw, sw128_desc(at_addr + ka * kTile + kb), sw128_desc(bt_addr + ka * ATOM_T + kb), idesc_n(64),
-                (first && kk == 0) ? 0u : 1u);
+        mma_f16(d_dw, sw128_mn_desc(af_addr + kk * 2048, kTile), sw128_mn_desc(bt_addr + kk * 2048, kTile),
+                kIdescGrad, (first && kk == 0) ? 0u : 1u);
       }
       mma_commit(mb);
     }
@@ -359,8 +359,8 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
       a.key[j] = (unsigned)((iz * (lat.R - 1) + iy) * (lat.R - 1) + ix);
       a.idx[j] = (unsigned)j;
     }
-    // the weight-gradient MMA reads this tile's transposed rows: wait before
-    // the next tile overwrites them
+    // the weight-gradient MMA reads this tile's input and delta rows: wait
+    // before the next tile overwrites them
     if (!__all_sync(0xffffffffu, mbar_wait_bounded(mb, phase))) {
       failed = true;
       misc[4 + wg] = 1;
