@@ -37,8 +37,8 @@ namespace {
 
 using namespace mma;
 
-constexpr int kFitWGS = 2;              // warpgroups per CTA (registers: 255 per thread)
-constexpr int kFitTmemCols = 256;       // per warpgroup: 64 forward + 64 dW0 accumulator columns
+constexpr int kFitWGS = 3;              // warpgroups per CTA (registers: 168 per thread)
+constexpr int kFitTmemCols = 512;       // 128 columns per warpgroup (64 forward + 64 dW0), power of two
 constexpr int kFitWgCols = 128;
 
 struct FitPlan {
