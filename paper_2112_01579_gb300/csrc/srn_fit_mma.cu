@@ -222,11 +222,7 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
       uint32_t hi[4], lo[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const float a0 = v[8 * cg + 2 * e], a1 = v[8 * cg + 2 * e + 1];
-        const __half2 h = __floats2half2_rn(a0, a1);
-        const float2 hb = __half22float2(h);
-        hi[e] = *reinterpret_cast<const uint32_t*>(&h);
-        lo[e] = pack_h2(a0 - hb.x, a1 - hb.y);
+        split_h2(v[8 * cg + 2 * e], v[8 * cg + 2 * e + 1], hi[e], lo[e]);
       }
       *reinterpret_cast<uint4*>(Af + a_off(row, cg)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
       *reinterpret_cast<uint4*>(Af + a_off(row, 8 + cg)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
@@ -301,11 +297,7 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
       uint32_t hi[4], lo[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const float a0 = delta[8 * cg + 2 * e], a1 = delta[8 * cg + 2 * e + 1];
-        const __half2 h = __floats2half2_rn(a0, a1);
-        const float2 hb = __half22float2(h);
-        hi[e] = *reinterpret_cast<const uint32_t*>(&h);
-        lo[e] = pack_h2(a0 - hb.x, a1 - hb.y);
+        split_h2(delta[8 * cg + 2 * e], delta[8 * cg + 2 * e + 1], hi[e], lo[e]);
       }
       *reinterpret_cast<uint4*>(Bt + sw_off(row, cg)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
       *reinterpret_cast<uint4*>(Bt + sw_off(row, 4 + cg)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);

@@ -163,6 +163,22 @@ __device__ __forceinline__ uint32_t pack_h2(float a, float b) {
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
+// FP16 hi + lo split of a pair: hi = fp16(a), lo = fp16(a - hi).  The
+// residual a - hi is exact in FP32; it is formed by one mixed-precision add
+// per element ((-hi) in FP16 plus a in FP32) instead of widening hi first.
+__device__ __forceinline__ void split_h2(float a0, float a1, uint32_t& hi, uint32_t& lo) {
+  hi = pack_h2(a0, a1);
+  const uint32_t neg = hi ^ 0x80008000u;
+  float r0, r1;
+  asm("{.reg .b16 x, y;\n\t"
+      "mov.b32 {x, y}, %2;\n\t"
+      "add.rn.f32.f16 %0, x, %3;\n\t"
+      "add.rn.f32.f16 %1, y, %4;}"
+      : "=f"(r0), "=f"(r1)
+      : "r"(neg), "f"(a0), "f"(a1));
+  lo = pack_h2(r0, r1);
+}
+
 // Activation value handed to the next layer from the accumulator value: sin(x)
 // for the sine network; for SnakeAlt the accumulator holds u = 2x and the
 // value is u / 2 - cos u = 2 SnakeAlt(x) - 1.
@@ -785,11 +801,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
             uint32_t hi[4], lo[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-              const float a0 = act_fold<ACT>(x[8 * j + 2 * e]), a1 = act_fold<ACT>(x[8 * j + 2 * e + 1]);
-              const __half2 h = __floats2half2_rn(a0, a1);
-              const float2 hb = __half22float2(h);
-              hi[e] = *reinterpret_cast<const uint32_t*>(&h);
-              lo[e] = pack_h2(a0 - hb.x, a1 - hb.y);
+              split_h2(act_fold<ACT>(x[8 * j + 2 * e]), act_fold<ACT>(x[8 * j + 2 * e + 1]), hi[e], lo[e]);
             }
             *reinterpret_cast<uint4*>(A + a_off(row, j)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
             *reinterpret_cast<uint4*>(A + a_off(row, C / 8 + j)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
@@ -854,11 +866,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
             uint32_t hi[4], lo[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-              const float a0 = dl[8 * j + 2 * e], a1 = dl[8 * j + 2 * e + 1];
-              const __half2 hh = __floats2half2_rn(a0, a1);
-              const float2 hb = __half22float2(hh);
-              hi[e] = *reinterpret_cast<const uint32_t*>(&hh);
-              lo[e] = pack_h2(a0 - hb.x, a1 - hb.y);
+              split_h2(dl[8 * j + 2 * e], dl[8 * j + 2 * e + 1], hi[e], lo[e]);
             }
             *reinterpret_cast<uint4*>(A + a_off(row, j)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
             *reinterpret_cast<uint4*>(A + a_off(row, C / 8 + j)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
