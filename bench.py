@@ -652,7 +652,7 @@ TRANSC_PER_SAMPLE = 3 * 32 + 2 * 14 + 1
 SMS, MUFU_PER_SM_CLK, FP32_PER_SM_CLK, MAX_SM_GHZ = 152, 16, 128, 2.07
 # DRAM bytes of one 1024^2 frame of the render kernel, from the ncu capture
 # summarised in profiles/ (null when the kernel changed after the capture).
-RENDER_DRAM_BYTES = 1145344
+RENDER_DRAM_BYTES = 1143552
 
 
 def roofline(res):

@@ -302,7 +302,9 @@ srn_status srn_fit_points(srn_ctx* ctx, int n_points, uint64_t seed, int step, f
 
 /* Mean squared difference of two float32 arrays of n values (densities):
  * PSNR = 10 log10(1 / MSE) for volumes normalised to [0,1] (Section 6
- * reports reconstruction PSNR).  One double to mse_dev; deterministic. */
+ * reports reconstruction PSNR).  One double to mse_dev; deterministic (a
+ * fixed two-level FP64 reduction over all SMs whose 8 KB of partial sums
+ * are stream-ordered scratch: cudaMallocAsync / cudaFreeAsync on `stream`). */
 srn_status srn_density_mse(const float* a_dev, const float* b_dev, long long n, double* mse_dev, void* stream);
 
 /* Vertex-aligned trilinear resampling of a float32 volume src_dims = {nx,
@@ -373,7 +375,8 @@ srn_status srn_sync_status(srn_ctx* ctx, void* stream);
 
 /* Mean squared error over the RGB channels of n RGBA float32 pixels, the
  * quantity behind the PSNR = 10 log10(1 / MSE) the paper reports for image
- * quality (Section 6).  Writes one double to mse_dev; deterministic. */
+ * quality (Section 6).  Writes one double to mse_dev; deterministic, with
+ * the reduction and scratch of srn_density_mse. */
 srn_status srn_image_mse(const float* a_dev, const float* b_dev, long long n_pixels, double* mse_dev,
                          void* stream);
 

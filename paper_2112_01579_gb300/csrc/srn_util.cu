@@ -12,44 +12,67 @@ __global__ void to_half_kernel(const float* __restrict__ src, __half* __restrict
   for (; i < n; i += stride) dst[i] = __float2half_rn(src[i]);
 }
 
-// Mean squared error over the RGB channels of n RGBA pixels.  One block,
-// fixed thread-to-pixel assignment and a fixed reduction tree, so the result
-// is deterministic.
-constexpr int kMseThreads = 1024;
-__global__ void __launch_bounds__(kMseThreads) mse_kernel(const float4* __restrict__ a, const float4* __restrict__ b,
-                                                          long long n, double* __restrict__ out) {
-  __shared__ double part[kMseThreads];
-  double s = 0.0;
-  for (long long i = threadIdx.x; i < n; i += kMseThreads) {
-    float4 x = a[i], y = b[i];
-    double d0 = (double)x.x - y.x, d1 = (double)x.y - y.y, d2 = (double)x.z - y.z;
-    s += d0 * d0 + d1 * d1 + d2 * d2;
+// Mean squared differences (image RGB, density) in FP64 over every SM, and
+// still deterministic: element range b of kMseParts fixed, equal ranges
+// (they depend on n only) is summed by block b in a fixed thread order and
+// tree, and one block adds the kMseParts partial sums in a fixed tree.  The
+// partial sums live in stream-ordered scratch of kMseParts doubles.
+constexpr int kMseThreads = 256;
+constexpr int kMseParts = 1024;
+
+template <int V>  // V = 4: RGBA pixels, RGB compared; V = 1: scalars
+__device__ __forceinline__ double sq_diff(const float* __restrict__ a, const float* __restrict__ b, long long i) {
+  if constexpr (V == 4) {
+    const float4 x = reinterpret_cast<const float4*>(a)[i], y = reinterpret_cast<const float4*>(b)[i];
+    const double d0 = (double)x.x - y.x, d1 = (double)x.y - y.y, d2 = (double)x.z - y.z;
+    return d0 * d0 + d1 * d1 + d2 * d2;
+  } else {
+    const double d = (double)a[i] - (double)b[i];
+    return d * d;
   }
-  part[threadIdx.x] = s;
-  __syncthreads();
-  for (int w = kMseThreads / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *out = n > 0 ? part[0] / (3.0 * (double)n) : 0.0;
 }
 
-// Mean squared difference of two float arrays (one block, fixed order).
-__global__ void __launch_bounds__(kMseThreads) mse1_kernel(const float* __restrict__ a, const float* __restrict__ b,
-                                                           long long n, double* __restrict__ out) {
-  __shared__ double part[kMseThreads];
-  double s = 0.0;
-  for (long long i = threadIdx.x; i < n; i += kMseThreads) {
-    const double d = (double)a[i] - (double)b[i];
-    s += d * d;
-  }
+template <int NT>
+__device__ __forceinline__ double block_sum(double s, double* part) {
   part[threadIdx.x] = s;
   __syncthreads();
-  for (int w = kMseThreads / 2; w > 0; w >>= 1) {
+#pragma unroll 1
+  for (int w = NT / 2; w > 0; w >>= 1) {
     if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *out = n > 0 ? part[0] / (double)n : 0.0;
+  return part[0];
+}
+
+template <int V>
+__global__ void __launch_bounds__(kMseThreads) mse_part_kernel(const float* __restrict__ a, const float* __restrict__ b,
+                                                               long long n, double* __restrict__ parts) {
+  __shared__ double part[kMseThreads];
+  const long long per = (n + kMseParts - 1) / kMseParts;
+  const long long lo = (long long)blockIdx.x * per, hi = lo + per < n ? lo + per : n;
+  double s = 0.0;
+  for (long long i = lo + threadIdx.x; i < hi; i += kMseThreads) s += sq_diff<V>(a, b, i);
+  const double t = block_sum<kMseThreads>(s, part);
+  if (threadIdx.x == 0) parts[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kMseParts) mse_final_kernel(const double* __restrict__ parts, double denom,
+                                                              double* __restrict__ out) {
+  __shared__ double part[kMseParts];
+  const double t = block_sum<kMseParts>(parts[threadIdx.x], part);
+  if (threadIdx.x == 0) *out = denom > 0.0 ? t / denom : 0.0;
+}
+
+template <int V>
+cudaError_t launch_mse(const float* a, const float* b, long long n, double denom, double* out, cudaStream_t s) {
+  double* parts = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&parts, kMseParts * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  mse_part_kernel<V><<<kMseParts, kMseThreads, 0, s>>>(a, b, n, parts);
+  mse_final_kernel<<<1, kMseParts, 0, s>>>(parts, denom, out);
+  e = cudaGetLastError();
+  const cudaError_t f = cudaFreeAsync(parts, s);
+  return e != cudaSuccess ? e : f;
 }
 
 // One separable Gaussian pass along `axis` with clamp-to-edge: normalised
@@ -138,8 +161,7 @@ unsigned int grid_for(long long n) {
 }  // namespace
 
 cudaError_t launch_density_mse(const float* a, const float* b, long long n, double* out, cudaStream_t s) {
-  mse1_kernel<<<1, kMseThreads, 0, s>>>(a, b, n, out);
-  return cudaGetLastError();
+  return launch_mse<1>(a, b, n, (double)n, out, s);
 }
 
 cudaError_t launch_resample(const float* src, const int sdims[3], float* dst, const int ddims[3], cudaStream_t s) {
@@ -184,9 +206,7 @@ cudaError_t launch_to_half(const float* src, __half* dst, size_t n, cudaStream_t
 }
 
 cudaError_t launch_image_mse(const float* a, const float* b, long long n, double* out, cudaStream_t s) {
-  mse_kernel<<<1, kMseThreads, 0, s>>>(reinterpret_cast<const float4*>(a), reinterpret_cast<const float4*>(b), n,
-                                       out);
-  return cudaGetLastError();
+  return launch_mse<4>(a, b, n, 3.0 * (double)n, out, s);
 }
 
 }  // namespace srn

@@ -208,3 +208,27 @@ def test_image_mse(srn):
     torch.cuda.synchronize()
     ref = 10 ** (-oracle.psnr(a.cpu().numpy(), b.cpu().numpy()) / 10)
     assert abs(out.item() - ref) <= 1e-9
+
+
+@pytest.mark.parametrize("n", [0, 1, 1000, 1025, 4194307])
+def test_mse_reductions(srn, n):
+    """Density and image MSE against FP64 numpy: empty input, fewer values
+    than partial sums, a ragged last range, 4 M values; two calls agree bit
+    for bit."""
+    import torch
+    S = srn
+    g = torch.Generator(device="cuda").manual_seed(n)
+    a = torch.rand(4 * n, device="cuda", generator=g)
+    b = torch.rand(4 * n, device="cuda", generator=g)
+    out = torch.full((2,), -1.0, dtype=torch.float64, device="cuda")
+    an, bn = a.double().cpu().numpy(), b.double().cpu().numpy()
+    S.srn_density_mse(a, b, out[0:1])
+    S.srn_density_mse(a, b, out[1:2])
+    torch.cuda.synchronize()
+    ref = float(np.mean((an - bn) ** 2)) if n else 0.0
+    assert abs(out[0].item() - ref) <= 1e-12 * max(ref, 1.0) and out[0].item() == out[1].item()
+    S.srn_image_mse(a.view(-1, 4), b.view(-1, 4), out[0:1])
+    torch.cuda.synchronize()
+    d = (an - bn).reshape(-1, 4)[:, :3]
+    ref = float(np.mean(d ** 2)) if n else 0.0
+    assert abs(out[0].item() - ref) <= 1e-12 * max(ref, 1.0)
