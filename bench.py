@@ -377,18 +377,23 @@ def run_ours(args, rank, world):
     # dense DVR of the full volume
     M, lp_grid, lp_dpsnr = lowpass_baseline(vol, 32, 16)
     lp_img = torch.zeros_like(out[0])
-    psnrs, lp_psnrs = [], []
+    psnrs, lp_psnrs, ssims, lp_ssims = [], [], [], []
     mse = torch.zeros(1, dtype=torch.float64, device=dev)
+    ssim = torch.zeros(1, dtype=torch.float64, device=dev)
     for v in range(N_VIEWS):
         srn.srn_render(net.ctx, [cams[v]], tf, desc, out)
         srn.srn_dvr_dense(vol, [cams[v]], tf, desc, dense)
         srn.srn_image_mse(out, dense, mse)
+        srn.srn_image_ssim(out[0, 0], dense[0], ssim)
         torch.cuda.synchronize()
         psnrs.append(10 * math.log10(1.0 / max(mse.item(), 1e-30)))
+        ssims.append(ssim.item())
         srn.srn_dvr_dense(lp_grid, [cams[v]], tf, desc, lp_img)
         srn.srn_image_mse(lp_img, dense, mse)
+        srn.srn_image_ssim(lp_img[0], dense[0], ssim)
         torch.cuda.synchronize()
         lp_psnrs.append(10 * math.log10(1.0 / max(mse.item(), 1e-30)))
+        lp_ssims.append(ssim.item())
     pts = vertex_points(vol.shape[0])
     fvsrn_dpsnr = density_psnr_network(net, vol, pts)
     # the paper's 8-bit latent grid (Section 4.2) on the same fitted network
@@ -419,6 +424,7 @@ def run_ours(args, rank, world):
                    "fvsrn_ms_per_frame": ms_frame, "dense_dvr_ms_per_frame": float(np.median(d_ms)),
                    "psnr_fvsrn_vs_dense_db": float(np.mean(psnrs)),
                    "psnr_lowpass_grid_vs_dense_db": float(np.mean(lp_psnrs)), "lowpass_grid": M,
+                   "ssim_fvsrn_vs_dense": float(np.mean(ssims)), "ssim_lowpass_grid_vs_dense": float(np.mean(lp_ssims)),
                    "density_psnr_fvsrn_db": fvsrn_dpsnr, "density_psnr_lowpass_db": lp_dpsnr, "u8_grid": u8,
                    "fit_render_network": fit_info,
                    "fit_steps_per_s": cfg3["steps_per_s"] if cfg3 else None, "fit_cfg3": cfg3,

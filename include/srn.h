@@ -380,6 +380,18 @@ srn_status srn_sync_status(srn_ctx* ctx, void* stream);
 srn_status srn_image_mse(const float* a_dev, const float* b_dev, long long n_pixels, double* mse_dev,
                          void* stream);
 
+/* Structural similarity (Wang, Bovik, Sheikh, Simoncelli 2004) of two
+ * height x width RGBA float32 images ([y][x][4], 16-byte aligned; alpha
+ * ignored), the second image-quality measure the evaluation states beside
+ * PSNR (Section 6): 11 x 11 Gaussian window of sigma 1.5 normalised to sum
+ * 1, K1 = 0.01, K2 = 0.03, dynamic range 1; the mean over the R, G, B
+ * channels and every window centre whose window lies inside the image
+ * (1.0 when none does).  Computed in FP64; one double to ssim_dev;
+ * deterministic (fixed tiles, fixed-order sums; stream-ordered scratch of
+ * one double per 32 x 8 tile of window centres).  width, height >= 1. */
+srn_status srn_image_ssim(const float* a_dev, const float* b_dev, int width, int height, double* ssim_dev,
+                          void* stream);
+
 #ifdef __cplusplus
 }
 #endif

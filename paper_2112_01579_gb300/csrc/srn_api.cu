@@ -496,6 +496,15 @@ srn_status srn_image_mse(const float* a_dev, const float* b_dev, long long n_pix
   return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_image_mse");
 }
 
+srn_status srn_image_ssim(const float* a_dev, const float* b_dev, int width, int height, double* ssim_dev,
+                          void* stream) {
+  if (width < 1 || height < 1 || !a_dev || !b_dev || !ssim_dev)
+    return fail(SRN_ERR_INVALID_ARG, "images of at least 1 x 1 pixels and the output are required");
+  if (!aligned16(a_dev) || !aligned16(b_dev)) return fail(SRN_ERR_INVALID_ARG, "images must be 16-byte aligned");
+  cudaError_t e = launch_image_ssim(a_dev, b_dev, width, height, ssim_dev, (cudaStream_t)stream);
+  return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_image_ssim");
+}
+
 namespace {
 
 const char kCkptMagic[8] = {'S', 'R', 'N', 'C', 'K', 'P', 'T', '1'};

@@ -75,6 +75,7 @@ cudaError_t launch_to_half(const float* src, __half* dst, size_t n, cudaStream_t
 cudaError_t launch_quantize_grid(const float* grid, size_t n_vert, int F, uint8_t* q, float* qp, cudaStream_t s);
 cudaError_t launch_image_mse(const float* a, const float* b, long long n, double* out, cudaStream_t s);
 cudaError_t launch_density_mse(const float* a, const float* b, long long n, double* out, cudaStream_t s);
+cudaError_t launch_image_ssim(const float* a, const float* b, int W, int H, double* out, cudaStream_t s);
 cudaError_t launch_resample(const float* src, const int sdims[3], float* dst, const int ddims[3], cudaStream_t s);
 bool lowpass_supported(const int dims[3], int M);
 cudaError_t launch_lowpass_resample(const float* vol, const int dims[3], int M, float* tmp, float* out,

@@ -75,6 +75,98 @@ cudaError_t launch_mse(const float* a, const float* b, long long n, double denom
   return e != cudaSuccess ? e : f;
 }
 
+// SSIM (Wang, Bovik, Sheikh, Simoncelli 2004) of two H x W RGBA images over
+// the RGB channels: 11 x 11 Gaussian window (sigma 1.5, normalised), K1
+// 0.01, K2 0.03, dynamic range 1, windows entirely inside the image, mean
+// over channels and window centres.  FP64 throughout: FP32 inputs widen
+// exactly and their products are exact in FP64, so the local variances
+// sxx - mx^2 lose nothing to cancellation beyond FP64 rounding.  A block
+// owns a 32 x 8 tile of window centres: it stages the tile's 42 x 18 halo of
+// one channel in shared memory, filters rows, then columns, and sums its
+// SSIM values in a fixed tree; the per-block sums are added in block order.
+constexpr int kSsimTX = 32, kSsimTY = 8, kSsimR = 5;
+constexpr int kSsimHX = kSsimTX + 2 * kSsimR, kSsimHY = kSsimTY + 2 * kSsimR;
+
+__global__ void __launch_bounds__(kSsimTX * kSsimTY) ssim_tile_kernel(const float4* __restrict__ a,
+                                                                      const float4* __restrict__ b, int W, int H,
+                                                                      double* __restrict__ parts) {
+  __shared__ double w[2 * kSsimR + 1];
+  __shared__ double va[kSsimHY][kSsimHX], vb[kSsimHY][kSsimHX];
+  __shared__ double hs[5][kSsimHY][kSsimTX];  // row-filtered a, b, aa, bb, ab
+  __shared__ double part[kSsimTX * kSsimTY];
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    double t[2 * kSsimR + 1], sum = 0.0;
+    for (int k = 0; k <= 2 * kSsimR; ++k) {
+      t[k] = exp(-0.5 * (double)((k - kSsimR) * (k - kSsimR)) / (1.5 * 1.5));
+      sum += t[k];
+    }
+    for (int k = 0; k <= 2 * kSsimR; ++k) w[k] = t[k] / sum;
+  }
+  const int Wv = W - 2 * kSsimR, Hv = H - 2 * kSsimR;  // window centres (> 0 here)
+  const int x0 = blockIdx.x * kSsimTX, y0 = blockIdx.y * kSsimTY;  // first centre, minus kSsimR
+  const int ox = tid % kSsimTX, oy = tid / kSsimTX;
+  const bool valid = x0 + ox < Wv && y0 + oy < Hv;
+  const double C1 = 0.01 * 0.01, C2 = 0.03 * 0.03;
+  double acc = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    __syncthreads();
+    for (int i = tid; i < kSsimHX * kSsimHY; i += kSsimTX * kSsimTY) {
+      const int hx = i % kSsimHX, hy = i / kSsimHX;
+      const int gx = min(x0 + hx, W - 1), gy = min(y0 + hy, H - 1);  // clamped: only feeds unused centres
+      const float4 pa = a[(size_t)gy * W + gx], pb = b[(size_t)gy * W + gx];
+      va[hy][hx] = (double)(c == 0 ? pa.x : (c == 1 ? pa.y : pa.z));
+      vb[hy][hx] = (double)(c == 0 ? pb.x : (c == 1 ? pb.y : pb.z));
+    }
+    __syncthreads();
+    for (int i = tid; i < kSsimHY * kSsimTX; i += kSsimTX * kSsimTY) {
+      const int tx = i % kSsimTX, hy = i / kSsimTX;
+      double m1 = 0.0, m2 = 0.0, s11 = 0.0, s22 = 0.0, s12 = 0.0;
+      for (int k = 0; k <= 2 * kSsimR; ++k) {
+        const double p = va[hy][tx + k], q = vb[hy][tx + k], wk = w[k];
+        m1 = fma(wk, p, m1);
+        m2 = fma(wk, q, m2);
+        s11 = fma(wk, p * p, s11);
+        s22 = fma(wk, q * q, s22);
+        s12 = fma(wk, p * q, s12);
+      }
+      hs[0][hy][tx] = m1;
+      hs[1][hy][tx] = m2;
+      hs[2][hy][tx] = s11;
+      hs[3][hy][tx] = s22;
+      hs[4][hy][tx] = s12;
+    }
+    __syncthreads();
+    if (valid) {
+      double m1 = 0.0, m2 = 0.0, s11 = 0.0, s22 = 0.0, s12 = 0.0;
+      for (int k = 0; k <= 2 * kSsimR; ++k) {
+        const double wk = w[k];
+        m1 = fma(wk, hs[0][oy + k][ox], m1);
+        m2 = fma(wk, hs[1][oy + k][ox], m2);
+        s11 = fma(wk, hs[2][oy + k][ox], s11);
+        s22 = fma(wk, hs[3][oy + k][ox], s22);
+        s12 = fma(wk, hs[4][oy + k][ox], s12);
+      }
+      const double v1 = s11 - m1 * m1, v2 = s22 - m2 * m2, cv = s12 - m1 * m2;
+      acc += ((2.0 * m1 * m2 + C1) * (2.0 * cv + C2)) / ((m1 * m1 + m2 * m2 + C1) * (v1 + v2 + C2));
+    }
+  }
+  const double t = block_sum<kSsimTX * kSsimTY>(acc, part);
+  if (tid == 0) parts[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
+}
+
+// Sum of n partial sums in index order per thread, then a fixed tree.
+__global__ void __launch_bounds__(kMseParts) sum_parts_kernel(const double* __restrict__ parts, long long n,
+                                                              double denom, double* __restrict__ out) {
+  __shared__ double part[kMseParts];
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < n; i += kMseParts) s += parts[i];
+  const double t = block_sum<kMseParts>(s, part);
+  if (threadIdx.x == 0) *out = t / denom;
+}
+
+__global__ void set_double_kernel(double* out, double v) { *out = v; }
+
 // One separable Gaussian pass along `axis` with clamp-to-edge: normalised
 // weights exp(-k^2 / (2 sigma^2)), |k| <= ceil(3 sigma).
 constexpr int kMaxTaps = 257;
@@ -217,6 +309,25 @@ cudaError_t launch_quantize_grid(const float* grid, size_t n_vert, int F, uint8_
   channel_range_kernel<<<F, kQThreads, 0, s>>>(grid, n_vert, F, qp);
   quantize_kernel<<<grid_for((long long)(n_vert * F)), 256, 0, s>>>(grid, n_vert * F, F, qp, q);
   return cudaGetLastError();
+}
+
+cudaError_t launch_image_ssim(const float* a, const float* b, int W, int H, double* out, cudaStream_t s) {
+  const int Wv = W - 2 * kSsimR, Hv = H - 2 * kSsimR;
+  if (Wv <= 0 || Hv <= 0) {  // no window fits: SSIM 1 by convention
+    set_double_kernel<<<1, 1, 0, s>>>(out, 1.0);
+    return cudaGetLastError();
+  }
+  const dim3 grid((Wv + kSsimTX - 1) / kSsimTX, (Hv + kSsimTY - 1) / kSsimTY);
+  const long long nb = (long long)grid.x * grid.y;
+  double* parts = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&parts, (size_t)nb * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  ssim_tile_kernel<<<grid, kSsimTX * kSsimTY, 0, s>>>(reinterpret_cast<const float4*>(a),
+                                                       reinterpret_cast<const float4*>(b), W, H, parts);
+  sum_parts_kernel<<<1, kMseParts, 0, s>>>(parts, nb, 3.0 * (double)Wv * (double)Hv, out);
+  e = cudaGetLastError();
+  const cudaError_t f = cudaFreeAsync(parts, s);
+  return e != cudaSuccess ? e : f;
 }
 
 }  // namespace srn

@@ -27,7 +27,7 @@ EXPORTED = ["srn_version", "srn_last_error", "srn_create", "srn_destroy", "srn_s
             "srn_render", "srn_dvr_dense", "srn_eval", "srn_density_grad", "srn_backward", "srn_fit_step",
             "srn_sync_status", "srn_image_mse", "srn_backward_static", "srn_density_mse", "srn_resample",
             "srn_lowpass_resample", "srn_save", "srn_load", "srn_error_grid", "srn_fit_set_sampling",
-            "srn_fit_points", "srn_fit_steps"]
+            "srn_fit_points", "srn_fit_steps", "srn_image_ssim"]
 
 
 class SrnError(RuntimeError):
@@ -101,6 +101,7 @@ def lib():
         L.srn_fit_set_sampling.argtypes = [vp, vp, i, vp]
         L.srn_fit_points.argtypes = [vp, i, C.c_uint64, i, vp, vp]
         L.srn_fit_steps.argtypes = [vp, vp, C.POINTER(C.c_int), i, C.c_uint64, i, i, f, f, f, f, f, vp, vp]
+        L.srn_image_ssim.argtypes = [vp, vp, i, i, vp, vp]
         for name in EXPORTED[2:]:
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -266,6 +267,12 @@ def srn_load(ctx, path):
     st = C.c_int()
     _check(lib().srn_load(ctx, str(path).encode(), C.byref(st)))
     return st.value
+
+
+def srn_image_ssim(a, b, out, stream=None):
+    """a, b: [H, W, 4] float32 CUDA images; out: float64 CUDA tensor [1]."""
+    H, W = a.shape[-3], a.shape[-2]
+    _check(lib().srn_image_ssim(_ptr(a), _ptr(b), int(W), int(H), _ptr(out), _stream(stream)))
 
 
 def srn_density_mse(a, b, out, stream=None):

@@ -210,6 +210,41 @@ def test_image_mse(srn):
     assert abs(out.item() - ref) <= 1e-9
 
 
+@pytest.mark.parametrize("h,w", [(23, 37), (11, 11), (10, 40), (64, 75), (1, 1)])
+def test_image_ssim(srn, h, w):
+    """SSIM against the FP64 oracle on ragged tiles, a single window, no
+    window (1 by convention); identical images give exactly 1; two calls agree
+    bit for bit."""
+    import torch
+    S = srn
+    g = torch.Generator(device="cuda").manual_seed(h * 1000 + w)
+    a = torch.rand((h, w, 4), device="cuda", generator=g)
+    b = (a + 0.2 * torch.rand((h, w, 4), device="cuda", generator=g)).clamp(0, 1)
+    b[: h // 2] = a[: h // 2]  # half the image identical: SSIM near 1 there
+    out = torch.full((3,), -1.0, dtype=torch.float64, device="cuda")
+    S.srn_image_ssim(a, b, out[0:1])
+    S.srn_image_ssim(a, b, out[1:2])
+    S.srn_image_ssim(a, a, out[2:3])
+    torch.cuda.synchronize()
+    ref = oracle.ssim(a.cpu().numpy(), b.cpu().numpy())
+    assert abs(out[0].item() - ref) <= 1e-12, (out[0].item(), ref)
+    assert out[0].item() == out[1].item() and out[2].item() == 1.0
+
+
+def test_image_ssim_constant_images(srn):
+    """Two constant images: (2 mu_a mu_b + C1) / (mu_a^2 + mu_b^2 + C1)."""
+    import torch
+    S = srn
+    a = torch.full((40, 70, 4), 0.3, device="cuda")
+    b = torch.full((40, 70, 4), 0.6, device="cuda")
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    S.srn_image_ssim(a, b, out)
+    torch.cuda.synchronize()
+    C1 = 0.01 ** 2
+    ma, mb = float(np.float32(0.3)), float(np.float32(0.6))
+    assert abs(out.item() - (2 * ma * mb + C1) / (ma * ma + mb * mb + C1)) <= 1e-12
+
+
 @pytest.mark.parametrize("n", [0, 1, 1000, 1025, 4194307])
 def test_mse_reductions(srn, n):
     """Density and image MSE against FP64 numpy: empty input, fewer values
