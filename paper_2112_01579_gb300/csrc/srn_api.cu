@@ -405,8 +405,9 @@ bool same_graph_args(const FitArgs& x, const FitArgs& y) {
          x.weights == y.weights && x.biases == y.biases && x.cdf == y.cdf && x.cdf_res == y.cdf_res;
 }
 
-// Captures one step (fit step, grid refresh, step counter += 1) on the
-// context's own stream into ctx->graph_exec.
+// Captures one step (fit step, whose Adam kernel advances the step index,
+// and the 8-bit grid refresh) on the context's own stream into
+// ctx->graph_exec.
 cudaError_t capture_fit_graph(srn_ctx* ctx, const FitArgs& a) {
   if (ctx->graph_exec) {
     cudaGraphExecDestroy(ctx->graph_exec);
@@ -418,8 +419,7 @@ cudaError_t capture_fit_graph(srn_ctx* ctx, const FitArgs& a) {
   // relaxed: the launchers set kernel attributes (shared-memory size) while capturing
   e = cudaStreamBeginCapture(ctx->graph_stream, cudaStreamCaptureModeRelaxed);
   if (e != cudaSuccess) return e;
-  cudaError_t le = enqueue_fit_step(ctx, a, ctx->graph_stream);
-  if (le == cudaSuccess) le = launch_step_counter(const_cast<int*>(a.step_ptr), 0, 1, ctx->graph_stream);
+  const cudaError_t le = enqueue_fit_step(ctx, a, ctx->graph_stream);
   cudaGraph_t g = nullptr;
   e = cudaStreamEndCapture(ctx->graph_stream, &g);  // always ends the capture
   if (le != cudaSuccess) e = le;
@@ -466,7 +466,7 @@ srn_status srn_fit_steps(srn_ctx* ctx, const float* volume_dev, const int dims[3
   // capturing records the launches without running them: nothing executes
   // before the replays below, which are ordered on `stream`
   if (!ctx->graph_exec || !same_graph_args(a, ctx->graph_key)) e = capture_fit_graph(ctx, a);
-  if (e == cudaSuccess) e = launch_step_counter(step_dev, first_step, 0, s);
+  if (e == cudaSuccess) e = launch_step_counter(step_dev, first_step, s);
   for (int i = 0; i < n_steps && e == cudaSuccess; ++i) e = cudaGraphLaunch(ctx->graph_exec, s);
   return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_fit_steps");
 }

@@ -383,8 +383,14 @@ __global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(const unsign
                                                                     unsigned int* __restrict__ kout,
                                                                     unsigned int* __restrict__ vout, int n, int shift,
                                                                     const unsigned int* __restrict__ scanned,
-                                                                    int nblocks) {
+                                                                    int nblocks, unsigned int* __restrict__ cell_start,
+                                                                    int n_cells) {
   __shared__ unsigned int cnt[8][NB];
+  // one-pass sort (the digit is the whole cell index): the start of cell c in
+  // the sorted order is the exclusive prefix of digit c, block 0's entry
+  if (cell_start && blockIdx.x == 0)
+    for (int c = threadIdx.x; c <= n_cells; c += kSortThreads)
+      cell_start[c] = c < NB ? scanned[(size_t)c * nblocks] : (unsigned int)n;
   for (int i = threadIdx.x; i < 8 * NB; i += kSortThreads) (&cnt[0][0])[i] = 0;
   __syncthreads();
   warp_digit_counts<NB>(kin, n, shift, cnt);
@@ -433,12 +439,29 @@ __global__ void cell_start_kernel(const unsigned int* __restrict__ skeys, int n,
 // One warp per grid vertex: gather w_corner(p_j) * dz_j over the points of the
 // vertex's adjacent cells (fixed cell order, sorted point order, lane-strided)
 // and reduce across lanes with a fixed butterfly.
+struct GradArgs {
+  const float* pts;
+  const float* dz;
+  const unsigned int* sidx;
+  const unsigned int* start;
+  const float* cell_part;
+  int R;
+  float w0, w1;
+  float* g0;
+  float* g1;
+};
+
 template <int F>
-__global__ void grid_grad_kernel(const float* __restrict__ pts, const float* __restrict__ dz,
-                                 const unsigned int* __restrict__ sidx, const unsigned int* __restrict__ start, int R,
-                                 float w0, float w1, float* __restrict__ g0, float* __restrict__ g1,
-                                 unsigned int* __restrict__ flag) {
-  const long long v = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__device__ __forceinline__ void grid_grad_block(const GradArgs& a, int block, unsigned int* __restrict__ flag) {
+  const float* __restrict__ pts = a.pts;
+  const float* __restrict__ dz = a.dz;
+  const unsigned int* __restrict__ sidx = a.sidx;
+  const unsigned int* __restrict__ start = a.start;
+  const int R = a.R;
+  const float w0 = a.w0, w1 = a.w1;
+  float* __restrict__ g0 = a.g0;
+  float* __restrict__ g1 = a.g1;
+  const long long v = ((long long)block * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (v >= (long long)R * R * R) return;
   const int vx = (int)(v % R), vy = (int)((v / R) % R), vz = (int)(v / ((long long)R * R));
@@ -488,7 +511,7 @@ __global__ void grid_grad_kernel(const float* __restrict__ pts, const float* __r
 
 // Dense cells (many points per cell): one block of 8 warps per cell, warp c
 // sums w_corner_c(p) * dz over the cell's points (sorted order, lane-strided,
-// fixed butterfly) into part[cell][c][F]; vertex_gather_kernel then adds the
+// fixed butterfly) into part[cell][c][F]; vertex_gather_block then adds the
 // <= 8 partials of each vertex in a fixed order.  The block stages the cell's
 // points (position, dz) in shared memory 256 at a time, so each point is
 // gathered from global memory once instead of once per corner; lane l still
@@ -553,9 +576,13 @@ __global__ void __launch_bounds__(256) cell_corner_kernel(const float* __restric
 }
 
 template <int F>
-__global__ void vertex_gather_kernel(const float* __restrict__ part, int R, float w0, float w1,
-                                     float* __restrict__ g0, float* __restrict__ g1, unsigned int* __restrict__ flag) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void vertex_gather_block(const GradArgs& a, int block, unsigned int* __restrict__ flag) {
+  const float* __restrict__ part = a.cell_part;
+  const int R = a.R;
+  const float w0 = a.w0, w1 = a.w1;
+  float* __restrict__ g0 = a.g0;
+  float* __restrict__ g1 = a.g1;
+  const long long i = (long long)block * blockDim.x + threadIdx.x;
   if (i >= (long long)R * R * R * F) return;
   const long long v = i / F;
   const int f = (int)(i - v * F);
@@ -576,13 +603,25 @@ __global__ void vertex_gather_kernel(const float* __restrict__ part, int R, floa
 // Fixed-order sum of the CTA partials: weights, biases and the loss.  A
 // block covers 32 entries; its 8 warps each sum a contiguous eighth of the
 // partial rows in row order, then the 8 sums are added in warp order.
-__global__ void __launch_bounds__(256) reduce_parts_kernel(const float* __restrict__ part, int n_cta, int nW, int nb,
-                                                           float* __restrict__ outW, float* __restrict__ outb,
-                                                           float* __restrict__ loss, float inv_n,
-                                                           unsigned int* __restrict__ flag) {
+struct ReduceArgs {
+  const float* part;
+  int n_cta, nW, nb;
+  float* outW;
+  float* outb;
+  float* loss;
+  float inv_n;
+};
+
+__device__ __forceinline__ void reduce_parts_block(const ReduceArgs& a, int block, unsigned int* __restrict__ flag) {
   __shared__ float acc[8][32];
+  const float* __restrict__ part = a.part;
+  const int n_cta = a.n_cta, nW = a.nW, nb = a.nb;
+  float* __restrict__ outW = a.outW;
+  float* __restrict__ outb = a.outb;
+  float* __restrict__ loss = a.loss;
+  const float inv_n = a.inv_n;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int e = blockIdx.x * 32 + lane;
+  const int e = block * 32 + lane;
   const int ne = nW + nb;
   const int r0 = (int)((long long)n_cta * w / 8), r1 = (int)((long long)n_cta * (w + 1) / 8);
   float s = 0.f;
@@ -604,20 +643,25 @@ __global__ void __launch_bounds__(256) reduce_parts_kernel(const float* __restri
   }
 }
 
-// Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias correction at step + 1) over
-// [grid | weights | biases]; refreshes the FP16 copies.  Skipped entirely
-// when the step produced a non-finite loss or gradient.
-__global__ void adam_kernel(float* __restrict__ grid, float* __restrict__ W, float* __restrict__ b,
-                            const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v, size_t ng,
-                            size_t nW, size_t nb, float lr_grid, float lr_net, int step_arg,
-                            const int* __restrict__ step_ptr, const unsigned int* __restrict__ flag,
-                            unsigned int* __restrict__ status, __half* __restrict__ grid_h,
-                            __half* __restrict__ W_h) {
-  const int step = step_ptr ? *step_ptr : step_arg;
-  if (*flag) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(status, (unsigned int)SRN_ERR_NONFINITE);
-    return;
+// The latent-grid gradient gather and the fixed-order reduction of the
+// weight partials are independent: one launch runs both, blocks
+// [0, gather_blocks) gathering, the rest reducing.
+template <int F, bool DENSE>
+__global__ void __launch_bounds__(256) grad_tail_kernel(const GradArgs g, int gather_blocks, const ReduceArgs r,
+                                                        unsigned int* __restrict__ flag) {
+  if ((int)blockIdx.x < gather_blocks) {
+    if (DENSE) vertex_gather_block<F>(g, blockIdx.x, flag);
+    else grid_grad_block<F>(g, blockIdx.x, flag);
+  } else {
+    reduce_parts_block(r, blockIdx.x - gather_blocks, flag);
   }
+}
+
+__device__ __forceinline__ void adam_update(float* __restrict__ grid, float* __restrict__ W, float* __restrict__ b,
+                                            const float* __restrict__ g, float* __restrict__ m,
+                                            float* __restrict__ v, size_t ng, size_t nW, size_t nb, float lr_grid,
+                                            float lr_net, int step, __half* __restrict__ grid_h,
+                                            __half* __restrict__ W_h) {
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   const float t1 = (float)step + 1.0f;  // exact below 2^24; no int overflow at INT_MAX
   const float bc1 = 1.0f - powf(b1, t1), bc2 = 1.0f - powf(b2, t1);
@@ -639,6 +683,36 @@ __global__ void adam_kernel(float* __restrict__ grid, float* __restrict__ W, flo
       if (W_h) W_h[i - ng] = __float2half_rn(t);
     } else {
       b[i - ng - nW] -= lr_net * upd;
+    }
+  }
+}
+
+// Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias correction at step + 1) over
+// [grid | weights | biases]; refreshes the FP16 copies.  Skipped entirely
+// when the step produced a non-finite loss or gradient.  With the step index
+// in device memory (step_ptr), the last block to finish advances it by one
+// for the next step (flag[1] counts finished blocks and is reset by that block).
+__global__ void adam_kernel(float* __restrict__ grid, float* __restrict__ W, float* __restrict__ b,
+                            const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v, size_t ng,
+                            size_t nW, size_t nb, float lr_grid, float lr_net, int step_arg, int* __restrict__ step_ptr,
+                            unsigned int* __restrict__ flag, unsigned int* __restrict__ status,
+                            __half* __restrict__ grid_h, __half* __restrict__ W_h) {
+  const int step = step_ptr ? *step_ptr : step_arg;
+  if (*flag) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(status, (unsigned int)SRN_ERR_NONFINITE);
+  } else {
+    adam_update(grid, W, b, g, m, v, ng, nW, nb, lr_grid, lr_net, step, grid_h, W_h);
+  }
+  if (step_ptr) {
+    __syncthreads();  // every thread of the block has read *step_ptr
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned int done = atomicAdd(flag + 1, 1u);
+      if (done == gridDim.x - 1) {
+        __threadfence();
+        flag[1] = 0u;
+        *step_ptr = (int)((unsigned int)step + 1u);
+      }
     }
   }
 }
@@ -699,7 +773,11 @@ cudaError_t run_backward(FitScratch& s, const NetDev& net, PointArgs pa, float* 
   const int hist_m = (1 << dbits) * nblocks;
   const int nseg = (hist_m + kScanTile - 1) / kScanTile;  // one 8192-value tile per scan block
   unsigned int* seg_sums = s.hist + (size_t)s.radix_bins * (size_t)((s.max_points + kSortItems - 1) / kSortItems);
+  bool starts_done = false;
   for (int shift = 0; shift < bits && n > 0; shift += dbits) {
+    // a single pass leaves the cell starts to the scatter kernel
+    unsigned int* cs = (shift == 0 && dbits >= bits) ? s.cell_start : nullptr;
+    starts_done = cs != nullptr;
     if (dbits == 9) sort_hist_kernel<512><<<nblocks, kSortThreads, 0, st>>>(k_in, n, shift, s.hist, nblocks);
     else sort_hist_kernel<256><<<nblocks, kSortThreads, 0, st>>>(k_in, n, shift, s.hist, nblocks);
     if (nseg > 1) {
@@ -710,19 +788,23 @@ cudaError_t run_backward(FitScratch& s, const NetDev& net, PointArgs pa, float* 
       scan_kernel<<<1, kScanThreads, 0, st>>>(s.hist, hist_m, hist_m, nullptr);
     }
     if (dbits == 9)
-      sort_scatter_kernel<512><<<nblocks, kSortThreads, 0, st>>>(k_in, v_in, k_out, v_out, n, shift, s.hist, nblocks);
+      sort_scatter_kernel<512><<<nblocks, kSortThreads, 0, st>>>(k_in, v_in, k_out, v_out, n, shift, s.hist, nblocks,
+                                                                 cs, (int)s.n_cells);
     else
       sort_scatter_kernel<256><<<nblocks, kSortThreads, 0, st>>>(k_in, v_in, k_out, v_out, n, shift, s.hist,
-                                                                 nblocks);
+                                                                 nblocks, cs, (int)s.n_cells);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     std::swap(k_in, k_out);
     std::swap(v_in, v_out);
   }
-  cell_start_kernel<<<(n + 1 + 255) / 256, 256, 0, st>>>(k_in, n, s.cell_start, (int)s.n_cells);
-  // grid gradient: zero all keyframes, then gather into the bracketing ones
+  if (!starts_done) cell_start_kernel<<<(n + 1 + 255) / 256, 256, 0, st>>>(k_in, n, s.cell_start, (int)s.n_cells);
+  // grid gradient: the gathers below write every vertex of the two bracketing
+  // keyframes; other keyframes (and everything when there are no points) are zeroed
   const size_t gsz = (size_t)net.R * net.R * net.R * net.F;
-  e = cudaMemsetAsync(dgrid, 0, sizeof(float) * gsz * net.nkey, st);
-  if (e != cudaSuccess) return e;
+  if (net.nkey > 2 || n == 0) {
+    e = cudaMemsetAsync(dgrid, 0, sizeof(float) * gsz * net.nkey, st);
+    if (e != cudaSuccess) return e;
+  }
   int k0 = 0;
   float f = 0.f;
   {
@@ -741,46 +823,45 @@ cudaError_t run_backward(FitScratch& s, const NetDev& net, PointArgs pa, float* 
   float* g0 = dgrid + (size_t)k0 * gsz;
   float* g1 = net.nkey > 1 ? g0 + gsz : nullptr;
   const long long n_vert = (long long)net.R * net.R * net.R;
-  const unsigned int gblocks = (unsigned int)((n_vert * 32 + 255) / 256);
-  const bool dense_cells = s.cell_part && (size_t)n >= 32 * s.n_cells;
-  if (n > 0 && dense_cells) {
-    const long long nw = (long long)s.n_cells * 8;
-    const unsigned int cb = (unsigned int)((nw * 32 + 255) / 256);
-    const long long nv = n_vert * net.F;
-    const unsigned int vb = (unsigned int)((nv + 255) / 256);
-    switch (net.F) {
-      case 4:
-        cell_corner_kernel<4><<<cb, 256, 0, st>>>(s.pts, s.dz, v_in, s.cell_start, net.R, (long long)s.n_cells, s.cell_part);
-        vertex_gather_kernel<4><<<vb, 256, 0, st>>>(s.cell_part, net.R, w0, w1, g0, g1, s.flag);
-        break;
-      case 8:
-        cell_corner_kernel<8><<<cb, 256, 0, st>>>(s.pts, s.dz, v_in, s.cell_start, net.R, (long long)s.n_cells, s.cell_part);
-        vertex_gather_kernel<8><<<vb, 256, 0, st>>>(s.cell_part, net.R, w0, w1, g0, g1, s.flag);
-        break;
-      case 16:
-        cell_corner_kernel<16><<<cb, 256, 0, st>>>(s.pts, s.dz, v_in, s.cell_start, net.R, (long long)s.n_cells, s.cell_part);
-        vertex_gather_kernel<16><<<vb, 256, 0, st>>>(s.cell_part, net.R, w0, w1, g0, g1, s.flag);
-        break;
-      default:
-        cell_corner_kernel<32><<<cb, 256, 0, st>>>(s.pts, s.dz, v_in, s.cell_start, net.R, (long long)s.n_cells, s.cell_part);
-        vertex_gather_kernel<32><<<vb, 256, 0, st>>>(s.cell_part, net.R, w0, w1, g0, g1, s.flag);
+  const int ne = nW + nb;
+  const ReduceArgs ra{s.part, n_cta, nW, nb, dW, db, loss, 1.0f / (float)n};
+  const int rblocks = (ne + 1 + 31) / 32;
+  if (n > 0) {
+    const GradArgs ga{s.pts, s.dz, v_in, s.cell_start, s.cell_part, net.R, w0, w1, g0, g1};
+    const bool dense_cells = s.cell_part && (size_t)n >= 32 * s.n_cells;
+    if (dense_cells) {
+      const long long nw = (long long)s.n_cells * 8;
+      const unsigned int cb = (unsigned int)((nw * 32 + 255) / 256);
+      const int vb = (int)((n_vert * net.F + 255) / 256);
+      switch (net.F) {
+        case 4:
+          cell_corner_kernel<4><<<cb, 256, 0, st>>>(s.pts, s.dz, v_in, s.cell_start, net.R, (long long)s.n_cells,
+                                                    s.cell_part);
+          grad_tail_kernel<4, true><<<vb + rblocks, 256, 0, st>>>(ga, vb, ra, s.flag);
+          break;
+        case 8:
+          cell_corner_kernel<8><<<cb, 256, 0, st>>>(s.pts, s.dz, v_in, s.cell_start, net.R, (long long)s.n_cells,
+                                                    s.cell_part);
+          grad_tail_kernel<8, true><<<vb + rblocks, 256, 0, st>>>(ga, vb, ra, s.flag);
+          break;
+        case 16:
+          cell_corner_kernel<16><<<cb, 256, 0, st>>>(s.pts, s.dz, v_in, s.cell_start, net.R, (long long)s.n_cells,
+                                                     s.cell_part);
+          grad_tail_kernel<16, true><<<vb + rblocks, 256, 0, st>>>(ga, vb, ra, s.flag);
+          break;
+        default:
+          cell_corner_kernel<32><<<cb, 256, 0, st>>>(s.pts, s.dz, v_in, s.cell_start, net.R, (long long)s.n_cells,
+                                                     s.cell_part);
+          grad_tail_kernel<32, true><<<vb + rblocks, 256, 0, st>>>(ga, vb, ra, s.flag);
+      }
+    } else {
+      const int gblocks = (int)((n_vert * 32 + 255) / 256);
+      if (net.F == 8) grad_tail_kernel<8, false><<<gblocks + rblocks, 256, 0, st>>>(ga, gblocks, ra, s.flag);
+      else if (net.F == 16) grad_tail_kernel<16, false><<<gblocks + rblocks, 256, 0, st>>>(ga, gblocks, ra, s.flag);
+      else if (net.F == 4) grad_tail_kernel<4, false><<<gblocks + rblocks, 256, 0, st>>>(ga, gblocks, ra, s.flag);
+      else grad_tail_kernel<32, false><<<gblocks + rblocks, 256, 0, st>>>(ga, gblocks, ra, s.flag);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  } else if (n > 0) {
-    if (net.F == 8)
-      grid_grad_kernel<8><<<gblocks, 256, 0, st>>>(s.pts, s.dz, v_in, s.cell_start, net.R, w0, w1, g0, g1, s.flag);
-    else if (net.F == 16)
-      grid_grad_kernel<16><<<gblocks, 256, 0, st>>>(s.pts, s.dz, v_in, s.cell_start, net.R, w0, w1, g0, g1, s.flag);
-    else if (net.F == 4)
-      grid_grad_kernel<4><<<gblocks, 256, 0, st>>>(s.pts, s.dz, v_in, s.cell_start, net.R, w0, w1, g0, g1, s.flag);
-    else
-      grid_grad_kernel<32><<<gblocks, 256, 0, st>>>(s.pts, s.dz, v_in, s.cell_start, net.R, w0, w1, g0, g1, s.flag);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  const int ne = nW + nb;
-  if (n_cta > 0) {
-    reduce_parts_kernel<<<(ne + 1 + 31) / 32, 256, 0, st>>>(s.part, n_cta, nW, nb, dW, db, loss,
-                                                             1.0f / (float)n, s.flag);
   } else {
     e = cudaMemsetAsync(dW, 0, sizeof(float) * nW, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(db, 0, sizeof(float) * nb, st);
@@ -818,6 +899,7 @@ cudaError_t fit_scratch_alloc(FitScratch& s, const NetDev& net, int max_points) 
   alloc((void**)&s.part, sizeof(float) * (size_t)s.max_cta * (s.n_entries + 1));
   alloc((void**)&s.grads, sizeof(float) * (s.n_grid + s.n_entries));
   alloc((void**)&s.flag, sizeof(unsigned int) * 4);
+  if (e == cudaSuccess) e = cudaMemset(s.flag, 0, sizeof(unsigned int) * 4);  // flag[1]: Adam's block counter
   if ((size_t)max_points >= 32 * s.n_cells) alloc((void**)&s.cell_part, sizeof(float) * s.n_cells * 8 * net.F);
   return e;
 }
@@ -873,13 +955,11 @@ cudaError_t launch_fit_step(FitScratch& s, const NetDev& net, const FitArgs& a, 
 }
 
 namespace {
-__global__ void step_counter_kernel(int* step, int value, int delta) {
-  *step = delta ? (int)((unsigned)*step + (unsigned)delta) : value;
-}
+__global__ void step_counter_kernel(int* step, int value) { *step = value; }
 }  // namespace
 
-cudaError_t launch_step_counter(int* step, int value, int delta, cudaStream_t st) {
-  step_counter_kernel<<<1, 1, 0, st>>>(step, value, delta);
+cudaError_t launch_step_counter(int* step, int value, cudaStream_t st) {
+  step_counter_kernel<<<1, 1, 0, st>>>(step, value);
   return cudaGetLastError();
 }
 

@@ -45,7 +45,8 @@ struct FitArgs {
   float* adam_v;
   const unsigned long long* cdf;  // Section 6.2 adaptive distribution over cdf_res^3 voxels (null: uniform)
   int cdf_res;
-  const int* step_ptr;  // when not null, the step index is read from here (CUDA-graph replay), not `step`
+  int* step_ptr;  // when not null, the step index is read from here (CUDA-graph replay), not `step`, and
+                  // the step's last kernel (Adam) advances it by one
 };
 
 bool fit_supported(const NetDev& net);
@@ -56,8 +57,8 @@ void fit_scratch_free(FitScratch& s);
 cudaError_t launch_backward(FitScratch& s, const NetDev& net, const float* pts, int n, float time, const float* dout,
                             float* dgrid, float* dW, float* db, cudaStream_t st);
 cudaError_t launch_fit_step(FitScratch& s, const NetDev& net, const FitArgs& a, cudaStream_t st);
-// *step += delta (delta = 0 with value >= 0: *step = value), one thread.
-cudaError_t launch_step_counter(int* step, int value, int delta, cudaStream_t st);
+// *step = value, one thread (the first step of a graph-replayed run).
+cudaError_t launch_step_counter(int* step, int value, cudaStream_t st);
 
 // Tensor-core point kernel of the fit (srn_fit_mma.cu): arguments, support
 // (width 32, two layers, density output, no time input, 12 Fourier rows / 8
