@@ -90,6 +90,8 @@ def test_calls_reject_null_contexts_and_bad_batches(lib):
     assert L.srn_dvr_dense(fake, dims, cams, 1, C.byref(tf), C.byref(desc), misaligned, None, None) == \
         lib.SRN_ERR_INVALID_ARG
     assert L.srn_image_mse(fake, fake, -1, fake, None) == lib.SRN_ERR_INVALID_ARG
+    assert L.srn_fit_steps(None, fake, dims, 16, 1, 0, 4, 0.0, 1e-2, 5e-3, 0.0, 1.0, fake, None) == \
+        lib.SRN_ERR_INVALID_ARG
     for w, h, pa, out in ((0, 4, fake, fake), (4, -1, fake, fake), (4, 4, None, fake), (4, 4, fake, None),
                           (4, 4, misaligned, fake)):
         assert L.srn_image_ssim(pa, fake, w, h, out, None) == lib.SRN_ERR_INVALID_ARG
