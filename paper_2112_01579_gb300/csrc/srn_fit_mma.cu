@@ -154,6 +154,16 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
     mbar_init(smem_u32(&mbar[wg]), 1);
     misc[4 + wg] = 0;
   }
+  if (tid == 0) {
+    // row k of a NeRF matrix (Eq. 2): 2 pi 2^(k div 3) on axis k mod 3, zero elsewhere
+    int ok = 1;
+    for (int k = 0; k < M && ok; ++k)
+      for (int ax = 0; ax < 3; ++ax) {
+        const float want = (ax == k % 3) ? 6.2831855f * (float)(1 << (k / 3)) : 0.0f;
+        if (net.fourier[3 * k + ax] != want) ok = 0;
+      }
+    misc[2] = ok;
+  }
   if (tid < 32) {
     tmem_alloc(smem_u32((const void*)&misc[0]), kFitTmemCols);
     tmem_relinquish();
@@ -176,6 +186,7 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
   bool failed = false;
 
   const net32::Latent lat = net32::make_latent(net, a.time);
+  const bool nerf = misc[2] != 0;
   const int step = a.step_ptr ? *a.step_ptr : a.step;
   const float inv_n = 1.0f / (float)a.n;
   const int nchunks = (a.n + 127) / 128;
@@ -194,12 +205,38 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
     float v[64];
 #pragma unroll
     for (int c = 0; c < 64; ++c) v[c] = 0.0f;
+    if (nerf) {
+      // NeRF rows: one MUFU sin/cos per axis from the argument reduced
+      // exactly (x - round(x) in FP32; 2 pi x = w (x - r) + (w - 2 pi) r modulo
+      // 2 pi with w the FP32 value of 2 pi), then angle doubling per octave:
+      // sin 2t = 2 s c, cos 2t = (c - s)(c + s).  With at most five octaves
+      // the doubled error stays below ~2^-17, inside the fit's FP16 hi + lo
+      // operand budget.
+      static_assert(M <= 15, "at most five octaves without re-seeding");
+      float sa[3], ca[3];
 #pragma unroll
-    for (int k = 0; k < M; ++k) {
-      float s, c;
-      net32::fourier_sincos(fm + 3 * k, p, s, c);
-      v[2 * k] = s;
-      v[2 * k + 1] = c;
+      for (int k = 0; k < M; ++k) {
+        const int ax = k % 3;
+        if (k < 3) {
+          const float pa = ax == 0 ? p.x : (ax == 1 ? p.y : p.z);
+          const float r = rintf(pa);
+          __sincosf(fmaf(6.28318548202514648f, pa - r, 1.74845560252379070e-7f * r), &sa[ax], &ca[ax]);
+        } else {
+          const float ss = sa[ax], cc = ca[ax];
+          sa[ax] = 2.0f * ss * cc;
+          ca[ax] = (cc - ss) * (cc + ss);
+        }
+        v[2 * k] = sa[ax];
+        v[2 * k + 1] = ca[ax];
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        float s, c;
+        net32::fourier_sincos(fm + 3 * k, p, s, c);
+        v[2 * k] = s;
+        v[2 * k + 1] = c;
+      }
     }
     v[2 * M] = p.x;
     v[2 * M + 1] = p.y;

@@ -179,20 +179,24 @@ def test_fit_step_matches_oracle(srn, shape):
     _check_params(net, on, grads, 1e-2, 5e-3, TOL_GRAD_MMA if _mma_fit(p) else TOL_GRAD)
 
 
-@pytest.mark.parametrize("shape", ["f8_sine", "f16_snake"])
+@pytest.mark.parametrize("shape", ["f8_sine", "f16_snake", "f8_gaussian_fourier"])
 def test_tensor_core_fit_gradients(srn, shape):
     """The tensor-core fit step's gradient, read back as Adam's first moment
     after one step with zero learning rates (m = (1 - beta1) g), against the
     oracle's loss gradient: 20,011 points (ragged tiles over all warpgroups),
     both instantiated input shapes, within TOL_GRAD_MMA of each block's
-    maximum; the loss within 1e-6."""
+    maximum; the loss within 1e-6.  NeRF Fourier rows take the angle-doubling
+    features; a Gaussian Fourier matrix the compensated sin/cos of each row."""
     import torch
     S = srn
     vol = synth.blobs_volume(48, 6, seed=42).numpy()
     if shape == "f8_sine":
         p = synth.random_params(R=8, F=8, m=12, layers=2, width=32, act=synth.ACT_SINE, seed=43, grid_std=0.3)
-    else:
+    elif shape == "f16_snake":
         p = synth.random_params(R=10, F=16, m=14, layers=2, width=32, act=synth.ACT_SNAKEALT, seed=44, grid_std=0.3)
+    else:
+        p = synth.random_params(R=8, F=8, m=12, layers=2, width=32, act=synth.ACT_SINE, seed=45, grid_std=0.3)
+        p["fourier"] = (np.random.default_rng(46).normal(0.0, 6.0, (12, 3))).astype(np.float32)
     assert _mma_fit(p)
     vol = _spread(vol)
     n = 20011
