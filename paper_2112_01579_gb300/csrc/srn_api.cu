@@ -783,6 +783,7 @@ size_t carve_static(FitScratch& s, const NetDev& net, int n, unsigned char* base
   s.radix_bins = 256;  // two 8-bit passes: the smaller histogram keeps the static area's batch
   const size_t hist_n = 256 * ((nn + 2047) / 2048);
   s.hist = (unsigned int*)take(sizeof(unsigned int) * (hist_n + hist_n / 8192 + 1));
+  s.digit_totals = (unsigned int*)take(sizeof(unsigned int) * 256);
   s.cell_start = (unsigned int*)take(sizeof(unsigned int) * (s.n_cells + 1));
   s.part = (float*)take(sizeof(float) * (size_t)s.max_cta * (s.n_entries + 1));
   s.flag = (unsigned int*)take(sizeof(unsigned int) * 4);

@@ -377,6 +377,45 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(unsigned int* __rest
   }
 }
 
+// Exclusive scan of one digit's counts over the sort blocks (one block per
+// digit, up to kDigitThreads * kDigitPer sort blocks), in place; the digit's
+// total to totals[digit].  The scatter kernel adds the exclusive scan of the
+// totals itself, so one launch replaces the segmented scan of the whole
+// histogram.  Integer sums in a fixed order.
+constexpr int kDigitThreads = 256, kDigitPer = 4;
+
+__global__ void __launch_bounds__(kDigitThreads) digit_scan_kernel(unsigned int* __restrict__ hist, int nblocks,
+                                                                  unsigned int* __restrict__ totals) {
+  __shared__ unsigned int part[kDigitThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned int* row = hist + (size_t)blockIdx.x * nblocks;
+  unsigned int v[kDigitPer], s = 0;
+#pragma unroll
+  for (int k = 0; k < kDigitPer; ++k) {
+    const int i = tid * kDigitPer + k;
+    v[k] = i < nblocks ? row[i] : 0u;
+    s += v[k];
+  }
+  unsigned int x = s;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned int y = __shfl_up_sync(0xffffffffu, x, off);
+    if (lane >= off) x += y;
+  }
+  if (lane == 31) part[warp] = x;
+  __syncthreads();
+  unsigned int before = 0;
+  for (int w = 0; w < warp; ++w) before += part[w];
+  unsigned int run = before + x - s;
+#pragma unroll
+  for (int k = 0; k < kDigitPer; ++k) {
+    const int i = tid * kDigitPer + k;
+    if (i < nblocks) row[i] = run;
+    run += v[k];
+  }
+  if (tid == kDigitThreads - 1) totals[blockIdx.x] = before + x;
+}
+
 template <int NB>
 __global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(const unsigned int* __restrict__ kin,
                                                                     const unsigned int* __restrict__ vin,
@@ -384,19 +423,50 @@ __global__ void __launch_bounds__(kSortThreads) sort_scatter_kernel(const unsign
                                                                     unsigned int* __restrict__ vout, int n, int shift,
                                                                     const unsigned int* __restrict__ scanned,
                                                                     int nblocks, unsigned int* __restrict__ cell_start,
-                                                                    int n_cells) {
+                                                                    int n_cells,
+                                                                    const unsigned int* __restrict__ totals) {
   __shared__ unsigned int cnt[8][NB];
+  __shared__ unsigned int dbase[NB];  // keys of all smaller digits (0 when `scanned` is already global)
+  __shared__ unsigned int wpart[kSortThreads / 32];
+  if (totals) {
+    // exclusive scan of the digit totals, NB / kSortThreads consecutive digits per thread
+    constexpr int PER = NB / kSortThreads;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned int v[PER], t = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      v[k] = totals[threadIdx.x * PER + k];
+      t += v[k];
+    }
+    unsigned int x = t;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xffffffffu, x, off);
+      if (lane >= off) x += y;
+    }
+    if (lane == 31) wpart[warp] = x;
+    __syncthreads();
+    unsigned int run = x - t;
+    for (int w = 0; w < warp; ++w) run += wpart[w];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      dbase[threadIdx.x * PER + k] = run;
+      run += v[k];
+    }
+  } else {
+    for (int d = threadIdx.x; d < NB; d += kSortThreads) dbase[d] = 0u;
+  }
+  for (int i = threadIdx.x; i < 8 * NB; i += kSortThreads) (&cnt[0][0])[i] = 0;
+  __syncthreads();
   // one-pass sort (the digit is the whole cell index): the start of cell c in
   // the sorted order is the exclusive prefix of digit c, block 0's entry
   if (cell_start && blockIdx.x == 0)
     for (int c = threadIdx.x; c <= n_cells; c += kSortThreads)
-      cell_start[c] = c < NB ? scanned[(size_t)c * nblocks] : (unsigned int)n;
-  for (int i = threadIdx.x; i < 8 * NB; i += kSortThreads) (&cnt[0][0])[i] = 0;
-  __syncthreads();
+      cell_start[c] = c < NB ? dbase[c] + scanned[(size_t)c * nblocks] : (unsigned int)n;
   warp_digit_counts<NB>(kin, n, shift, cnt);
   __syncthreads();
   for (int d = threadIdx.x; d < NB; d += kSortThreads) {
-    unsigned int base = scanned[(size_t)d * nblocks + blockIdx.x];
+    unsigned int base = dbase[d] + scanned[(size_t)d * nblocks + blockIdx.x];
 #pragma unroll
     for (int w = 0; w < 8; ++w) {
       const unsigned int c = cnt[w][d];
@@ -780,7 +850,12 @@ cudaError_t run_backward(FitScratch& s, const NetDev& net, PointArgs pa, float* 
     starts_done = cs != nullptr;
     if (dbits == 9) sort_hist_kernel<512><<<nblocks, kSortThreads, 0, st>>>(k_in, n, shift, s.hist, nblocks);
     else sort_hist_kernel<256><<<nblocks, kSortThreads, 0, st>>>(k_in, n, shift, s.hist, nblocks);
-    if (nseg > 1) {
+    const unsigned int* totals = nullptr;
+    if (nblocks <= kDigitThreads * kDigitPer) {
+      // one block per digit; the scatter kernel adds the digits' prefix
+      digit_scan_kernel<<<1 << dbits, kDigitThreads, 0, st>>>(s.hist, nblocks, s.digit_totals);
+      totals = s.digit_totals;
+    } else if (nseg > 1) {
       seg_sum_kernel<<<nseg, kScanThreads, 0, st>>>(s.hist, hist_m, kScanTile, seg_sums);
       scan_kernel<<<1, kScanThreads, 0, st>>>(seg_sums, nseg, nseg, nullptr);
       scan_kernel<<<nseg, kScanThreads, 0, st>>>(s.hist, hist_m, kScanTile, seg_sums);
@@ -789,10 +864,10 @@ cudaError_t run_backward(FitScratch& s, const NetDev& net, PointArgs pa, float* 
     }
     if (dbits == 9)
       sort_scatter_kernel<512><<<nblocks, kSortThreads, 0, st>>>(k_in, v_in, k_out, v_out, n, shift, s.hist, nblocks,
-                                                                 cs, (int)s.n_cells);
+                                                                 cs, (int)s.n_cells, totals);
     else
       sort_scatter_kernel<256><<<nblocks, kSortThreads, 0, st>>>(k_in, v_in, k_out, v_out, n, shift, s.hist,
-                                                                 nblocks, cs, (int)s.n_cells);
+                                                                 nblocks, cs, (int)s.n_cells, totals);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     std::swap(k_in, k_out);
     std::swap(v_in, v_out);
@@ -895,6 +970,7 @@ cudaError_t fit_scratch_alloc(FitScratch& s, const NetDev& net, int max_points) 
   s.radix_bins = sort_bins(s.n_cells);
   // radix histograms, then the per-segment sums of their scan
   alloc((void**)&s.hist, sizeof(unsigned int) * (s.radix_bins * nsb + (s.radix_bins * nsb) / 8192 + 1));
+  alloc((void**)&s.digit_totals, sizeof(unsigned int) * s.radix_bins);
   alloc((void**)&s.cell_start, sizeof(unsigned int) * (s.n_cells + 1));
   alloc((void**)&s.part, sizeof(float) * (size_t)s.max_cta * (s.n_entries + 1));
   alloc((void**)&s.grads, sizeof(float) * (s.n_grid + s.n_entries));
@@ -905,7 +981,8 @@ cudaError_t fit_scratch_alloc(FitScratch& s, const NetDev& net, int max_points) 
 }
 
 void fit_scratch_free(FitScratch& s) {
-  void* ps[] = {s.pts, s.dz, s.key, s.key_alt, s.idx, s.idx_alt, s.hist, s.cell_start, s.part, s.grads, s.flag,
+  void* ps[] = {s.pts, s.dz, s.key, s.key_alt, s.idx, s.idx_alt, s.hist, s.digit_totals, s.cell_start, s.part,
+                s.grads, s.flag,
                 s.cell_part};
   for (void* p : ps)
     if (p) cudaFree(p);

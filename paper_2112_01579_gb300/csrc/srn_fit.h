@@ -20,6 +20,7 @@ struct FitScratch {
   unsigned int* idx;       // [n] point index, sorted by cell
   unsigned int* idx_alt;
   unsigned int* hist;      // radix histograms [256][sort blocks]
+  unsigned int* digit_totals;  // [radix_bins] keys per digit in one sort pass
   unsigned int* cell_start;  // [n_cells + 1]
   float* part;             // [max_cta][n_entries + 1] per-CTA weight-gradient / loss partials
   float* grads;            // [n_grid + n_entries] gradient of one step (grid | weights | biases)
