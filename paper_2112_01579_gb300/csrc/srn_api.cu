@@ -466,7 +466,7 @@ srn_status srn_fit_steps(srn_ctx* ctx, const float* volume_dev, const int dims[3
   // capturing records the launches without running them: nothing executes
   // before the replays below, which are ordered on `stream`
   if (!ctx->graph_exec || !same_graph_args(a, ctx->graph_key)) e = capture_fit_graph(ctx, a);
-  if (e == cudaSuccess) e = launch_step_counter(step_dev, first_step, s);
+  if (e == cudaSuccess) e = launch_step_counter(step_dev, first_step, ctx->fit.flag, s);
   for (int i = 0; i < n_steps && e == cudaSuccess; ++i) e = cudaGraphLaunch(ctx->graph_exec, s);
   return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_fit_steps");
 }

@@ -781,6 +781,7 @@ __global__ void adam_kernel(float* __restrict__ grid, float* __restrict__ W, flo
       if (done == gridDim.x - 1) {
         __threadfence();
         flag[1] = 0u;
+        flag[0] = 0u;  // the next replayed step starts with a clear non-finite flag
         *step_ptr = (int)((unsigned int)step + 1u);
       }
     }
@@ -814,7 +815,9 @@ cudaError_t run_backward(FitScratch& s, const NetDev& net, PointArgs pa, float* 
   int n_cta = std::min(s.max_cta, (n + kFitThreads - 1) / kFitThreads);
   size_t smem = sizeof(float) * ((size_t)L.total + kFitThreads * (net.c + 1) + (size_t)kFitThreads * dstride +
                                  ((pa.n_entries + 3) & ~3) + kFitThreads);
-  cudaError_t e = cudaMemsetAsync(s.flag, 0, sizeof(unsigned int), st);
+  // graph-replayed fit steps (step index in device memory) find the flag
+  // cleared by the previous step's Adam kernel or by the replay set-up
+  cudaError_t e = pa.step_ptr ? cudaSuccess : cudaMemsetAsync(s.flag, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return e;
   if (pa.mode == 0 && n > 0 && mma_status && fit_mma_supported(net) && s.max_cta >= fit_mma_rows_per_cta()) {
     // tensor-core point kernel: one partial row per warpgroup
@@ -1032,11 +1035,14 @@ cudaError_t launch_fit_step(FitScratch& s, const NetDev& net, const FitArgs& a, 
 }
 
 namespace {
-__global__ void step_counter_kernel(int* step, int value) { *step = value; }
+__global__ void step_counter_kernel(int* step, int value, unsigned int* flag) {
+  *step = value;
+  *flag = 0u;
+}
 }  // namespace
 
-cudaError_t launch_step_counter(int* step, int value, cudaStream_t st) {
-  step_counter_kernel<<<1, 1, 0, st>>>(step, value);
+cudaError_t launch_step_counter(int* step, int value, unsigned int* flag, cudaStream_t st) {
+  step_counter_kernel<<<1, 1, 0, st>>>(step, value, flag);
   return cudaGetLastError();
 }
 

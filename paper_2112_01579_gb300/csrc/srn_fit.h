@@ -58,8 +58,9 @@ void fit_scratch_free(FitScratch& s);
 cudaError_t launch_backward(FitScratch& s, const NetDev& net, const float* pts, int n, float time, const float* dout,
                             float* dgrid, float* dW, float* db, cudaStream_t st);
 cudaError_t launch_fit_step(FitScratch& s, const NetDev& net, const FitArgs& a, cudaStream_t st);
-// *step = value, one thread (the first step of a graph-replayed run).
-cudaError_t launch_step_counter(int* step, int value, cudaStream_t st);
+// *step = value and the scratch's non-finite flag cleared, one thread (before
+// the first step of a graph-replayed run).
+cudaError_t launch_step_counter(int* step, int value, unsigned int* flag, cudaStream_t st);
 
 // Tensor-core point kernel of the fit (srn_fit_mma.cu): arguments, support
 // (width 32, two layers, density output, no time input, 12 Fourier rows / 8
