@@ -714,10 +714,9 @@ def short(name):
     name = re.sub(r"^void ", "", name)
     name = re.sub(r"<.*", "", name) if "srn::" not in name else name
     for k in ["render_mma_kernel", "render_fp32_kernel", "dvr_dense_kernel", "eval_fp32_kernel", "fit_point_kernel",
-              "sort_hist_kernel", "sort_scatter_kernel", "scan_kernel", "cell_start_kernel", "grid_grad_kernel",
-              "reduce_parts_kernel", "adam_kernel", "to_half_kernel", "mse_kernel", "mse1_kernel",
-              "gauss_pass_kernel", "resample_kernel"]:
-        if k in name:
+              "sort_hist_kernel", "sort_scatter_kernel", "scan_kernel", "digit_scan_kernel", "cell_start_kernel",
+              "adam_kernel", "to_half_kernel", "gauss_pass_kernel", "resample_kernel"]:
+        if re.search(r"(?<![A-Za-z0-9_])" + k + r"\b", name):
             return "srn::" + k
     return name[:60]
 
