@@ -199,12 +199,36 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
     const bool valid = j < a.n;
     float3 p = make_float3(0.5f, 0.5f, 0.5f);
     if (valid) p = sample::fit_point(a.cdf, a.cdf_res, a.seed, step, j, a.n);
-    const float y = valid ? vol_sample(a.vol, p) : 0.0f;
+    // ground truth y = V(p) (trilinear): the eight corner loads issue here,
+    // the combination waits until after the forward MMA; the latent corners
+    // are gathered first as well, so both latencies overlap the Fourier features
+    float yc[8], yfx, yfy, yfz;
+    {
+      int ix, iy, iz;
+      cell_coord(p.x, a.vol.nx, ix, yfx);
+      cell_coord(p.y, a.vol.ny, iy, yfy);
+      cell_coord(p.z, a.vol.nz, iz, yfz);
+      const size_t sy = (size_t)a.vol.nx, sz = (size_t)a.vol.nx * a.vol.ny;
+      const float* b = a.vol.vol + iz * sz + iy * sy + ix;
+      yc[0] = __ldg(b); yc[1] = __ldg(b + 1); yc[2] = __ldg(b + sy); yc[3] = __ldg(b + sy + 1);
+      yc[4] = __ldg(b + sz); yc[5] = __ldg(b + sz + 1); yc[6] = __ldg(b + sz + sy); yc[7] = __ldg(b + sz + sy + 1);
+    }
 
     // ---- layer-0 input v0 in the tile's column order, FP16 hi + lo
     float v[64];
 #pragma unroll
     for (int c = 0; c < 64; ++c) v[c] = 0.0f;
+    {
+      const net32::Cell cell = net32::make_cell(lat, p);
+#pragma unroll
+      for (int f = 0; f < F; f += 4) {
+        const float4 z = net32::latent4(lat, cell, f);
+        v[2 * M + 3 + f] = z.x;
+        v[2 * M + 4 + f] = z.y;
+        v[2 * M + 5 + f] = z.z;
+        v[2 * M + 6 + f] = z.w;
+      }
+    }
     if (nerf) {
       // NeRF rows: one MUFU sin/cos per axis from the argument reduced
       // exactly (x - round(x) in FP32; 2 pi x = w (x - r) + (w - 2 pi) r modulo
@@ -241,17 +265,6 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
     v[2 * M] = p.x;
     v[2 * M + 1] = p.y;
     v[2 * M + 2] = p.z;
-    {
-      const net32::Cell cell = net32::make_cell(lat, p);
-#pragma unroll
-      for (int f = 0; f < F; f += 4) {
-        const float4 z = net32::latent4(lat, cell, f);
-        v[2 * M + 3 + f] = z.x;
-        v[2 * M + 4 + f] = z.y;
-        v[2 * M + 5 + f] = z.z;
-        v[2 * M + 6 + f] = z.w;
-      }
-    }
     v[D0] = 1.0f;
     v[D0 + 1] = 1.0f;
 #pragma unroll
@@ -299,6 +312,12 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
       dact[o] = SNAKE ? fmaf(2.0f * s, c, 0.5f) : c;
       x[o] = av;  // x now holds the activation
       out = fmaf(wl[o], av, out);
+    }
+    float y = 0.0f;
+    if (valid) {
+      const float gx = 1.0f - yfx, gy = 1.0f - yfy, gz = 1.0f - yfz;
+      y = gx * gy * gz * yc[0] + yfx * gy * gz * yc[1] + gx * yfy * gz * yc[2] + yfx * yfy * gz * yc[3] +
+          gx * gy * yfz * yc[4] + yfx * gy * yfz * yc[5] + gx * yfy * yfz * yc[6] + yfx * yfy * yfz * yc[7];
     }
     const float r = out - y;
     const float dout = valid ? (r > 0.f ? inv_n : (r < 0.f ? -inv_n : 0.f)) : 0.0f;
