@@ -7,10 +7,11 @@
 // A warpgroup takes 128 points at a time, one per thread (thread = MMA row =
 // TMEM lane), from a fixed, static assignment of point tiles:
 // * forward: the thread writes its layer-0 input row v0 = [sin/cos, p, z, 1, 1]
-//   as FP16 blocks [v hi | v lo | v hi] (v = hi + lo to ~2^-22); one MMA
-//   against [W hi | W hi | W lo] (the FP32 master weights split the same
-//   way) gives x1 = W0 v0 + b0 in TMEM, FP32-accurate (the bias as FP16
-//   hi + lo weights of the two constant columns);
+//   as FP16 blocks [v hi | v lo] (v = hi + lo to ~2^-22); one MMA over the
+//   K blocks [v hi | v lo | v hi] (the third re-reads the first) against
+//   [W hi | W hi | W lo] (the FP32 master weights split the same way) gives
+//   x1 = W0 v0 + b0 in TMEM, FP32-accurate (the bias as FP16 hi + lo weights
+//   of the two constant columns);
 // * the thread reads x1, applies the activation and its derivative (MUFU
 //   sin/cos), evaluates the last layer and the L1 loss in FP32, and forms
 //   delta = dL/dx1 = sign(r)/n * w_last * a'(x1);
@@ -25,8 +26,8 @@
 //   all four hi/lo products in TMEM across the warpgroup's tiles.  The bias
 //   gradient of layer 0 is the row of the constant-1 column.
 // * last-layer gradients and the loss are warp reductions in a fixed order.
-// Each warpgroup writes one partial row [W | b | loss], reduced with the FP32
-// path's rows by the same fixed-order kernel: the step is deterministic.
+// Each warpgroup writes one partial row [W | b | loss], reduced in a fixed
+// order by the same kernel as the FP32 path's rows: the step is deterministic.
 #include "srn_fit.h"
 #include "srn_mma_kernel.cuh"
 #include "srn_net32.cuh"
