@@ -10,13 +10,19 @@
 //      128 points in shared memory and accumulates dW_i = sum_p delta v^T for
 //      the entries it owns (fixed order); one partial row per CTA.  Latent
 //      adjoints dz and the cell of every point go to scratch.
-//   2. stable LSD radix sort of (cell, point) pairs, 8-bit digits: per-block
-//      per-warp digit counts, one exclusive scan, stable scatter.
-//   3. cell offsets, then one warp per grid vertex gathers w_corner(p) * dz
-//      over the points of its (up to 8) cells in sorted order and reduces
-//      across lanes with a fixed butterfly: no floating-point atomics, the
-//      latent-grid gradient is bit-reproducible.
-//   4. fixed-order reduction of the CTA partials (weights, biases, loss).
+//      (Two-layer width-32 density networks take the tensor-core point
+//      kernel of srn_fit_mma.cu instead.)
+//   2. stable LSD radix sort of (cell, point) pairs, one 9-bit pass for up to
+//      512 cells, else 8-bit digits: per-block per-warp digit counts, a scan
+//      per digit over the blocks, stable scatter (which adds the digits'
+//      prefix and, for one pass, writes the cell offsets).
+//   3. latent-grid gradient without floating-point atomics: dense cells (many
+//      points per cell) sum w_corner(p) * dz per (cell, corner) in one block
+//      per cell, then each vertex adds its <= 8 partials; sparse cells use one
+//      warp per vertex over its cells' points in sorted order.  Fixed orders
+//      and butterflies throughout, so the gradient is bit-reproducible.
+//   4. fixed-order reduction of the CTA partials (weights, biases, loss), in
+//      the same launch as the vertex gather.
 //   5. Adam over grid, weights and biases (skipped if anything is not
 //      finite), refreshing the FP16 copies.
 #include <algorithm>
