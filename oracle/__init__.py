@@ -68,6 +68,7 @@ def lib():
             L.orc_sample_point.argtypes = [C.c_uint64, C.c_int, C.c_int, dp]
             L.orc_trilinear.argtypes = [dp, C.c_int, C.c_int, C.c_int, C.c_int, dp, dp]
             L.orc_trilinear_grad.argtypes = [dp, C.c_int, C.c_int, C.c_int, C.c_int, dp, dp]
+            L.orc_volume_fd_grad.argtypes = [dp, C.c_int, C.c_int, C.c_int, dp, dp]
             L.orc_net_check.argtypes = [C.POINTER(Net)]
             L.orc_net_forward.argtypes = [C.POINTER(Net), dp, C.c_int, C.c_double, dp]
             L.orc_net_backward.argtypes = [C.POINTER(Net), dp, C.c_int, C.c_double, dp, dp, dp, dp]
@@ -192,6 +193,17 @@ def trilinear_grad(vol, p):
     out = np.zeros((Cc, 3))
     lib().orc_trilinear_grad(_p(v), nx, ny, nz, Cc, _p(_d(p)), _p(out))
     return out
+
+
+def volume_fd_grad(vol, p):
+    """One-voxel central differences of the trilinear volume [nz, ny, nx] at
+    p [3] in [0,1]^3 (the dense-grid shading gradient and the head's
+    targets)."""
+    v = _d(vol)
+    nz, ny, nx = v.shape
+    g = np.zeros(3)
+    lib().orc_volume_fd_grad(_p(v), nx, ny, nz, _p(_d(p)), _p(g))
+    return g
 
 
 def net_forward(net: OracleNet, pts, t: float = 0.0) -> np.ndarray:

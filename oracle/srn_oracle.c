@@ -475,6 +475,24 @@ static double field_density(const orc_field* fd, const double p[3], orc_trace* t
   return r;
 }
 
+/* Central differences of the trilinear volume with a step of one voxel per
+ * axis (h = 1 / (n_a - 1) along axis a), positions clamped to the domain
+ * (Section 5 "FD"): the gradient of dense-grid shading and of the head's
+ * training targets. */
+void orc_volume_fd_grad(const double* vol, int nx, int ny, int nz, const double p[3], double g[3]) {
+  int dims[3] = {nx, ny, nz};
+  for (int a = 0; a < 3; ++a) {
+    double h = 1.0 / (double)(dims[a] - 1);
+    double pp[3] = {p[0], p[1], p[2]}, pm[3] = {p[0], p[1], p[2]};
+    pp[a] = clamp01(p[a] + h);
+    pm[a] = clamp01(p[a] - h);
+    double vp, vm;
+    orc_trilinear(vol, nx, ny, nz, 1, pp, &vp);
+    orc_trilinear(vol, nx, ny, nz, 1, pm, &vm);
+    g[a] = (vp - vm) / (2.0 * h);
+  }
+}
+
 /* Ray march of one pixel (Section 3 DVR; Section 6: constant step).
  * Reading: segments [t0 + k ds, min(t0 + (k+1) ds, t1)], density sampled at
  * the segment midpoint, alpha = 1 - exp(-kappa * length), premultiplied
@@ -505,10 +523,13 @@ static void march(const orc_field* fd, const orc_tf* tf, const double o[3], cons
         for (int a = 0; a < 3; ++a) grad[a] = tr->v[fd->net->l][1 + a];
       } else {
         rho = field_density(fd, p, tr);
-        if (fd->shading == ORC_SHADE_FD) {
-          /* central differences, step of one voxel (Section 5 "FD") */
+        if (fd->shading == ORC_SHADE_FD && !fd->net) {
+          /* dense volume: central differences, step of one voxel */
+          orc_volume_fd_grad(fd->vol, fd->nx, fd->ny, fd->nz, p, grad);
+        } else if (fd->shading == ORC_SHADE_FD) {
+          /* network: central differences with the given step (Section 5 "FD") */
           for (int a = 0; a < 3; ++a) {
-            double h = fd->net ? fd->fd_h : 1.0 / (double)((a == 0 ? fd->nx : a == 1 ? fd->ny : fd->nz) - 1);
+            double h = fd->fd_h;
             double pp[3] = {p[0], p[1], p[2]}, pm[3] = {p[0], p[1], p[2]};
             pp[a] = clamp01(p[a] + h);
             pm[a] = clamp01(p[a] - h);
@@ -580,22 +601,6 @@ void orc_dvr_dense(const double* vol, int nx, int ny, int nz, const orc_camera* 
 }
 
 /* ------------------------------------------------------------------------ */
-/* Central differences of the trilinear volume with a step of one voxel per
- * axis, positions clamped to the domain (Section 5 "FD"). */
-static void volume_fd_grad(const double* vol, int nx, int ny, int nz, const double p[3], double g[3]) {
-  int dims[3] = {nx, ny, nz};
-  for (int a = 0; a < 3; ++a) {
-    double h = 1.0 / (double)(dims[a] - 1);
-    double pp[3] = {p[0], p[1], p[2]}, pm[3] = {p[0], p[1], p[2]};
-    pp[a] = clamp01(p[a] + h);
-    pm[a] = clamp01(p[a] - h);
-    double vp, vm;
-    orc_trilinear(vol, nx, ny, nz, 1, pp, &vp);
-    orc_trilinear(vol, nx, ny, nz, 1, pm, &vm);
-    g[a] = (vp - vm) / (2.0 * h);
-  }
-}
-
 static double sgn(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
 
 /* ------------------------------------------------------------------------ */
@@ -725,7 +730,7 @@ double orc_fit_loss_grad(const orc_net* n, const double* vol, int nx, int ny, in
     dout[0] = sgn(r) * inv_n;
     if (n->D == 4) {
       double gv[3];
-      volume_fd_grad(vol, nx, ny, nz, p, gv);
+      orc_volume_fd_grad(vol, nx, ny, nz, p, gv);
       for (int a = 0; a < 3; ++a) {
         double ra = tr->v[n->l][1 + a] - gs * gv[a];
         loss += gw * fabs(ra);
