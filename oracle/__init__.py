@@ -73,6 +73,7 @@ def lib():
             L.orc_net_forward.argtypes = [C.POINTER(Net), dp, C.c_int, C.c_double, dp]
             L.orc_net_backward.argtypes = [C.POINTER(Net), dp, C.c_int, C.c_double, dp, dp, dp, dp]
             L.orc_net_input_grad.argtypes = [C.POINTER(Net), dp, C.c_int, C.c_double, dp, dp]
+            L.orc_net_input_vjp.argtypes = [C.POINTER(Net), dp, C.c_int, C.c_double, dp, dp]
             L.orc_tf_eval.argtypes = [C.POINTER(TF), C.c_double, dp]
             L.orc_camera_ray.argtypes = [C.POINTER(Camera), C.c_int, C.c_int, C.c_int, C.c_int, dp, dp]
             L.orc_box_intersect.argtypes = [dp, dp, dp, dp]
@@ -86,6 +87,15 @@ def lib():
             L.orc_fit_loss_grad.restype = C.c_double
             L.orc_fit_loss_grad.argtypes = [C.POINTER(Net), dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64,
                                             C.c_int, C.c_double, C.c_double, C.c_double, dp, dp, dp, u64p, C.c_int]
+            L.orc_error_bounds.argtypes = [C.POINTER(Net), dp, C.c_int, C.c_double, dp, dp, dp]
+            L.orc_render_shade_bound.argtypes = [C.POINTER(Net), C.POINTER(Camera), C.c_int, dp, C.c_int,
+                                                 C.POINTER(TF), C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
+                                                 C.c_double, C.POINTER(C.c_longlong), C.c_longlong, dp, dp, dp]
+            L.orc_dvr_dense_shade_bound.argtypes = [dp, C.c_int, C.c_int, C.c_int, C.POINTER(Camera), C.c_int,
+                                                    C.POINTER(TF), C.c_int, C.c_int, C.c_double, C.c_double,
+                                                    C.POINTER(C.c_longlong), C.c_longlong, dp, dp, dp]
+            L.orc_fit_residuals.argtypes = [C.POINTER(Net), dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64,
+                                            C.c_int, C.c_double, u64p, C.c_int, dp, dp]
             L.orc_adam.argtypes = [dp, dp, dp, dp, C.c_size_t, C.c_double, C.c_int, C.c_double, C.c_double,
                                    C.c_double]
             L.orc_fit_step.restype = C.c_double
@@ -232,6 +242,15 @@ def net_input_grad(net: OracleNet, pts, t: float = 0.0):
     return rho, g
 
 
+def net_input_vjp(net: OracleNet, pts, dout, t: float = 0.0):
+    """grad [n, 3] = sum_d dout[:, d] d out_d / d p."""
+    P = _d(pts).reshape(-1, 3)
+    G = _d(dout).reshape(len(P), net.dims["D"])
+    g = np.zeros((len(P), 3))
+    lib().orc_net_input_vjp(C.byref(net.s), _p(P), len(P), t, _p(G), _p(g))
+    return g
+
+
 class OracleTF:
     def __init__(self, pos, rgba, opacity_scale):
         self.pos = _d(pos).reshape(-1)
@@ -332,6 +351,18 @@ def fit_loss_grad(net: OracleNet, vol, n_points, seed, step, t=0.0, gw=0.0, gs=1
     return loss, net.unpack_W(dW), net.unpack_b(db), dg
 
 
+def fit_residuals(net: OracleNet, vol, n_points, seed, step, t=0.0, cdf=None):
+    """(r [n], points [n, 3]): density residuals rho(p_j) - y_j of a fit
+    step's points, in FP64."""
+    v = _d(vol)
+    nz, ny, nx = v.shape
+    r = np.zeros(n_points)
+    P = np.zeros((n_points, 3))
+    cp, cres = _cdf_args(cdf)
+    lib().orc_fit_residuals(C.byref(net.s), _p(v), nx, ny, nz, n_points, seed, step, t, cp, cres, _p(r), _p(P))
+    return r, P
+
+
 def error_grid(net: OracleNet, vol, res, spv, seed, t=0.0):
     """Section 6.2 error grid E [res, res, res] (z, y, x) in float64."""
     v = _d(vol)
@@ -402,3 +433,84 @@ def ssim(a, b):
     A, B = _d(a), _d(b)
     H, W = A.shape[-3], A.shape[-2]
     return lib().orc_ssim(_p(A.reshape(-1)), _p(B.reshape(-1)), W, H)
+
+
+# ---------------------------------------------------------------- error bounds
+# Precision models of the two kernel paths for the first-order bounds (field
+# order of orc_prec: in_rel, in_abs, act_abs, act_rel, acc, dact_abs, bwd_rel,
+# jac_rel, vol_abs, rho_rel).
+#  FP16 tensor-core path: layer-0 inputs computed in FP32 and rounded to FP16
+#   (half an FP16 ulp, 2^-11, plus the FP32 features' error, 2^-19 absolute);
+#   hidden activations from MUFU sin / cos (absolute error ~2^-21 for
+#   |x| <= pi, taken as 2^-20 (1 + |x|)) carried as FP16 hi + lo (2^-22);
+#   tensor-core FP32 accumulation (2^-23 per term, K terms); derivatives from
+#   MUFU as the activations; adjoint rows as hi + lo (2^-22); Fourier and
+#   latent Jacobians recomputed in FP32 with angle doubling (2^-17).
+#  FP32 CUDA-core path: inputs from compensated FP32 sin / cos and an FP32
+#   trilinear (2^-21 relative, 2^-23 absolute); accurate sinf / sincosf
+#   (2^-22); FMA chains (2^-24 per term); Jacobians 2^-21.
+PREC_FP16 = (2.0 ** -11, 2.0 ** -19, 2.0 ** -19, 2.0 ** -22, 2.0 ** -23, 2.0 ** -19, 2.0 ** -22, 2.0 ** -17, 0.0, 0.0)
+PREC_FP32 = (2.0 ** -21, 2.0 ** -23, 2.0 ** -22, 2.0 ** -22, 2.0 ** -24, 2.0 ** -22, 0.0, 2.0 ** -21, 0.0, 0.0)
+
+
+def error_bounds(net: OracleNet, pts, prec, t: float = 0.0, grad=True):
+    """First-order rounding-error bounds of a kernel path with precision
+    model prec at each point: (B_out [n, D], B_grad [n, 3] or None)."""
+    P = _d(pts).reshape(-1, 3)
+    pr = _d(prec)
+    Bo = np.zeros((len(P), net.dims["D"]))
+    Bg = np.zeros((len(P), 3)) if grad else None
+    lib().orc_error_bounds(C.byref(net.s), _p(P), len(P), t, _p(pr), _p(Bo), _p(Bg) if grad else None)
+    return Bo, Bg
+
+
+def fp16_grad_bound(net: OracleNet, pts, t: float = 0.0):
+    """Per-component bound on the FP16 tensor-core adjoint gradient's error."""
+    return error_bounds(net, pts, PREC_FP16, t)[1]
+
+
+def density_image_bound(net: OracleNet, cams, tf: OracleTF, W, H, step, et, rho_rel, times=None, pixels=None):
+    """(rgba, bound): the oracle render and, per pixel, the first-order bound
+    on the image error that a density error of rho_rel max(|rho|, 1) at
+    every sample causes through the TF and the compositing (unshaded)."""
+    prec = (0.0,) * 9 + (float(rho_rel),)
+    return render_shade_bound(net, cams, tf, W, H, step, et, SHADE_NONE, prec, times=times, pixels=pixels)
+
+
+def render_shade_bound(net: OracleNet, cams, tf: OracleTF, W, H, step, et, shading, prec, fd_h=0.0, times=None,
+                       pixels=None):
+    """(rgba, bound): the oracle render and, per pixel, the bound on the
+    shaded image's error that the gradient error of a kernel path with
+    precision model prec causes (to be added to the unshaded image bound);
+    with prec's rho_rel > 0, plus the propagated density error."""
+    T = 1 if times is None else len(times)
+    tarr = None if times is None else _d(times)
+    pp, npix, keep = _pix(pixels)
+    total = npix if pixels is not None else T * len(cams) * H * W
+    out = np.zeros((total, 4))
+    bound = np.zeros(total)
+    pr = _d(prec)
+    lib().orc_render_shade_bound(C.byref(net.s), _cams(cams), len(cams), _p(tarr) if tarr is not None else None, T,
+                                 C.byref(tf.s), W, H, step, et, shading, fd_h, pp, npix, _p(pr), _p(out), _p(bound))
+    if pixels is None:
+        out = out.reshape(T, len(cams), H, W, 4)
+        bound = bound.reshape(T, len(cams), H, W)
+    return out, bound
+
+
+def dvr_dense_shade_bound(vol, cams, tf: OracleTF, W, H, step, et, vol_abs, pixels=None):
+    """(rgba, bound) of FD-shaded dense DVR whose volume samples are off by
+    at most vol_abs."""
+    v = _d(vol)
+    nz, ny, nx = v.shape
+    pp, npix, keep = _pix(pixels)
+    total = npix if pixels is not None else len(cams) * H * W
+    out = np.zeros((total, 4))
+    bound = np.zeros(total)
+    pr = _d((0, 0, 0, 0, 0, 0, 0, 0, vol_abs, 0))
+    lib().orc_dvr_dense_shade_bound(_p(v), nx, ny, nz, _cams(cams), len(cams), C.byref(tf.s), W, H, step, et, pp,
+                                    npix, _p(pr), _p(out), _p(bound))
+    if pixels is None:
+        out = out.reshape(len(cams), H, W, 4)
+        bound = bound.reshape(len(cams), H, W)
+    return out, bound

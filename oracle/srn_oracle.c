@@ -346,12 +346,13 @@ void orc_net_backward(const orc_net* n, const double* pts, int n_pts, double t, 
   free(tr);
 }
 
-/* Adjoint input gradient (Section 5 "Adjoint"): d out_0 / d p by
- * backpropagation through the layers, the Fourier features (d sin(e) =
- * cos(e) F_k, d cos(e) = -sin(e) F_k) and the trilinear latent grid. */
-static void input_grad_traced(const orc_net* n, const orc_trace* tr, double t, double grad[3]) {
+/* Adjoint input gradient (Section 5 "Adjoint") of sum_d s_d out_d (s = dout;
+ * NULL: s = e_0, i.e. d out_0 / d p) by backpropagation through the layers,
+ * the Fourier features (d sin(e) = cos(e) F_k, d cos(e) = -sin(e) F_k) and
+ * the trilinear latent grid. */
+static void input_vjp_traced(const orc_net* n, const orc_trace* tr, double t, const double* seed, double grad[3]) {
   double dout[ORC_MAXW], dv0[ORC_MAXW];
-  for (int d = 0; d < n->D; ++d) dout[d] = (d == 0) ? 1.0 : 0.0;
+  for (int d = 0; d < n->D; ++d) dout[d] = seed ? seed[d] : ((d == 0) ? 1.0 : 0.0);
   backward(n, tr, t, dout, NULL, NULL, NULL, dv0);
   for (int a = 0; a < 3; ++a) grad[a] = dv0[a];
   for (int k = 0; k < n->m; ++k) {
@@ -373,6 +374,10 @@ static void input_grad_traced(const orc_net* n, const orc_trace* tr, double t, d
   free(jac);
 }
 
+static void input_grad_traced(const orc_net* n, const orc_trace* tr, double t, double grad[3]) {
+  input_vjp_traced(n, tr, t, NULL, grad);
+}
+
 /* Density and its adjoint gradient at n_pts positions: rho n, grad n x 3. */
 void orc_net_input_grad(const orc_net* n, const double* pts, int n_pts, double t, double* rho, double* grad) {
   #pragma omp parallel for schedule(dynamic, 64)
@@ -381,6 +386,18 @@ void orc_net_input_grad(const orc_net* n, const double* pts, int n_pts, double t
     forward(n, pts + 3 * j, t, tr);
     rho[j] = tr->v[n->l][0];
     input_grad_traced(n, tr, t, grad + 3 * (size_t)j);
+    free(tr);
+  }
+}
+
+/* Backward with respect to the positions: grad_j = sum_d dout_j[d]
+ * d out_d / d p_j (n_pts x 3), dout n_pts x D. */
+void orc_net_input_vjp(const orc_net* n, const double* pts, int n_pts, double t, const double* dout, double* grad) {
+  #pragma omp parallel for schedule(dynamic, 64)
+  for (int j = 0; j < n_pts; ++j) {
+    orc_trace* tr = (orc_trace*)malloc(sizeof(orc_trace));
+    forward(n, pts + 3 * j, t, tr);
+    input_vjp_traced(n, tr, t, dout + (size_t)j * n->D, grad + 3 * (size_t)j);
     free(tr);
   }
 }
@@ -493,17 +510,61 @@ void orc_volume_fd_grad(const double* vol, int nx, int ny, int nz, const double 
   }
 }
 
+/* Precision model of a kernel path, for the first-order rounding-error
+ * bounds that set the test tolerances of gradients and shaded images (see
+ * the section "First-order rounding-error bounds" below; not the method). */
+typedef struct {
+  double in_rel, in_abs;   /* layer-0 inputs: |dv| <= in_rel |v| + in_abs */
+  double act_abs, act_rel; /* hidden activations: |da| <= act_abs (1 + |x|) + act_rel |a| */
+  double acc;              /* accumulation: |dx| <= acc K sum |terms| for the K terms of a layer */
+  double dact_abs;         /* activation derivatives: |da'| <= dact_abs (1 + |x|) */
+  double bwd_rel;          /* backward: relative error of each stored adjoint entry */
+  double jac_rel;          /* Jacobian d v0 / d p: relative error of each term */
+  double vol_abs;          /* dense volume samples: |drho| <= vol_abs */
+  double rho_rel;          /* > 0: propagate a density error rho_rel max(|rho|, 1) through the compositing */
+} orc_prec;
+
+/* Largest |slope| of the TF's RGBA channels over densities within e of rho
+ * (the piecewise-linear TF of orc_tf_eval; flat outside the control
+ * points). */
+static void tf_slope_bound(const orc_tf* tf, double rho, double e, double slope[4]) {
+  for (int c = 0; c < 4; ++c) slope[c] = 0.0;
+  const double* P = tf->pos;
+  for (int i = 0; i + 1 < tf->n; ++i) {
+    double lo = P[i], hi = P[i + 1];
+    if (hi <= lo) continue;
+    double a = rho - e < 0.0 ? 0.0 : rho - e, b = rho + e > 1.0 ? 1.0 : rho + e;
+    if (b < lo || a > hi) continue; /* [rho - e, rho + e] (clamped) misses the segment */
+    for (int c = 0; c < 4; ++c) {
+      double sl = fabs(tf->rgba[4 * (i + 1) + c] - tf->rgba[4 * i + c]) / (hi - lo);
+      if (sl > slope[c]) slope[c] = sl;
+    }
+  }
+}
+
+static double sample_shade_bound(const orc_field* fd, const orc_prec* pr, const orc_trace* tr, const double p[3],
+                                 const double grad[3], const double rgb[3], const double d[3]);
+
 /* Ray march of one pixel (Section 3 DVR; Section 6: constant step).
  * Reading: segments [t0 + k ds, min(t0 + (k+1) ds, t1)], density sampled at
  * the segment midpoint, alpha = 1 - exp(-kappa * length), premultiplied
  * front-to-back compositing over black, terminated after the sample that
  * brings the opacity to et or above.  *margin receives min_k |A_k - et|. */
 static void march(const orc_field* fd, const orc_tf* tf, const double o[3], const double d[3], double ds, double et,
-                  double out[4], double* margin, long long* n_samples, orc_trace* tr) {
+                  double out[4], double* margin, long long* n_samples, orc_trace* tr, const orc_prec* pr,
+                  double* bound) {
+  if (bound) *bound = 0.0;
   double C[3] = {0, 0, 0}, A = 0.0, mg = INFINITY;
   long long ns = 0;
   double t0, t1;
+  /* density-error propagation (tolerance bookkeeping): per sample the
+   * transmittance T, opacity, colour and the changes of opacity and colour
+   * that the sample's density error can cause */
+  int prop = bound && pr && pr->rho_rel > 0.0;
+  double* rec = NULL;
+  long long nrec = 0;
   if (orc_box_intersect(o, d, &t0, &t1)) {
+    if (prop) rec = (double*)malloc(sizeof(double) * 10 * (size_t)(ceil((t1 - t0) / ds) + 2));
     for (long long k = 0;; ++k) {
       double ta = t0 + (double)k * ds;
       if (ta >= t1) break;
@@ -545,6 +606,24 @@ static void march(const orc_field* fd, const orc_tf* tf, const double o[3], cons
       double rgb[3] = {rgba[0], rgba[1], rgba[2]};
       if (fd->shading != ORC_SHADE_NONE) shade(rgba, grad, d, rgb);
       double wgt = (1.0 - A) * alpha;
+      if (prop) {
+        double e = pr->rho_rel * (fabs(rho) > 1.0 ? fabs(rho) : 1.0), sl[4];
+        tf_slope_bound(tf, rho, e, sl);
+        double* r = rec + 10 * nrec++;
+        r[0] = 1.0 - A;                                       /* T */
+        r[1] = alpha;
+        r[2] = rgb[0]; r[3] = rgb[1]; r[4] = rgb[2];
+        r[5] = (1.0 - alpha) * tf->opacity_scale * len * sl[3] * e; /* |d alpha| */
+        r[6] = sl[0] * e; r[7] = sl[1] * e; r[8] = sl[2] * e; /* |d colour| (unshaded TF colour) */
+        r[9] = 0.0;
+      }
+      if (bound && fd->shading != ORC_SHADE_NONE) {
+        /* tolerance bookkeeping only: the composite weight times the bound
+         * on the sample's shaded colour error */
+        double rgb0[3] = {rgba[0], rgba[1], rgba[2]};
+        if (fd->net && fd->shading == ORC_SHADE_FD) forward(fd->net, p, fd->time, tr);
+        *bound += wgt * sample_shade_bound(fd, pr, tr, p, grad, rgb0, d);
+      }
       for (int c = 0; c < 3; ++c) C[c] += wgt * rgb[c];
       A += wgt;
       double dm = fabs(A - et);
@@ -552,6 +631,26 @@ static void march(const orc_field* fd, const orc_tf* tf, const double o[3], cons
       if (A >= et) break;
     }
   }
+  if (prop) {
+    /* C = sum_k T_k alpha_k c_k: dC / d alpha_k = T_k c_k - (sum_{i>k} T_i
+     * alpha_i c_i) / (1 - alpha_k), dC / d c_k = T_k alpha_k; the same with
+     * c = 1 for the opacity channel */
+    double suf[4] = {0, 0, 0, 0}, pb[4] = {0, 0, 0, 0};
+    for (long long k = nrec - 1; k >= 0; --k) {
+      const double* r = rec + 10 * k;
+      double T = r[0], al = r[1];
+      for (int c = 0; c < 4; ++c) {
+        double col = c < 3 ? r[2 + c] : 1.0;
+        double dA = T * col - (1.0 - al > 1e-300 ? suf[c] / (1.0 - al) : 0.0);
+        pb[c] += fabs(dA) * r[5] + (c < 3 ? T * al * r[6 + c] : 0.0);
+        suf[c] += T * al * col;
+      }
+    }
+    double m = pb[0];
+    for (int c = 1; c < 4; ++c) m = fmax(m, pb[c]);
+    *bound += m;
+  }
+  free(rec);
   out[0] = C[0]; out[1] = C[1]; out[2] = C[2]; out[3] = A;
   if (margin) *margin = mg;
   if (n_samples) *n_samples = ns;
@@ -562,7 +661,7 @@ static void march(const orc_field* fd, const orc_tf* tf, const double o[3], cons
 static void render_common(const orc_net* net, const double* vol, int nx, int ny, int nz, const orc_camera* cams,
                           int n_views, const double* times, int n_times, const orc_tf* tf, int W, int H, double ds,
                           double et, int shading, double fd_h, const long long* pix, long long n_pix, double* out,
-                          double* margin, long long* samples) {
+                          double* margin, long long* samples, const orc_prec* pr, double* bound) {
   long long total = pix ? n_pix : (long long)n_times * n_views * H * W;
   long long ns_sum = 0;
   #pragma omp parallel for schedule(dynamic, 16) reduction(+ : ns_sum)
@@ -577,7 +676,7 @@ static void render_common(const orc_net* net, const double* vol, int nx, int ny,
     orc_camera_ray(&cams[v], W, H, px, py, o, d);
     orc_trace* tr = (orc_trace*)malloc(sizeof(orc_trace));
     long long ns = 0;
-    march(&fd, tf, o, d, ds, et, out + 4 * k, margin ? margin + k : NULL, &ns, tr);
+    march(&fd, tf, o, d, ds, et, out + 4 * k, margin ? margin + k : NULL, &ns, tr, pr, bound ? bound + k : NULL);
     free(tr);
     ns_sum += ns;
   }
@@ -589,7 +688,20 @@ void orc_render(const orc_net* net, const orc_camera* cams, int n_views, const d
                 const orc_tf* tf, int W, int H, double ds, double et, int shading, double fd_h, const long long* pix,
                 long long n_pix, double* out, double* margin, long long* samples) {
   render_common(net, NULL, 0, 0, 0, cams, n_views, times, n_times, tf, W, H, ds, et, shading, fd_h, pix, n_pix, out,
-                margin, samples);
+                margin, samples, NULL, NULL);
+}
+
+/* orc_render plus, per pixel, the first-order bound on the image error that
+ * the gradient error of a kernel path with precision model prec (an array of
+ * the orc_prec fields in order) causes through the shading (test
+ * tolerances; see "First-order rounding-error bounds"). */
+void orc_render_shade_bound(const orc_net* net, const orc_camera* cams, int n_views, const double* times, int n_times,
+                            const orc_tf* tf, int W, int H, double ds, double et, int shading, double fd_h,
+                            const long long* pix, long long n_pix, const double* prec, double* out, double* bound) {
+  orc_prec pr;
+  memcpy(&pr, prec, sizeof(pr));
+  render_common(net, NULL, 0, 0, 0, cams, n_views, times, n_times, tf, W, H, ds, et, shading, fd_h, pix, n_pix, out,
+                NULL, NULL, &pr, bound);
 }
 
 /* Dense-grid DVR of the raw volume (the reference renderer of Section 4). */
@@ -597,7 +709,18 @@ void orc_dvr_dense(const double* vol, int nx, int ny, int nz, const orc_camera* 
                    int W, int H, double ds, double et, int shading, const long long* pix, long long n_pix,
                    double* out, double* margin, long long* samples) {
   render_common(NULL, vol, nx, ny, nz, cams, n_views, NULL, 1, tf, W, H, ds, et, shading, 0.0, pix, n_pix, out,
-                margin, samples);
+                margin, samples, NULL, NULL);
+}
+
+/* orc_dvr_dense plus the per-pixel shading error bound (FD shading, volume
+ * samples off by at most prec.vol_abs). */
+void orc_dvr_dense_shade_bound(const double* vol, int nx, int ny, int nz, const orc_camera* cams, int n_views,
+                               const orc_tf* tf, int W, int H, double ds, double et, const long long* pix,
+                               long long n_pix, const double* prec, double* out, double* bound) {
+  orc_prec pr;
+  memcpy(&pr, prec, sizeof(pr));
+  render_common(NULL, vol, nx, ny, nz, cams, n_views, NULL, 1, tf, W, H, ds, et, ORC_SHADE_FD, 0.0, pix, n_pix, out,
+                NULL, NULL, &pr, bound);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -743,6 +866,25 @@ double orc_fit_loss_grad(const orc_net* n, const double* vol, int nx, int ny, in
   return loss * inv_n;
 }
 
+/* The density residuals r_j = rho(p_j) - y_j of a fit step's points (the
+ * quantity whose sign the L1 gradient takes) and the points themselves
+ * (n_points x 3): test infrastructure for deciding which points' signs are
+ * settled beyond rounding. */
+void orc_fit_residuals(const orc_net* n, const double* vol, int nx, int ny, int nz, int n_points, uint64_t seed,
+                       int step, double t, const uint64_t* cdf, int cdf_res, double* r, double* pts) {
+  #pragma omp parallel for schedule(dynamic, 256)
+  for (int j = 0; j < n_points; ++j) {
+    orc_trace* tr = (orc_trace*)malloc(sizeof(orc_trace));
+    double* p = pts + 3 * (size_t)j;
+    fit_point(cdf, cdf_res, seed, step, j, n_points, p);
+    double y;
+    orc_trilinear(vol, nx, ny, nz, 1, p, &y);
+    forward(n, p, t, tr);
+    r[j] = tr->v[n->l][0] - y;
+    free(tr);
+  }
+}
+
 /* Adam (Kingma & Ba 2015) with bias correction at step index step+1.
  * Reading: beta1 0.9, beta2 0.999, eps 1e-8 (paper names Adam, lr 0.01). */
 void orc_adam(double* theta, double* m, double* v, const double* g, size_t n, double lr, int step, double beta1,
@@ -861,4 +1003,313 @@ double orc_ssim(const double* a, const double* b, int W, int H) {
         ++cnt;
       }
   return cnt ? total / (double)cnt : 1.0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* First-order rounding-error bounds (test infrastructure: they set the
+ * tolerances of the gradient and shaded-image tests; the method does not use
+ * them).  A kernel path is described by an orc_prec: how far each layer-0
+ * input, hidden activation, accumulated sum, activation derivative, adjoint
+ * entry and Jacobian term may be off.  Every such rounding site s is off by
+ * at most c_s |d y / d site_s| in its effect on an output y, to first order.
+ * The sites are distinct rounding operations; modelled as independent,
+ * mean-zero and bounded (the probabilistic model of Higham and Mary, "A new
+ * approach to probabilistic rounding error analysis", SIAM J. Sci. Comput.
+ * 41, 2019), Hoeffding's inequality bounds the total by
+ * lambda sqrt(sum_s c_s^2) except with probability 2 exp(-lambda^2 / 2);
+ * lambda = 6 makes that 3e-8 per bounded quantity.  An inner product of K
+ * terms contributes one site of scale acc sqrt(K) sum |terms| (the same
+ * paper's bound for a length-K sum).  Sensitivities of outputs are one
+ * backward pass; those of the adjoint gradient to the forward pass are
+ * central differences of the traced gradient with respect to each
+ * pre-activation, and to the backward pass the linear maps from each
+ * adjoint entry to the gradient. */
+#define ORC_LAMBDA 6.0
+
+/* delta[i][o] = d out_d / d h_i[o] for every layer i of a traced evaluation. */
+static void layer_deltas(const orc_net* n, const orc_trace* tr, int d, double delta[ORC_MAXL][ORC_MAXW]) {
+  size_t woff[ORC_MAXL + 1];
+  woff[0] = 0;
+  for (int i = 0; i < n->l; ++i) woff[i + 1] = woff[i] + (size_t)layer_out(n, i) * layer_in(n, i);
+  for (int o = 0; o < n->D; ++o) delta[n->l - 1][o] = (o == d) ? 1.0 : 0.0;
+  for (int i = n->l - 1; i >= 1; --i) {
+    int din = layer_in(n, i), dout_i = layer_out(n, i);
+    const double* W = n->W + woff[i];
+    for (int j = 0; j < din; ++j) {
+      double g = 0.0;
+      for (int o = 0; o < dout_i; ++o) g += W[(size_t)o * din + j] * delta[i][o];
+      delta[i - 1][j] = g * act_df(n->act, tr->h[i - 1][j]);
+    }
+  }
+}
+
+/* Scales of the forward sites: sv[i][j] for input j of layer i (its
+ * rounding), sr[i][o] for the accumulation of pre-activation h_i[o]. */
+static void forward_sites(const orc_net* n, const orc_trace* tr, const orc_prec* pr, double sv[ORC_MAXL][ORC_MAXW],
+                          double sr[ORC_MAXL][ORC_MAXW]) {
+  const double* W = n->W;
+  const double* b = n->b;
+  for (int i = 0; i < n->l; ++i) {
+    int din = layer_in(n, i), dout_i = layer_out(n, i);
+    int K = i == 0 ? din + 2 : 2 * din + 2;
+    for (int j = 0; j < din; ++j) {
+      double v = tr->v[i][j];
+      sv[i][j] = i == 0 ? pr->in_rel * fabs(v) + pr->in_abs
+                        : pr->act_abs * (1.0 + fabs(tr->h[i - 1][j])) + pr->act_rel * fabs(v);
+    }
+    for (int o = 0; o < dout_i; ++o) {
+      double mag = fabs(b[o]);
+      for (int j = 0; j < din; ++j) mag += fabs(W[(size_t)o * din + j] * tr->v[i][j]);
+      sr[i][o] = pr->acc * sqrt((double)K) * mag;
+    }
+    W += (size_t)dout_i * din;
+    b += dout_i;
+  }
+}
+
+/* Bound on the error of output d of a traced evaluation. */
+static double output_bound(const orc_net* n, const orc_trace* tr, const orc_prec* pr, int d) {
+  static __thread double sv[ORC_MAXL][ORC_MAXW], sr[ORC_MAXL][ORC_MAXW], delta[ORC_MAXL][ORC_MAXW];
+  forward_sites(n, tr, pr, sv, sr);
+  layer_deltas(n, tr, d, delta);
+  double var = 0.0;
+  const double* W = n->W;
+  for (int i = 0; i < n->l; ++i) {
+    int din = layer_in(n, i), dout_i = layer_out(n, i);
+    for (int j = 0; j < din; ++j) {
+      double dj = 0.0; /* d out_d / d v_i[j] */
+      for (int o = 0; o < dout_i; ++o) dj += delta[i][o] * W[(size_t)o * din + j];
+      var += dj * dj * sv[i][j] * sv[i][j];
+    }
+    for (int o = 0; o < dout_i; ++o) var += delta[i][o] * delta[i][o] * sr[i][o] * sr[i][o];
+    W += (size_t)dout_i * din;
+  }
+  return ORC_LAMBDA * sqrt(var);
+}
+
+/* Jacobian d v0 / d p (d0 x 3) at the traced position. */
+static void input_jacobian(const orc_net* n, const orc_trace* tr, double t, double* J) {
+  int d0 = layer_in(n, 0);
+  memset(J, 0, sizeof(double) * 3 * d0);
+  for (int a = 0; a < 3; ++a) J[3 * a + a] = 1.0;
+  for (int k = 0; k < n->m; ++k)
+    for (int a = 0; a < 3; ++a) {
+      J[3 * (3 + k) + a] = cos(tr->e[k]) * n->fourier[3 * k + a];
+      J[3 * (3 + n->m + k) + a] = -sin(tr->e[k]) * n->fourier[3 * k + a];
+    }
+  size_t gsz = (size_t)n->R * n->R * n->R * n->F;
+  int k0;
+  double f;
+  time_weights(n, t, &k0, &f);
+  double jac[3 * ORC_MAXW];
+  for (int kk = 0; kk < (n->nkey > 1 ? 2 : 1); ++kk) {
+    double tw = (n->nkey > 1) ? (kk ? f : 1.0 - f) : 1.0;
+    orc_trilinear_grad(n->grid + (size_t)(k0 + kk) * gsz, n->R, n->R, n->R, n->F, tr->p, jac);
+    for (int ch = 0; ch < n->F; ++ch)
+      for (int a = 0; a < 3; ++a) J[3 * (3 + 2 * n->m + ch) + a] += tw * jac[3 * ch + a];
+  }
+}
+
+/* Layers after layer i of a trace recomputed after h_i changed. */
+static void forward_from(const orc_net* n, orc_trace* tr, int i) {
+  const double* W = n->W;
+  const double* b = n->b;
+  for (int q = 0; q < n->l; ++q) {
+    int din = layer_in(n, q), dout_q = layer_out(n, q);
+    if (q == i) {
+      for (int o = 0; o < dout_q; ++o) tr->v[q + 1][o] = (q < n->l - 1) ? act_f(n->act, tr->h[q][o]) : tr->h[q][o];
+    } else if (q > i) {
+      for (int o = 0; o < dout_q; ++o) {
+        double h = b[o];
+        for (int j = 0; j < din; ++j) h += W[(size_t)o * din + j] * tr->v[q][j];
+        tr->h[q][o] = h;
+        tr->v[q + 1][o] = (q < n->l - 1) ? act_f(n->act, h) : h;
+      }
+    }
+    W += (size_t)dout_q * din;
+    b += dout_q;
+  }
+}
+
+/* g = J^T W0^T delta_0, the adjoint gradient of output 0, of a trace (J
+ * fixed: the kernels evaluate the Jacobian at the sample position). */
+static void traced_gradient(const orc_net* n, const orc_trace* tr, const double* J, double g[3],
+                            double delta[ORC_MAXL][ORC_MAXW], double* dv0) {
+  layer_deltas(n, tr, 0, delta);
+  int d0 = layer_in(n, 0), c0 = layer_out(n, 0);
+  for (int j = 0; j < d0; ++j) {
+    double s = 0.0;
+    for (int o = 0; o < c0; ++o) s += n->W[(size_t)o * d0 + j] * delta[0][o];
+    dv0[j] = s;
+  }
+  for (int a = 0; a < 3; ++a) {
+    g[a] = 0.0;
+    for (int j = 0; j < d0; ++j) g[a] += J[3 * j + a] * dv0[j];
+  }
+}
+
+/* Bound (per component) on the error of the adjoint gradient of output 0. */
+static void gradient_bound(const orc_net* n, const orc_trace* tr0, double t, const orc_prec* pr, double B[3]) {
+  static __thread double sv[ORC_MAXL][ORC_MAXW], sr[ORC_MAXL][ORC_MAXW], delta[ORC_MAXL][ORC_MAXW];
+  static __thread double dl2[ORC_MAXL][ORC_MAXW], S[ORC_MAXL][ORC_MAXW][3];
+  static __thread double J[3 * ORC_MAXW], dv0[ORC_MAXW], dv1[ORC_MAXW], M[3][ORC_MAXW], M2[3][ORC_MAXW];
+  static __thread orc_trace tr;
+  int d0 = layer_in(n, 0), c = n->c, L = n->l;
+  size_t woff[ORC_MAXL + 1];
+  woff[0] = 0;
+  for (int i = 0; i < L; ++i) woff[i + 1] = woff[i] + (size_t)layer_out(n, i) * layer_in(n, i);
+  forward_sites(n, tr0, pr, sv, sr);
+  input_jacobian(n, tr0, t, J);
+  double g0[3], var[3] = {0.0, 0.0, 0.0};
+  traced_gradient(n, tr0, J, g0, delta, dv0);
+  /* forward sites: S[i][o] = d g / d h_i[o] by central differences (the
+   * linear output layer does not enter the gradient) */
+  for (int i = 0; i < L - 1; ++i)
+    for (int o = 0; o < c; ++o) {
+      double eta = 1e-6 * (1.0 + fabs(tr0->h[i][o])), gp[3], gm[3];
+      memcpy(&tr, tr0, sizeof(tr));
+      tr.h[i][o] += eta;
+      forward_from(n, &tr, i);
+      traced_gradient(n, &tr, J, gp, dl2, dv1);
+      memcpy(&tr, tr0, sizeof(tr));
+      tr.h[i][o] -= eta;
+      forward_from(n, &tr, i);
+      traced_gradient(n, &tr, J, gm, dl2, dv1);
+      for (int a = 0; a < 3; ++a) S[i][o][a] = (gp[a] - gm[a]) / (2.0 * eta);
+    }
+  for (int i = 0; i < L - 1; ++i) {
+    const double* W = n->W + woff[i];
+    int din = layer_in(n, i);
+    for (int j = 0; j < din; ++j)
+      for (int a = 0; a < 3; ++a) {
+        double s = 0.0; /* d g_a / d v_i[j] */
+        for (int o = 0; o < c; ++o) s += S[i][o][a] * W[(size_t)o * din + j];
+        var[a] += s * s * sv[i][j] * sv[i][j];
+      }
+    for (int o = 0; o < c; ++o)
+      for (int a = 0; a < 3; ++a) var[a] += S[i][o][a] * S[i][o][a] * sr[i][o] * sr[i][o];
+  }
+  /* backward sites.  M (3 x c) maps a change of delta_i to the gradient:
+   * M_0 = J^T W0^T, M_{i+1} = M_i diag(a'(h_i)) W_{i+1}^T.  Each adjoint
+   * entry delta_i[j] = (W_{i+1}^T delta_{i+1})_j a'(h_i[j]) carries: its
+   * storage (bwd_rel |delta|), the derivative (|(W^T delta)_j| dact
+   * (1 + |h|)) and the accumulation (acc sqrt(2c) sum_o |W_oj delta_o|
+   * |a'|); the final dv0 accumulation and the Jacobian terms enter through J
+   * directly. */
+  for (int a = 0; a < 3; ++a)
+    for (int o = 0; o < c; ++o) {
+      double s = 0.0;
+      for (int j = 0; j < d0; ++j) s += J[3 * j + a] * n->W[(size_t)o * d0 + j];
+      M[a][o] = s;
+    }
+  for (int i = 0; i <= L - 2; ++i) {
+    const double* Wn = n->W + woff[i + 1]; /* layer i+1: rows o' (its outputs), columns j (= h_i entries) */
+    int dn = layer_out(n, i + 1);
+    for (int j = 0; j < c; ++j) {
+      double gsum = 0.0, mag = 0.0;
+      for (int o2 = 0; o2 < dn; ++o2) {
+        double w = Wn[(size_t)o2 * c + j], dd = (i + 1 == L - 1) ? (o2 == 0 ? 1.0 : 0.0) : delta[i + 1][o2];
+        gsum += w * dd;
+        mag += fabs(w * dd);
+      }
+      double ad = act_df(n->act, tr0->h[i][j]);
+      double e_store = pr->bwd_rel * fabs(delta[i][j]);
+      double e_der = fabs(gsum) * pr->dact_abs * (1.0 + fabs(tr0->h[i][j]));
+      double e_acc = (i + 1 == L - 1) ? 0.0 : pr->acc * sqrt((double)(2 * c)) * mag * fabs(ad);
+      for (int a = 0; a < 3; ++a) {
+        double m = M[a][j];
+        var[a] += m * m * (e_store * e_store + e_der * e_der + e_acc * e_acc);
+      }
+    }
+    if (i + 1 <= L - 2) { /* M_{i+1} = M_i diag(a'(h_i)) W_{i+1}^T */
+      for (int a = 0; a < 3; ++a)
+        for (int o2 = 0; o2 < c; ++o2) {
+          double s = 0.0;
+          for (int j = 0; j < c; ++j) s += M[a][j] * act_df(n->act, tr0->h[i][j]) * Wn[(size_t)o2 * c + j];
+          M2[a][o2] = s;
+        }
+      memcpy(M, M2, sizeof(M));
+    }
+  }
+  for (int j = 0; j < d0; ++j) {
+    double mag = 0.0;
+    for (int o = 0; o < c; ++o) mag += fabs(n->W[(size_t)o * d0 + j] * delta[0][o]);
+    double e_acc = pr->acc * sqrt((double)(2 * c)) * mag;
+    for (int a = 0; a < 3; ++a) {
+      double ej = J[3 * j + a] * e_acc, ejac = pr->jac_rel * J[3 * j + a] * dv0[j];
+      var[a] += ej * ej + ejac * ejac;
+    }
+  }
+  for (int a = 0; a < 3; ++a) B[a] = ORC_LAMBDA * sqrt(var[a]);
+}
+
+/* Per point: bounds on the error of every output (n_pts x D) and of the
+ * adjoint gradient of output 0 (n_pts x 3, may be NULL), for a kernel path
+ * with precision model prec (the orc_prec fields in order). */
+void orc_error_bounds(const orc_net* n, const double* pts, int n_pts, double t, const double* prec, double* B_out,
+                      double* B_grad) {
+  orc_prec pr;
+  memcpy(&pr, prec, sizeof(pr));
+  #pragma omp parallel for schedule(dynamic, 16)
+  for (int j = 0; j < n_pts; ++j) {
+    orc_trace* tr = (orc_trace*)malloc(sizeof(orc_trace));
+    forward(n, pts + 3 * j, t, tr);
+    for (int d = 0; d < n->D; ++d) B_out[(size_t)j * n->D + d] = output_bound(n, tr, &pr, d);
+    if (B_grad) gradient_bound(n, tr, t, &pr, B_grad + 3 * (size_t)j);
+    free(tr);
+  }
+}
+
+/* The shaded colour of one sample is rgb (0.1 + 0.6 c) + 0.3 c^32 with
+ * c = |n.d| (the reading of Section 5's Phong shading); a gradient error e
+ * moves the unit normal by at most 2 e / |g|, so c by at most
+ * min(1, 2 e / |g|), and the colour by (0.6 max rgb + 9.6 c^31) times that
+ * (to first order).  A sample whose |g| lies within e of the 1e-6 unshaded
+ * threshold may switch between shaded and unshaded: up to 0.9 max rgb + 0.3.
+ * e per mode: the adjoint's gradient bound; for central differences the
+ * density bounds of the two neighbours over 2h per axis; for the head the
+ * bounds of outputs 1..3. */
+static double sample_shade_bound(const orc_field* fd, const orc_prec* pr, const orc_trace* tr, const double p[3],
+                                 const double grad[3], const double rgb[3], const double d[3]) {
+  double e2 = 0.0;
+  if (fd->net && fd->shading == ORC_SHADE_ADJOINT) {
+    double B[3];
+    gradient_bound(fd->net, tr, fd->time, pr, B);
+    e2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+  } else if (fd->net && fd->shading == ORC_SHADE_HEAD) {
+    for (int a = 0; a < 3; ++a) {
+      double b = output_bound(fd->net, tr, pr, 1 + a);
+      e2 += b * b;
+    }
+  } else if (fd->shading == ORC_SHADE_FD) {
+    orc_trace* tq = (orc_trace*)malloc(sizeof(orc_trace));
+    for (int a = 0; a < 3; ++a) {
+      double h = fd->net ? fd->fd_h : 1.0 / (double)((a == 0 ? fd->nx : a == 1 ? fd->ny : fd->nz) - 1);
+      double s = 0.0;
+      for (int sg = -1; sg <= 1; sg += 2) {
+        double q[3] = {p[0], p[1], p[2]};
+        q[a] = clamp01(p[a] + sg * h);
+        if (fd->net) {
+          forward(fd->net, q, fd->time, tq);
+          s += output_bound(fd->net, tq, pr, 0);
+        } else {
+          s += pr->vol_abs;
+        }
+      }
+      e2 += (s / (2.0 * h)) * (s / (2.0 * h));
+    }
+    free(tq);
+  }
+  double e = sqrt(e2);
+  double gn = sqrt(grad[0] * grad[0] + grad[1] * grad[1] + grad[2] * grad[2]);
+  double mrgb = fmax(rgb[0], fmax(rgb[1], rgb[2]));
+  double bound = 0.0;
+  if (gn - e < 1e-6) bound += 0.9 * mrgb + 0.3; /* may switch between shaded and unshaded */
+  if (gn >= 1e-6) {
+    double c = fabs(grad[0] * d[0] + grad[1] * d[1] + grad[2] * d[2]) / gn;
+    double dc = fmin(1.0, 2.0 * e / gn);
+    double cmax = fmin(1.0, c + dc);
+    bound += (0.6 * mrgb + 9.6 * pow(cmax, 31.0)) * dc;
+  }
+  return bound;
 }

@@ -262,6 +262,28 @@ def test_input_gradient_matches_finite_differences(act):
         np.testing.assert_allclose(g[:, a], fd, rtol=1e-6, atol=1e-6)
 
 
+def test_input_vjp_matches_finite_differences():
+    """Backward with respect to the positions of sum_d dout_d out_d for a
+    four-output network (Section 5 head): brute-force central differences of
+    that sum; the density-only seed equals net_input_grad."""
+    p = synth.random_params(R=5, F=4, m=9, layers=3, width=8, out_dim=4, act=synth.ACT_SNAKEALT, seed=14)
+    net = _net(p)
+    rng = np.random.default_rng(15)
+    pts = rng.uniform(0.05, 0.95, (10, 3))
+    dout = rng.normal(size=(10, 4))
+    g = oracle.net_input_vjp(net, pts, dout)
+    h = 1e-6
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = h
+        fp = (oracle.net_forward(net, pts + e) * dout).sum(axis=1)
+        fm = (oracle.net_forward(net, pts - e) * dout).sum(axis=1)
+        np.testing.assert_allclose(g[:, a], (fp - fm) / (2 * h), rtol=1e-6, atol=1e-6)
+    e0 = np.zeros((10, 4))
+    e0[:, 0] = 1.0
+    np.testing.assert_allclose(oracle.net_input_vjp(net, pts, e0), oracle.net_input_grad(net, pts)[1], atol=0)
+
+
 def test_time_interpolation_is_trilerp_of_lerped_grid():
     """Section 7: the latent vector is interpolated linearly in time between
     keyframes.  By linearity this equals trilinear interpolation of the
