@@ -211,9 +211,23 @@ srn_status srn_dvr_dense(const float* volume_dev, const int dims[3], const srn_c
 srn_status srn_eval(srn_ctx* ctx, const float* pts_dev, int n, float time, float* out_dev, void* stream);
 
 /* Density and its adjoint input gradient (Section 5 "Adjoint"): rho_dev [n],
- * grad_dev [n][3] (d rho / d p; may be NULL).  FP32 arithmetic. */
+ * grad_dev [n][3] (d rho / d p at the position clamped to [0,1]^3; may be
+ * NULL).  Precision follows the context: FP32 CUDA cores, or on FP16 contexts
+ * the tensor-core adjoint of the render (FP16 operands, hidden activations
+ * and adjoint rows as FP16 hi + lo pairs, FP32 accumulate), which takes
+ * width-32 density networks of at most four layers, 12 Fourier rows / 8
+ * latent channels or 14 / 16, no time input, FP16 grid (other shapes on FP16
+ * contexts: SRN_ERR_UNSUPPORTED). */
 srn_status srn_density_grad(srn_ctx* ctx, const float* pts_dev, int n, float time, float* rho_dev,
                             float* grad_dev, void* stream);
+
+/* Backward of srn_eval with respect to the positions (Section 5 "Adjoint",
+ * seeded with dout): dpts_dev float32 [n][3] is OVERWRITTEN with
+ * dpts_j = sum_d dout_j[d] d out_d / d p_j (derivative at the position
+ * clamped to [0,1]^3), dout_dev float32 [n][D].  FP32 CUDA-core arithmetic
+ * for every context precision (as srn_backward); allocates nothing. */
+srn_status srn_input_backward(srn_ctx* ctx, const float* pts_dev, int n, float time, const float* dout_dev,
+                              float* dpts_dev, void* stream);
 
 /*
  * Parameter gradients of sum_j <dout_j, net(p_j)> (backward of srn_eval):
@@ -327,13 +341,13 @@ srn_status srn_lowpass_resample(const float* volume_dev, const int dims[3], int 
  * srn_backward for callers that cannot allocate device memory.  The paper
  * has no counterpart; this exists for integrators, not for the method.
  *
- * Some callers must not call cudaMalloc: code that runs while a stream is
- * being captured into a CUDA graph (allocation is not a capturable
- * operation), hosts whose device memory is owned by another allocator (a
- * framework's caching pool, a preallocated arena) or frame loops that may
- * not take the implicit device synchronization cudaMalloc/cudaFree can
- * cause.  srn_create allocates scratch, so such callers cannot use
- * srn_backward; this entry point needs no context and allocates nothing.
+ * Some callers must not call cudaMalloc: hosts whose device memory is
+ * owned by another allocator (a framework's caching pool, or an arena sized
+ * once at start-up whose budget an outside allocation would break), and
+ * frame loops that may not take the device-wide synchronization that
+ * cudaMalloc / cudaFree can cause.  srn_create allocates scratch, so such
+ * callers cannot use srn_backward; this entry point needs no context and
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library call).
  *
  * It computes exactly what srn_backward computes for the network described
  * by *cfg / *params (same arguments, same outputs, overwritten), using a
@@ -344,8 +358,11 @@ srn_status srn_lowpass_resample(const float* volume_dev, const int dims[3], int 
  *   larger n returns SRN_ERR_INVALID_ARG and srn_last_error() states the
  *   largest n that fits.  cfg->max_fit_points is ignored.
  * - The first call on each device looks up the area's device address
- *   (once per device, with that device current); make that first call
- *   before any stream capture begins.
+ *   (once per device, with that device current) and keeps it for the life
+ *   of the process; make that first call before any stream capture begins.
+ *   The kept address is not valid after cudaDeviceReset on that device, so
+ *   do not use this entry point in a process that resets the device.
+ * - n = 0 is valid and writes zeros to every output.
  * - All calls share the one area, which keeps the previous call's contents
  *   (everything the call relies on is rewritten first).  Calls whose work
  *   overlaps on the GPU (different streams, or different host threads) race

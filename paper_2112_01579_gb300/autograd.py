@@ -2,8 +2,9 @@
 
 ``SRNFunction`` runs the forward pass with ``srn_eval`` and the backward pass
 with the library's hand-written kernels: ``srn_backward`` for the latent grid
-(atomic-free gather over points sorted by cell), weights and biases, and the
-adjoint ``srn_density_grad`` for the input positions.  ``SRNModule`` owns the
+(atomic-free gather over points sorted by cell), weights and biases, and
+``srn_input_backward`` (the adjoint seeded with the incoming gradient) for the
+input positions.  ``SRNModule`` owns the
 parameters as ``nn.Parameter`` tensors so any torch optimizer can train the
 network (``srn_fit_step`` is the fused alternative).  Marshalling only: no
 computation happens in Python.
@@ -45,12 +46,8 @@ class SRNFunction(torch.autograd.Function):
             db = torch.empty_like(net.biases)
             S.srn_backward(net.ctx, pts, dout, dgrid, dW, db, time=ctx.time)
         if ctx.needs_input_grad[0]:
-            if net.out_dim != 1:
-                raise NotImplementedError("input gradients are implemented for density-only networks")
-            rho = torch.empty(pts.shape[0], device=pts.device)
-            g = torch.empty((pts.shape[0], 3), device=pts.device)
-            S.srn_density_grad(net.ctx, pts, rho, g, time=ctx.time)
-            dpts = g * dout[:, :1]
+            dpts = torch.empty((pts.shape[0], 3), device=pts.device)
+            S.srn_input_backward(net.ctx, pts, dout, dpts, time=ctx.time)
         return dpts, dgrid, dW, db, None, None
 
 

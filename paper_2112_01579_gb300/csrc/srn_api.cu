@@ -20,7 +20,9 @@ struct srn_ctx {
   srn_config cfg;
   srn_params prm;
   int device;
-  unsigned int* status;       // device status word (SRN_OK / SRN_ERR_NONFINITE / SRN_ERR_INTERNAL)
+  // device words: [0] status (SRN_OK / SRN_ERR_NONFINITE / ...), [1] graph step
+  // index, [2..3] render work counter, [4] FP16 latent-grid scale exponent
+  unsigned int* status;
   unsigned long long* ray_counter;  // persistent-render work counter (8-byte aligned)
   FitScratch fit;             // scratch of srn_fit_step / srn_backward
   // Section 6.2 adaptive distribution (srn_fit_set_sampling)
@@ -118,8 +120,55 @@ NetDev make_net(const srn_ctx* ctx) {
   n.gq = c.grid_u8;
   n.grid_q = reinterpret_cast<const uint8_t*>(ctx->prm.grid_q);
   n.grid_qp = ctx->prm.grid_qp;
+  n.grid_exp = ctx->status ? reinterpret_cast<const int*>(ctx->status + 4) : nullptr;
   for (int k = 0; k < SRN_MAX_KEYFRAMES; ++k) n.key_times[k] = k < c.n_keyframes ? c.key_times[k] : 0.0f;
   return n;
+}
+
+// FP16 copies of the FP32 masters: the latent grid with its power-of-two
+// scale (exponent into status[4]), the weights as they are, the 8-bit grid.
+cudaError_t write_half_copies(srn_ctx* ctx, cudaStream_t s) {
+  const NetDev n = make_net(ctx);
+  cudaError_t e = launch_grid_to_half_scaled(n.grid, (__half*)ctx->prm.grid_h, net_grid_count(n),
+                                             reinterpret_cast<int*>(ctx->status + 4), s);
+  if (e == cudaSuccess) e = launch_to_half(n.W, (__half*)ctx->prm.weights_h, net_weight_count(n), s);
+  if (e == cudaSuccess && ctx->cfg.grid_u8)
+    e = launch_quantize_grid(n.grid, net_grid_count(n) / n.F, n.F, (uint8_t*)ctx->prm.grid_q, ctx->prm.grid_qp, s);
+  return e;
+}
+
+// Camera frame in FP64 (view set-up, once per camera and call), stored as
+// FP32 pairs hi + lo; see CamDev.
+void split2(double x, float& hi, float& lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
+}
+
+CamDev camera_frame(const srn_camera& c, int W, int H) {
+  double f[3], r[3], u[3];
+  for (int a = 0; a < 3; ++a) f[a] = (double)c.target[a] - (double)c.eye[a];
+  const double nf = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+  for (int a = 0; a < 3; ++a) f[a] /= nf;
+  const double up[3] = {c.up[0], c.up[1], c.up[2]};
+  r[0] = f[1] * up[2] - f[2] * up[1];
+  r[1] = f[2] * up[0] - f[0] * up[2];
+  r[2] = f[0] * up[1] - f[1] * up[0];
+  const double nr = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+  for (int a = 0; a < 3; ++a) r[a] /= nr;
+  u[0] = r[1] * f[2] - r[2] * f[1];
+  u[1] = r[2] * f[0] - r[0] * f[2];
+  u[2] = r[0] * f[1] - r[1] * f[0];
+  const double th = tan(0.5 * (double)c.fovy);
+  CamDev d;
+  for (int a = 0; a < 3; ++a) {
+    d.eye[a] = c.eye[a];
+    split2(f[a], d.f[a], d.fl[a]);
+    split2(r[a], d.r[a], d.rl[a]);
+    split2(u[a], d.u[a], d.ul[a]);
+  }
+  split2(th, d.th[0], d.th[1]);
+  split2(th * ((double)W / (double)H), d.tha[0], d.tha[1]);
+  return d;
 }
 
 srn_status fill_batch(BatchDev& b, const srn_camera* cams, int n_views, const float* times, int n_times,
@@ -151,7 +200,7 @@ srn_status fill_batch(BatchDev& b, const srn_camera* cams, int n_views, const fl
     if (f[0] * f[0] + f[1] * f[1] + f[2] * f[2] == 0.0f || r[0] * r[0] + r[1] * r[1] + r[2] * r[2] == 0.0f ||
         !(c.fovy > 0.0f && c.fovy < 3.14159f))
       return fail(SRN_ERR_INVALID_ARG, "camera %d is degenerate", v);
-    b.cams[v] = c;
+    b.cams[v] = camera_frame(c, desc->width, desc->height);
   }
   for (int t = 0; t < n_times; ++t) b.times[t] = times ? times[t] : 0.0f;
   b.n_views = n_views;
@@ -203,10 +252,10 @@ srn_status srn_create(const srn_config* cfg, const srn_params* params, srn_ctx**
   ctx->cfg = *cfg;
   ctx->prm = *params;
   cudaError_t e = cudaGetDevice(&ctx->device);
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->status, 4 * sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->status, 8 * sizeof(unsigned int));
   if (e == cudaSuccess) {
     ctx->ray_counter = reinterpret_cast<unsigned long long*>(ctx->status + 2);
-    e = cudaMemset(ctx->status, 0, 4 * sizeof(unsigned int));
+    e = cudaMemset(ctx->status, 0, 8 * sizeof(unsigned int));
   }
   if (e == cudaSuccess) e = fit_scratch_alloc(ctx->fit, make_net(ctx), cfg->max_fit_points);
   if (e != cudaSuccess) {
@@ -246,12 +295,7 @@ srn_status srn_sync_half(srn_ctx* ctx, void* stream) {
   if (!ctx->prm.grid_h || !ctx->prm.weights_h) return fail(SRN_ERR_INVALID_ARG, "no FP16 copies to write");
   srn_status st = use_device(ctx);
   if (st) return st;
-  NetDev n = make_net(ctx);
-  cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = launch_to_half(n.grid, (__half*)ctx->prm.grid_h, net_grid_count(n), s);
-  if (e == cudaSuccess) e = launch_to_half(n.W, (__half*)ctx->prm.weights_h, net_weight_count(n), s);
-  if (e == cudaSuccess && ctx->cfg.grid_u8)
-    e = launch_quantize_grid(n.grid, net_grid_count(n) / n.F, n.F, (uint8_t*)ctx->prm.grid_q, ctx->prm.grid_qp, s);
+  cudaError_t e = write_half_copies(ctx, (cudaStream_t)stream);
   return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_sync_half");
 }
 
@@ -316,8 +360,29 @@ srn_status srn_density_grad(srn_ctx* ctx, const float* pts_dev, int n, float tim
   if (n < 0 || (n > 0 && (!pts_dev || !rho_dev))) return fail(SRN_ERR_INVALID_ARG, "bad points / output");
   srn_status st = use_device(ctx);
   if (st) return st;
-  cudaError_t e = launch_eval_fp32(make_net(ctx), pts_dev, n, time, rho_dev, grad_dev, 1, (cudaStream_t)stream);
+  const NetDev net = make_net(ctx);
+  cudaError_t e;
+  if (ctx->cfg.precision == SRN_PREC_FP16) {
+    if (!density_grad_mma_supported(net))
+      return fail(SRN_ERR_UNSUPPORTED, "the FP16 tensor-core adjoint does not implement this shape");
+    e = launch_density_grad_mma(net, pts_dev, n, time, rho_dev, grad_dev, ctx->ray_counter, ctx->status,
+                                (cudaStream_t)stream);
+  } else {
+    e = launch_eval_fp32(net, pts_dev, n, time, rho_dev, grad_dev, 1, (cudaStream_t)stream);
+  }
   return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_density_grad");
+}
+
+srn_status srn_input_backward(srn_ctx* ctx, const float* pts_dev, int n, float time, const float* dout_dev,
+                              float* dpts_dev, void* stream) {
+  if (!ctx) return fail(SRN_ERR_INVALID_ARG, "ctx is NULL");
+  if (n < 0 || (n > 0 && (!pts_dev || !dout_dev || !dpts_dev)))
+    return fail(SRN_ERR_INVALID_ARG, "points, dout and dpts are required");
+  srn_status st = use_device(ctx);
+  if (st) return st;
+  cudaError_t e = launch_eval_fp32(make_net(ctx), pts_dev, n, time, nullptr, dpts_dev, 2, (cudaStream_t)stream,
+                                   dout_dev);
+  return e == cudaSuccess ? SRN_OK : cuda_fail(e, "srn_input_backward");
 }
 
 srn_status srn_backward(srn_ctx* ctx, const float* pts_dev, int n, float time, const float* dout_dev,
@@ -372,6 +437,7 @@ srn_status make_fit_args(srn_ctx* ctx, const float* volume_dev, const int dims[3
   a.status = ctx->status;
   a.grid_h = reinterpret_cast<__half*>(ctx->prm.grid_h);
   a.weights_h = reinterpret_cast<__half*>(ctx->prm.weights_h);
+  a.grid_exp = reinterpret_cast<const int*>(ctx->status + 4);
   a.adam_m = ctx->prm.adam_m;
   a.adam_v = ctx->prm.adam_v;
   a.grid = ctx->prm.grid;
@@ -618,8 +684,7 @@ srn_status srn_load(srn_ctx* ctx, const char* path, int* step_out) {
   free(host);
   if (e != cudaSuccess) return cuda_fail(e, "srn_load");
   if (ctx->prm.grid_h && ctx->prm.weights_h) {
-    e = launch_to_half(n.grid, (__half*)ctx->prm.grid_h, net_grid_count(n), 0);
-    if (e == cudaSuccess) e = launch_to_half(n.W, (__half*)ctx->prm.weights_h, net_weight_count(n), 0);
+    e = write_half_copies(ctx, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "srn_load");
   }
@@ -727,8 +792,8 @@ srn_status srn_lowpass_resample(const float* volume_dev, const int dims[3], int 
 
 // ---------------------------------------------------------------------------
 // srn_backward_static: the backward without any allocation, for callers that
-// cannot call cudaMalloc (stream capture in progress, device memory owned by
-// another allocator, frame loops that must not synchronize).  Its scratch is
+// cannot call cudaMalloc (device memory owned by another allocator, frame
+// loops that must not take an allocation's synchronization).  Its scratch is
 // the file-scope device array below.  In host code the array's name is only
 // a host-side stand-in for the symbol, never a device address: the address is
 // looked up with cudaGetSymbolAddress once per device (with that device

@@ -7,22 +7,15 @@ namespace srn {
 
 __device__ __forceinline__ float clamp01f(float x) { return fminf(fmaxf(x, 0.0f), 1.0f); }
 
-// Pinhole ray through the centre of pixel (px, py); row 0 at the top.
-__device__ __forceinline__ void camera_ray(const srn_camera& c, int W, int H, int px, int py, float3& o, float3& d) {
-  float fx = c.target[0] - c.eye[0], fy = c.target[1] - c.eye[1], fz = c.target[2] - c.eye[2];
-  float nf = sqrtf(fx * fx + fy * fy + fz * fz);
-  fx /= nf; fy /= nf; fz /= nf;
-  float rx = fy * c.up[2] - fz * c.up[1];
-  float ry = fz * c.up[0] - fx * c.up[2];
-  float rz = fx * c.up[1] - fy * c.up[0];
-  float nr = sqrtf(rx * rx + ry * ry + rz * rz);
-  rx /= nr; ry /= nr; rz /= nr;
-  float ux = ry * fz - rz * fy, uy = rz * fx - rx * fz, uz = rx * fy - ry * fx;
-  float th = tanf(0.5f * c.fovy);
-  float sx = (2.0f * (px + 0.5f) / W - 1.0f) * th * ((float)W / (float)H);
-  float sy = (1.0f - 2.0f * (py + 0.5f) / H) * th;
-  float dx = fx + sx * rx + sy * ux, dy = fy + sx * ry + sy * uy, dz = fz + sx * rz + sy * uz;
-  float nd = sqrtf(dx * dx + dy * dy + dz * dz);
+// Pinhole ray through the centre of pixel (px, py) in FP32 from the camera
+// frame (host-computed, see CamDev); row 0 at the top.
+__device__ __forceinline__ void camera_ray(const CamDev& c, int W, int H, int px, int py, float3& o, float3& d) {
+  const float sx = (2.0f * (px + 0.5f) / W - 1.0f) * c.tha[0];
+  const float sy = (1.0f - 2.0f * (py + 0.5f) / H) * c.th[0];
+  const float dx = c.f[0] + sx * c.r[0] + sy * c.u[0];
+  const float dy = c.f[1] + sx * c.r[1] + sy * c.u[1];
+  const float dz = c.f[2] + sx * c.r[2] + sy * c.u[2];
+  const float nd = sqrtf(dx * dx + dy * dy + dz * dz);
   d = make_float3(dx / nd, dy / nd, dz / nd);
   o = make_float3(c.eye[0], c.eye[1], c.eye[2]);
 }

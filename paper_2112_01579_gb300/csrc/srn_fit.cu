@@ -737,8 +737,9 @@ __device__ __forceinline__ void adam_update(float* __restrict__ grid, float* __r
                                             const float* __restrict__ g, float* __restrict__ m,
                                             float* __restrict__ v, size_t ng, size_t nW, size_t nb, float lr_grid,
                                             float lr_net, int step, __half* __restrict__ grid_h,
-                                            __half* __restrict__ W_h) {
+                                            __half* __restrict__ W_h, const int* __restrict__ grid_exp) {
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const int gk = (grid_h && grid_exp) ? *grid_exp : 0;
   const float t1 = (float)step + 1.0f;  // exact below 2^24; no int overflow at INT_MAX
   const float bc1 = 1.0f - powf(b1, t1), bc2 = 1.0f - powf(b2, t1);
   const size_t n = ng + nW + nb;
@@ -752,7 +753,7 @@ __device__ __forceinline__ void adam_update(float* __restrict__ grid, float* __r
     if (i < ng) {
       const float t = grid[i] - lr_grid * upd;
       grid[i] = t;
-      if (grid_h) grid_h[i] = __float2half_rn(t);
+      if (grid_h) grid_h[i] = __float2half_rn(ldexpf(t, -gk));
     } else if (i < ng + nW) {
       const float t = W[i - ng] - lr_net * upd;
       W[i - ng] = t;
@@ -772,12 +773,13 @@ __global__ void adam_kernel(float* __restrict__ grid, float* __restrict__ W, flo
                             const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v, size_t ng,
                             size_t nW, size_t nb, float lr_grid, float lr_net, int step_arg, int* __restrict__ step_ptr,
                             unsigned int* __restrict__ flag, unsigned int* __restrict__ status,
-                            __half* __restrict__ grid_h, __half* __restrict__ W_h) {
+                            __half* __restrict__ grid_h, __half* __restrict__ W_h,
+                            const int* __restrict__ grid_exp) {
   const int step = step_ptr ? *step_ptr : step_arg;
   if (*flag) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(status, (unsigned int)SRN_ERR_NONFINITE);
   } else {
-    adam_update(grid, W, b, g, m, v, ng, nW, nb, lr_grid, lr_net, step, grid_h, W_h);
+    adam_update(grid, W, b, g, m, v, ng, nW, nb, lr_grid, lr_net, step, grid_h, W_h, grid_exp);
   }
   if (step_ptr) {
     __syncthreads();  // every thread of the block has read *step_ptr
@@ -1036,7 +1038,8 @@ cudaError_t launch_fit_step(FitScratch& s, const NetDev& net, const FitArgs& a, 
   const size_t n = ng + nW + nb;
   unsigned int blocks = (unsigned int)std::min<size_t>((n + 255) / 256, (size_t)sm_count() * 8);
   adam_kernel<<<blocks, 256, 0, st>>>(a.grid, a.weights, a.biases, s.grads, a.adam_m, a.adam_v, ng, nW, nb, a.lr_grid,
-                                      a.lr_net, a.step, a.step_ptr, s.flag, a.status, a.grid_h, a.weights_h);
+                                      a.lr_net, a.step, a.step_ptr, s.flag, a.status, a.grid_h, a.weights_h,
+                                      a.grid_exp);
   return cudaGetLastError();
 }
 

@@ -42,6 +42,7 @@ struct FitArgs {
   float* biases;
   __half* grid_h;
   __half* weights_h;
+  const int* grid_exp;  // FP16 grid scale exponent: grid_h = fp16(grid 2^-k) (see NetDev)
   float* adam_m;
   float* adam_v;
   const unsigned long long* cdf;  // Section 6.2 adaptive distribution over cdf_res^3 voxels (null: uniform)

@@ -19,10 +19,11 @@ cudaError_t render_width(const NetDev& net, const BatchDev& b, cudaStream_t s) {
   }
 }
 template <int C>
-cudaError_t eval_width(const NetDev& net, const float* pts, int n, float time, float* out, float* grad, int mode,
-                       cudaStream_t s) {
-  if (mode == 0) return launch_eval_t<C, 0>(net, pts, n, time, out, grad, s);
-  return launch_eval_t<C, 1>(net, pts, n, time, out, grad, s);
+cudaError_t eval_width(const NetDev& net, const float* pts, int n, float time, float* out, float* grad,
+                       const float* dout, int mode, cudaStream_t s) {
+  if (mode == 0) return launch_eval_t<C, 0>(net, pts, n, time, out, grad, dout, s);
+  if (mode == 1) return launch_eval_t<C, 1>(net, pts, n, time, out, grad, dout, s);
+  return launch_eval_t<C, 2>(net, pts, n, time, out, grad, dout, s);
 }
 }  // namespace
 
@@ -33,11 +34,11 @@ cudaError_t launch_render_fp32(const NetDev& net, const BatchDev& b, cudaStream_
 }
 
 cudaError_t launch_eval_fp32(const NetDev& net, const float* pts, int n, float time, float* out, float* grad,
-                             int mode, cudaStream_t s) {
+                             int mode, cudaStream_t s, const float* dout) {
   if (n == 0) return cudaSuccess;
-  if (net.c == 48) return eval_width<48>(net, pts, n, time, out, grad, mode, s);
-  if (net.c == 64) return eval_width<64>(net, pts, n, time, out, grad, mode, s);
-  return eval_width<32>(net, pts, n, time, out, grad, mode, s);
+  if (net.c == 48) return eval_width<48>(net, pts, n, time, out, grad, dout, mode, s);
+  if (net.c == 64) return eval_width<64>(net, pts, n, time, out, grad, dout, mode, s);
+  return eval_width<32>(net, pts, n, time, out, grad, dout, mode, s);
 }
 
 }  // namespace srn

@@ -12,7 +12,7 @@ cudaError_t launch_render_t(const NetDev& net, const BatchDev& b, cudaStream_t s
 
 template <int C, int MODE>
 cudaError_t launch_eval_t(const NetDev& net, const float* pts, int n, float time, float* out, float* grad,
-                          cudaStream_t s);
+                          const float* dout, cudaStream_t s);
 
 }  // namespace fp32
 }  // namespace srn

@@ -39,23 +39,22 @@ __global__ void __launch_bounds__(kThreads) render_fp32_kernel(const NetDev net,
   if (px >= b.W || py >= b.H) return;
 
   const Latent lat = make_latent(net, b.times[ti]);
-  float3 o, d;
-  camera_ray(b.cams[view], b.W, b.H, px, py, o, d);
+  // ray geometry in double-float arithmetic (srn_df.cuh): direction, box
+  // entry / exit and sample positions carry ~44 bits, so the network sees
+  // positions rounded once
+  df::Ray ray;
   float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
   unsigned int ns = 0;
-  float t0, t1;
-  if (box_intersect(o, d, t0, t1)) {
-    for (int k = 0;; ++k) {
-      float ta = fmaf((float)k, b.step, t0);
-      if (ta >= t1) break;
-      float tb = fminf(fmaf((float)(k + 1), b.step, t0), t1);
-      float len = tb - ta, tm = 0.5f * (ta + tb);
-      float3 p = clamp_p(make_float3(fmaf(tm, d.x, o.x) + 0.5f, fmaf(tm, d.y, o.y) + 0.5f, fmaf(tm, d.z, o.z) + 0.5f));
+  if (df::ray_setup(b.cams[view], b.W, b.H, px, py, ray)) {
+    const float3 d = make_float3(ray.d[0].h, ray.d[1].h, ray.d[2].h);
+    float len;
+    float3 p, pl;
+    for (int k = 0; df::segment(ray, k, b.step, len, p, pl); ++k) {
       float3 g = make_float3(0.f, 0.f, 0.f);
-      float rho = sample_field<C, SH>(sm, L, net.act, lat, p, b.fd_h, g);
+      float rho = sample_field<C, SH>(sm, L, net.act, lat, p, pl, b.fd_h, g);
       ++ns;
       float4 c = tf_eval(tf, rho);
-      float alpha = 1.0f - expf(-c.w * tf.opacity_scale * len);
+      float alpha = -expm1f(-c.w * tf.opacity_scale * len);
       if (SH != SRN_SHADE_NONE) shade(c, g, d);
       float w = (1.0f - A) * alpha;
       C0 = fmaf(w, c.x, C0);
@@ -71,11 +70,13 @@ __global__ void __launch_bounds__(kThreads) render_fp32_kernel(const NetDev net,
 }
 
 // Point evaluation: mode 0 writes out[n][D]; mode 1 writes rho[n] and the
-// adjoint gradient grad[n][3] (when grad is not null).
+// adjoint gradient grad[n][3] (when grad is not null); mode 2 writes the
+// input vector-Jacobian product grad[n][3] = sum_d dout[n][d] d out_d / d p.
 template <int C, int MODE>
 __global__ void __launch_bounds__(kThreads) eval_fp32_kernel(const NetDev net, const float* __restrict__ pts, int n,
                                                              float time, float* __restrict__ out,
-                                                             float* __restrict__ grad, const Layout L) {
+                                                             float* __restrict__ grad,
+                                                             const float* __restrict__ dout, const Layout L) {
   extern __shared__ float4 smem4[];
   float* sm = reinterpret_cast<float*>(smem4);
   load_net<C>(sm, L, net);
@@ -87,16 +88,31 @@ __global__ void __launch_bounds__(kThreads) eval_fp32_kernel(const NetDev net, c
   if (MODE == 0) {
     forward<C, false>(sm, L, net.act, lat, p, o, nullptr);
     for (int d = 0; d < L.D; ++d) out[(size_t)j * L.D + d] = o[d];
-  } else {
+  } else if (MODE == 1) {
     float hs[kMaxL][C];
     forward<C, true>(sm, L, net.act, lat, p, o, hs);
     out[j] = o[0];
     if (grad) {
-      float3 g = adjoint<C>(sm, L, net.act, lat, p, hs);
+      float3 g = adjoint<C>(sm, L, net.act, lat, p, hs, sm + L.oWl);
       grad[3 * j] = g.x;
       grad[3 * j + 1] = g.y;
       grad[3 * j + 2] = g.z;
     }
+  } else {
+    float hs[kMaxL][C];
+    forward<C, true>(sm, L, net.act, lat, p, o, hs);
+    float seed[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) seed[c] = 0.0f;
+    for (int d = 0; d < L.D; ++d) {
+      const float s = dout[(size_t)j * L.D + d];
+#pragma unroll
+      for (int c = 0; c < C; ++c) seed[c] = fmaf(s, sm[L.oWl + d * C + c], seed[c]);
+    }
+    const float3 g = adjoint<C>(sm, L, net.act, lat, p, hs, seed);
+    grad[3 * j] = g.x;
+    grad[3 * j + 1] = g.y;
+    grad[3 * j + 2] = g.z;
   }
 }
 
@@ -115,13 +131,13 @@ cudaError_t launch_render_t(const NetDev& net, const BatchDev& b, cudaStream_t s
 
 template <int C, int MODE>
 cudaError_t launch_eval_t(const NetDev& net, const float* pts, int n, float time, float* out, float* grad,
-                          cudaStream_t s) {
-  Layout L = make_layout(net, MODE == 1);
+                          const float* dout, cudaStream_t s) {
+  Layout L = make_layout(net, MODE != 0);
   size_t smem = (size_t)L.total * sizeof(float);
   auto k = eval_fp32_kernel<C, MODE>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k<<<(n + kThreads - 1) / kThreads, kThreads, smem, s>>>(net, pts, n, time, out, grad, L);
+  k<<<(n + kThreads - 1) / kThreads, kThreads, smem, s>>>(net, pts, n, time, out, grad, dout, L);
   return cudaGetLastError();
 }
 
@@ -131,7 +147,7 @@ cudaError_t launch_eval_t(const NetDev& net, const float* pts, int n, float time
   template cudaError_t launch_render_t<C, SH>(const NetDev&, const BatchDev&, cudaStream_t);
 #define SRN_FP32_EVAL(C, MODE)                                                                  \
   template cudaError_t launch_eval_t<C, MODE>(const NetDev&, const float*, int, float, float*, float*, \
-                                              cudaStream_t);
+                                              const float*, cudaStream_t);
 
 }  // namespace fp32
 }  // namespace srn

@@ -7,6 +7,7 @@ namespace fp32 {
 
 SRN_FP32_RENDER(48, SRN_SHADE_ADJOINT)
 SRN_FP32_EVAL(48, 1)
+SRN_FP32_EVAL(48, 2)
 
 }  // namespace fp32
 }  // namespace srn

@@ -7,6 +7,7 @@ namespace fp32 {
 
 SRN_FP32_RENDER(64, SRN_SHADE_ADJOINT)
 SRN_FP32_EVAL(64, 1)
+SRN_FP32_EVAL(64, 2)
 
 }  // namespace fp32
 }  // namespace srn

@@ -32,12 +32,28 @@ struct NetDev {
   int gq;  // 1: the FP16 path reads the 8-bit grid
   const uint8_t* grid_q;  // 8-bit codes
   const float* grid_qp;   // [F][2] per-channel lo, step
+  // FP16 path: the FP16 latent grid holds G 2^-k (k = *grid_exp >= 0, chosen
+  // by srn_sync_half from max |G| so that the FP16 latent vector stays below
+  // 2^15); the layer-0 weights of the latent columns are staged times 2^k.
+  const int* grid_exp;
   float key_times[SRN_MAX_KEYFRAMES];
+};
+
+// Camera frame of a pinhole camera, computed on the host in FP64 from the
+// srn_camera (forward f = normalize(target - eye), right r = normalize(f x
+// up), up' = r x f, th = tan(fovy / 2), tha = th W / H) and stored as FP32
+// pairs value = hi + lo: the FP32 render builds its rays in double-float
+// arithmetic from the pairs, the other kernels use the FP32 parts.
+struct CamDev {
+  float eye[3];
+  float f[3], r[3], u[3];     // hi parts
+  float fl[3], rl[3], ul[3];  // lo parts
+  float th[2], tha[2];        // hi, lo
 };
 
 // One render batch: n_times x n_views frames of H x W pixels.
 struct BatchDev {
-  srn_camera cams[SRN_MAX_VIEWS];
+  CamDev cams[SRN_MAX_VIEWS];
   float times[SRN_MAX_TIMES];
   int n_views, n_times;
   int W, H;
@@ -58,8 +74,9 @@ struct VolDev {
 // Launchers (return the cudaGetLastError of the launch).
 cudaError_t launch_render_fp32(const NetDev& net, const BatchDev& b, cudaStream_t s);
 cudaError_t launch_dvr_dense(const VolDev& v, const BatchDev& b, cudaStream_t s);
+// mode 0: out[n][D]; 1: rho[n] + grad[n][3]; 2: grad[n][3] = sum_d dout[n][d] d out_d / d p
 cudaError_t launch_eval_fp32(const NetDev& net, const float* pts, int n, float time, float* out, float* grad,
-                             int mode, cudaStream_t s);  // mode 0: out[n][D]; 1: rho[n] + grad[n][3]
+                             int mode, cudaStream_t s, const float* dout = nullptr);
 bool render_fp32_supported(int width);
 
 // FP16 tensor-core render (tcgen05 / TMEM).
@@ -69,9 +86,19 @@ bool render_mma_supported(const NetDev& net, int shading);
 bool eval_mma_supported(const NetDev& net);
 cudaError_t launch_eval_mma(const NetDev& net, const float* pts, long long n, float time, float* out,
                             unsigned long long* ray_counter, unsigned int* status, cudaStream_t s);
+// Density and adjoint input gradient at n points on the tensor cores (the
+// render's adjoint MMAs; width 32, density output, at most four layers).
+bool density_grad_mma_supported(const NetDev& net);
+cudaError_t launch_density_grad_mma(const NetDev& net, const float* pts, long long n, float time, float* rho,
+                                    float* grad, unsigned long long* ray_counter, unsigned int* status,
+                                    cudaStream_t s);
 
 // Conversions and small utilities.
 cudaError_t launch_to_half(const float* src, __half* dst, size_t n, cudaStream_t s);
+// FP16 latent grid with power-of-two scaling: *exp_out = max(0, e - 15) for
+// max |grid| <= 2^e, then dst = fp16(grid 2^-k) (one block reduces, then a
+// grid-stride conversion reads the exponent from device memory).
+cudaError_t launch_grid_to_half_scaled(const float* grid, __half* dst, size_t n, int* exp_out, cudaStream_t s);
 cudaError_t launch_quantize_grid(const float* grid, size_t n_vert, int F, uint8_t* q, float* qp, cudaStream_t s);
 cudaError_t launch_image_mse(const float* a, const float* b, long long n, double* out, cudaStream_t s);
 cudaError_t launch_density_mse(const float* a, const float* b, long long n, double* out, cudaStream_t s);

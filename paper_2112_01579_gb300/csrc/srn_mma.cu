@@ -7,6 +7,7 @@
 
 namespace srn {
 using mma::kPoints;
+using mma::kPointsAdj;
 using mma::launch_t;
 using mma::PointsDev;
 
@@ -79,7 +80,7 @@ cudaError_t launch_eval_mma(const NetDev& n, const float* pts, long long count, 
   BatchDev b;
   memset(&b, 0, sizeof(b));
   b.tf.n = 2;
-  PointsDev pd{pts, out, count, time};
+  PointsDev pd{pts, out, count, time, nullptr};
   if (n.ti) return launch_t<32, 14, 16, SRN_ACT_SNAKEALT, kPoints, 1, 0>(n, b, pd, ctr, status, s);
   if (n.gq) return launch_t<32, 14, 16, SRN_ACT_SNAKEALT, kPoints, 0, 1>(n, b, pd, ctr, status, s);
   if (n.c == 48) return launch_t<48, 22, 16, SRN_ACT_SNAKEALT, kPoints, 0, 0>(n, b, pd, ctr, status, s);
@@ -89,6 +90,27 @@ cudaError_t launch_eval_mma(const NetDev& n, const float* pts, long long count, 
                                      : launch_t<32, 14, 16, SRN_ACT_SINE, kPoints, 0, 0>(n, b, pd, ctr, status, s);
   return n.act == SRN_ACT_SNAKEALT ? launch_t<32, 12, 8, SRN_ACT_SNAKEALT, kPoints, 0, 0>(n, b, pd, ctr, status, s)
                                    : launch_t<32, 12, 8, SRN_ACT_SINE, kPoints, 0, 0>(n, b, pd, ctr, status, s);
+}
+
+bool density_grad_mma_supported(const NetDev& n) {
+  return render_mma_supported(n, SRN_SHADE_ADJOINT) && n.D == 1;
+}
+
+// Density and adjoint input gradient at n points (mode kPointsAdj): the
+// forward and backward MMAs of the adjoint-shaded render without the march.
+cudaError_t launch_density_grad_mma(const NetDev& n, const float* pts, long long count, float time, float* rho,
+                                    float* grad, unsigned long long* ctr, unsigned int* status, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  BatchDev b;
+  memset(&b, 0, sizeof(b));
+  b.tf.n = 2;
+  PointsDev pd{pts, rho, count, time, grad};
+  if (n.m == 14 && n.F == 16)
+    return n.act == SRN_ACT_SNAKEALT
+               ? launch_t<32, 14, 16, SRN_ACT_SNAKEALT, kPointsAdj, 0, 0>(n, b, pd, ctr, status, s)
+               : launch_t<32, 14, 16, SRN_ACT_SINE, kPointsAdj, 0, 0>(n, b, pd, ctr, status, s);
+  return n.act == SRN_ACT_SNAKEALT ? launch_t<32, 12, 8, SRN_ACT_SNAKEALT, kPointsAdj, 0, 0>(n, b, pd, ctr, status, s)
+                                   : launch_t<32, 12, 8, SRN_ACT_SINE, kPointsAdj, 0, 0>(n, b, pd, ctr, status, s);
 }
 
 }  // namespace srn

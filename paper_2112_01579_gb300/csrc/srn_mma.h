@@ -9,30 +9,36 @@ namespace srn {
 namespace mma {
 
 
+constexpr int kPoints = 4;     // kernel mode: network output at given points (no ray march)
+constexpr int kPointsAdj = 5;  // kernel mode: density and adjoint input gradient at given points
+constexpr bool is_adjoint(int SH) { return SH == SRN_SHADE_ADJOINT || SH == kPointsAdj; }
+constexpr bool is_points(int SH) { return SH == kPoints || SH == kPointsAdj; }
+
 // Warpgroups per CTA for hidden width C and shading mode SH (one CTA per
 // SM): what the shared memory of the A tiles and weight tiles and the
 // register file allow.  Width 32 runs 7 (72 registers a thread), except the
-// finite-difference variant, whose extra state needs the 80 registers of 6.
+// finite-difference variant, whose extra state needs the 80 registers of 6,
+// and the adjoint variants, whose TMEM stash limits them to 4.
 constexpr int wgs_for(int C, int SH) {
-  return C == 32 ? (SH == SRN_SHADE_FD ? 6 : (SH == SRN_SHADE_ADJOINT ? 4 : 7)) : (C == 48 ? 4 : 3);
+  return C == 32 ? (SH == SRN_SHADE_FD ? 6 : (is_adjoint(SH) ? 4 : 7)) : (C == 48 ? 4 : 3);
 }
 // TMEM columns a CTA allocates, and the columns of one warpgroup: the
-// adjoint variant keeps a 64-column accumulator (the input-gradient MMA has
+// adjoint variants keep a 64-column accumulator (the input-gradient MMA has
 // N = 64) plus two 32-column stashes of activation derivatives.
-constexpr int tmem_cols_for(int SH) { return SH == SRN_SHADE_ADJOINT ? 512 : 256; }
-constexpr int tmem_wg_cols(int C, int SH) { return SH == SRN_SHADE_ADJOINT ? 128 : C; }
+constexpr int tmem_cols_for(int SH) { return is_adjoint(SH) ? 512 : 256; }
+constexpr int tmem_wg_cols(int C, int SH) { return is_adjoint(SH) ? 128 : C; }
 constexpr int kAdjMaxLayers = 4;  // layers of the networks the tensor-core adjoint takes
 constexpr int kTile = 128 * 128;       // one A K-atom: 128 rows x 128 B (64 fp16)
 
 constexpr long long kWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
-constexpr int kPoints = 4;             // kernel mode: network output at given points (no ray march)
 
-// Point-evaluation arguments (mode kPoints).
+// Point-evaluation arguments (modes kPoints, kPointsAdj).
 struct PointsDev {
   const float* pts;  // [n][3]
-  float* out;        // [n][D]
+  float* out;        // [n][D] (kPointsAdj: density [n])
   long long n;
   float time;
+  float* grad;       // kPointsAdj: d rho / d p [n][3], or null
 };
 
 // ---------------------------------------------------------------- layout

@@ -473,9 +473,9 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
   constexpr uint32_t IDESC = idesc_n(C);
   static_assert(C % 16 == 0 && C <= 64 && K0 <= 128, "shape outside the kernel's tiling");
   constexpr int NP = SH == SRN_SHADE_FD ? 7 : 1;  // network passes per sample
-  constexpr bool POINTS = SH == kPoints;
+  constexpr bool POINTS = is_points(SH);
   constexpr bool SNAKE = ACT == SRN_ACT_SNAKEALT;
-  constexpr bool ADJ = SH == SRN_SHADE_ADJOINT;  // input gradient by backward MMAs (Section 5 "adjoint")
+  constexpr bool ADJ = is_adjoint(SH);  // input gradient by backward MMAs (Section 5 "adjoint")
   constexpr int TMC = tmem_cols_for(SH);
   static_assert(!ADJ || (C == 32 && K0 <= 64 && TI == 0 && GQ == 0), "tensor-core adjoint: width 32, K0 <= 64");
 
@@ -499,6 +499,9 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
   const int wg = tid >> 7, row = tid & 127, lane = tid & 31;
   const int L = net.l, D = net.D;
   const int NA = NA0 > NAH ? NA0 : NAH;
+  // the FP16 latent grid holds G 2^-gexp: the latent columns' layer-0 weights
+  // are staged times 2^gexp (exact), the 8-bit grid's lo / step times 2^-gexp
+  const int gexp = net.grid_exp ? *net.grid_exp : 0;
 
   // ---- stage parameters as FP16 B tiles (row o = output neuron, K-major,
   // 128B-swizzled K-atoms).  Layer 0: columns in the tile's input order, FP32
@@ -541,7 +544,8 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
             if (col < 2 * M) src = (col & 1) ? 3 + M + (col >> 1) : 3 + (col >> 1);
             else if (col < 2 * M + 3) src = col - 2 * M;
             else if (col < D0) src = col;
-            if (src >= 0) v = __float2half_rn(scale * __half2float(Wsrc[src]));
+            const bool lat = src >= 3 + 2 * M && src < 3 + 2 * M + F;
+            if (src >= 0) v = __float2half_rn(ldexpf(scale * __half2float(Wsrc[src]), lat ? gexp : 0));
             if (col == D0) v = bh;
             if (col == D0 + 1) v = bl;
           } else {
@@ -612,7 +616,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
     }
     for (int i = tid; i < 3 * M; i += THREADS) fm[i] = net.fourier[i];
     if (GQ)
-      for (int i = tid; i < 2 * F; i += THREADS) qp[i] = net.grid_qp[i];
+      for (int i = tid; i < 2 * F; i += THREADS) qp[i] = ldexpf(net.grid_qp[i], -gexp);
   }
   load_tf(tf, b.tf);
   // the thread's A row starts at zero; the constant tile has ones in columns
@@ -746,6 +750,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
     float3 qs = make_float3(0.f, 0.f, 0.f);  // sample position of this pass
     if (POINTS && active && !failed) {
       write_input_row<M, F, K0, TI, GQ>(A, row, ppos, nerf, fm, net.grid_h, net.grid_q, qp, net.R, rl);
+      qs = ppos;
     } else if (active && !failed) {
       const float ta = fmaf((float)k, b.step, t0);
       const float tb = fminf(fmaf((float)(k + 1), b.step, t0), t1);
@@ -945,7 +950,8 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
                 gp.z = fmaf(coef, fm[3 * kq + 2], gp.z);
               }
             }
-            const float3 gl = latent_grad_h<F>(net.grid_h, net.R, rl, qs, gv + 2 * M + 3);
+            float3 gl = latent_grad_h<F>(net.grid_h, net.R, rl, qs, gv + 2 * M + 3);
+            gl = make_float3(ldexpf(gl.x, gexp), ldexpf(gl.y, gexp), ldexpf(gl.z, gexp));  // grid_h = G 2^-gexp
             gadj = make_float3(gp.x + gl.x, gp.y + gl.y, gp.z + gl.z);
           }
         }
@@ -955,6 +961,11 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
 
     if (POINTS) {
       if (active && !failed) {
+        if (ADJ && pd.grad) {
+          pd.grad[3 * pix] = gadj.x;
+          pd.grad[3 * pix + 1] = gadj.y;
+          pd.grad[3 * pix + 2] = gadj.z;
+        }
         for (int dd = 0; dd < D; ++dd) pd.out[pix * D + dd] = out[dd];
         overflow |= !(fabsf(out[0]) < INFINITY);
         ++ns;
@@ -1019,7 +1030,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
 template <int C, int M, int F, int ACT, int SH, int TI, int GQ>
 cudaError_t launch_t(const NetDev& net, const BatchDev& b, const PointsDev& pd, unsigned long long* ctr,
                      unsigned int* status, cudaStream_t s) {
-  SmemPlan plan = make_plan(net, C, wgs_for(C, SH), SH == SRN_SHADE_ADJOINT);
+  SmemPlan plan = make_plan(net, C, wgs_for(C, SH), is_adjoint(SH));
   auto k = render_mma_kernel<C, M, F, ACT, SH, TI, GQ>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total);
   if (e != cudaSuccess) return e;

@@ -5,6 +5,7 @@
 #pragma once
 
 #include "srn_device.cuh"
+#include "srn_df.cuh"
 
 namespace srn {
 namespace net32 {
@@ -219,7 +220,10 @@ __device__ __forceinline__ void latent4_grad(const Latent& lat, const Cell& c, i
 // A plain FP32 dot product would lose |e| * 2^-24 of the argument, which for
 // the high NeRF octaves (|e| in the thousands) dominates the error; the
 // rounded-to-nearest intrinsics keep the compiler from contracting the steps.
-__device__ __forceinline__ void fourier_sincos(const float* f, float3 p, float& s, float& c) {
+// pl is the low part of a position carried as a pair p + pl (the render's
+// sample positions); F_k . pl joins the low part of the argument.
+__device__ __forceinline__ void fourier_sincos(const float* f, float3 p, float& s, float& c,
+                                               float3 pl = make_float3(0.f, 0.f, 0.f)) {
   const float p0 = __fmul_rn(f[0], p.x), e0 = fmaf(f[0], p.x, -p0);
   const float p1 = __fmul_rn(f[1], p.y), e1 = fmaf(f[1], p.y, -p1);
   const float p2 = __fmul_rn(f[2], p.z), e2 = fmaf(f[2], p.z, -p2);
@@ -229,18 +233,19 @@ __device__ __forceinline__ void fourier_sincos(const float* f, float3 p, float& 
   const float hi = __fadd_rn(s1, p2);
   const float b2 = __fsub_rn(hi, s1);
   const float t2 = __fadd_rn(__fsub_rn(s1, __fsub_rn(hi, b2)), __fsub_rn(p2, b2));
-  const float lo = e0 + e1 + e2 + t1 + t2;
+  const float lo = e0 + e1 + e2 + t1 + t2 + (f[0] * pl.x + f[1] * pl.y + f[2] * pl.z);
   float sh, ch;
   sincosf(hi, &sh, &ch);
   s = fmaf(ch, lo, sh);
   c = fmaf(-sh, lo, ch);
 }
 
-// Full forward pass at p.  out[0..D-1]; when STASH, hs[i] receives the
-// pre-activation of layer i (i = 0..l-2) for the adjoint.
+// Full forward pass at p (+ pl, the low part of a position carried as a
+// pair, which only the Fourier arguments use).  out[0..D-1]; when STASH,
+// hs[i] receives the pre-activation of layer i (i = 0..l-2) for the adjoint.
 template <int C, bool STASH>
 __device__ __forceinline__ void forward(const float* sm, const Layout& L, int act, const Latent& lat, float3 p,
-                                        float (&out)[4], float (*hs)[C]) {
+                                        float (&out)[4], float (*hs)[C], float3 pl = make_float3(0.f, 0.f, 0.f)) {
   float h[C];
   const float* W0T = sm + L.oW0T;
 #pragma unroll
@@ -251,7 +256,7 @@ __device__ __forceinline__ void forward(const float* sm, const Layout& L, int ac
   const float* Fm = sm + L.oF;
   for (int k = 0; k < L.m; ++k) {
     float s, c;
-    fourier_sincos(Fm + 3 * k, p, s, c);
+    fourier_sincos(Fm + 3 * k, p, s, c, pl);
     axpy<C>(h, W0T + (3 + k) * C, s);
     axpy<C>(h, W0T + (3 + L.m + k) * C, c);
   }
@@ -289,17 +294,18 @@ __device__ __forceinline__ void forward(const float* sm, const Layout& L, int ac
     out[d] = d < L.D ? sm[L.obl + d] + dotrow<C>(sm + L.oWl + d * C, a) : 0.0f;
 }
 
-// Adjoint input gradient d out_0 / d p (Section 5 "Adjoint"): backpropagate
-// through the hidden layers, then through layer 0's inputs: identity for p,
-// cos(e) F_k / -sin(e) F_k for the Fourier features, trilinear Jacobian for
-// the latent vector.
+// Adjoint input gradient (Section 5 "Adjoint") of sum_d s_d out_d, whose
+// derivative with respect to the last hidden activation is seed[o] =
+// sum_d s_d W_last[d][o] (seed = row 0 of W_last: d out_0 / d p):
+// backpropagate through the hidden layers, then through layer 0's inputs:
+// identity for p, cos(e) F_k / -sin(e) F_k for the Fourier features,
+// trilinear Jacobian for the latent vector.
 template <int C>
 __device__ __forceinline__ float3 adjoint(const float* sm, const Layout& L, int act, const Latent& lat, float3 p,
-                                          float (*hs)[C]) {
+                                          float (*hs)[C], const float* seed, float3 pl = make_float3(0.f, 0.f, 0.f)) {
   float delta[C];
-  const float* Wl0 = sm + L.oWl;
 #pragma unroll
-  for (int o = 0; o < C; ++o) delta[o] = Wl0[o] * act_df(act, hs[L.l - 2][o]);
+  for (int o = 0; o < C; ++o) delta[o] = seed[o] * act_df(act, hs[L.l - 2][o]);
   for (int i = L.l - 2; i >= 1; --i) {
     const float* Wrm = sm + L.oHid + (i - 1) * L.hidStride + C * C + C;
     float g[C];
@@ -317,7 +323,7 @@ __device__ __forceinline__ float3 adjoint(const float* sm, const Layout& L, int 
     float gs = dotrow<C>(W0T + (3 + k) * C, delta);
     float gc = dotrow<C>(W0T + (3 + L.m + k) * C, delta);
     float s, c;
-    fourier_sincos(Fm + 3 * k, p, s, c);
+    fourier_sincos(Fm + 3 * k, p, s, c, pl);
     float coef = gs * c - gc * s;
     dp.x = fmaf(coef, Fm[3 * k], dp.x);
     dp.y = fmaf(coef, Fm[3 * k + 1], dp.y);
@@ -339,30 +345,30 @@ __device__ __forceinline__ float3 adjoint(const float* sm, const Layout& L, int 
 
 __device__ __forceinline__ float3 clamp_p(float3 p) { return make_float3(clamp01f(p.x), clamp01f(p.y), clamp01f(p.z)); }
 
-// Density (and gradient for shading) at p for shading mode SH.
+// Density (and gradient for shading) at the position ph + pl (a pair) for
+// shading mode SH; the finite-difference neighbours are offset as pairs.
 template <int C, int SH>
 __device__ __forceinline__ float sample_field(const float* sm, const Layout& L, int act, const Latent& lat, float3 p,
-                                              float fd_h, float3& g) {
+                                              float3 pl, float fd_h, float3& g) {
   float out[4];
   if (SH == SRN_SHADE_ADJOINT) {
     float hs[kMaxL][C];
-    forward<C, true>(sm, L, act, lat, p, out, hs);
-    g = adjoint<C>(sm, L, act, lat, p, hs);
+    forward<C, true>(sm, L, act, lat, p, out, hs, pl);
+    g = adjoint<C>(sm, L, act, lat, p, hs, sm + L.oWl, pl);
     return out[0];
   }
-  forward<C, false>(sm, L, act, lat, p, out, nullptr);
+  forward<C, false>(sm, L, act, lat, p, out, nullptr, pl);
   if (SH == SRN_SHADE_HEAD) g = make_float3(out[1], out[2], out[3]);
   if (SH == SRN_SHADE_FD) {
     float gg[3];
-    const float pp[3] = {p.x, p.y, p.z};
 #pragma unroll 1
     for (int a = 0; a < 3; ++a) {
-      float q[3] = {pp[0], pp[1], pp[2]}, r[3] = {pp[0], pp[1], pp[2]};
-      q[a] = clamp01f(pp[a] + fd_h);
-      r[a] = clamp01f(pp[a] - fd_h);
+      float3 qh = p, ql = pl, rh = p, rl = pl;
+      df::offset_axis(qh, ql, a, fd_h);
+      df::offset_axis(rh, rl, a, -fd_h);
       float o1[4], o2[4];
-      forward<C, false>(sm, L, act, lat, make_float3(q[0], q[1], q[2]), o1, nullptr);
-      forward<C, false>(sm, L, act, lat, make_float3(r[0], r[1], r[2]), o2, nullptr);
+      forward<C, false>(sm, L, act, lat, qh, o1, nullptr, ql);
+      forward<C, false>(sm, L, act, lat, rh, o2, nullptr, rl);
       gg[a] = (o1[0] - o2[0]) / (2.0f * fd_h);
     }
     g = make_float3(gg[0], gg[1], gg[2]);

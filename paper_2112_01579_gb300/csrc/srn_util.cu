@@ -297,6 +297,49 @@ cudaError_t launch_to_half(const float* src, __half* dst, size_t n, cudaStream_t
   return cudaGetLastError();
 }
 
+namespace {
+// Exponent of the FP16 latent-grid scale: the smallest k >= 0 with
+// max |grid| 2^-k <= 2^15 (max |grid| = 0 or non-finite: k = 0; a non-finite
+// grid is reported by the kernels that read it).
+__global__ void grid_exp_kernel(const float* __restrict__ g, size_t n, int* __restrict__ exp_out) {
+  __shared__ float red[32];
+  float m = 0.0f;
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, fabsf(g[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) {
+      int e = 0;
+      if (m > 0.0f && m <= 3.4e38f) frexpf(m, &e);  // m = f 2^e, f in [0.5, 1): m <= 2^e
+      *exp_out = e > 15 ? e - 15 : 0;
+    }
+  }
+}
+
+__global__ void to_half_scaled_kernel(const float* __restrict__ src, __half* __restrict__ dst, size_t n,
+                                      const int* __restrict__ exp_in) {
+  const int k = *exp_in;
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (; i < n; i += stride) dst[i] = __float2half_rn(ldexpf(src[i], -k));
+}
+}  // namespace
+
+cudaError_t launch_grid_to_half_scaled(const float* grid, __half* dst, size_t n, int* exp_out, cudaStream_t s) {
+  grid_exp_kernel<<<1, 1024, 0, s>>>(grid, n, exp_out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || n == 0) return e;
+  size_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  to_half_scaled_kernel<<<(unsigned)blocks, 256, 0, s>>>(grid, dst, n, exp_out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_image_mse(const float* a, const float* b, long long n, double* out, cudaStream_t s) {
   return launch_mse<4>(a, b, n, 3.0 * (double)n, out, s);
 }

@@ -27,7 +27,7 @@ EXPORTED = ["srn_version", "srn_last_error", "srn_create", "srn_destroy", "srn_s
             "srn_render", "srn_dvr_dense", "srn_eval", "srn_density_grad", "srn_backward", "srn_fit_step",
             "srn_sync_status", "srn_image_mse", "srn_backward_static", "srn_density_mse", "srn_resample",
             "srn_lowpass_resample", "srn_save", "srn_load", "srn_error_grid", "srn_fit_set_sampling",
-            "srn_fit_points", "srn_fit_steps", "srn_image_ssim"]
+            "srn_fit_points", "srn_fit_steps", "srn_image_ssim", "srn_input_backward"]
 
 
 class SrnError(RuntimeError):
@@ -86,6 +86,7 @@ def lib():
                                     C.POINTER(srn_render_desc), vp, vp, vp]
         L.srn_eval.argtypes = [vp, vp, i, f, vp, vp]
         L.srn_density_grad.argtypes = [vp, vp, i, f, vp, vp, vp]
+        L.srn_input_backward.argtypes = [vp, vp, i, f, vp, vp, vp]
         L.srn_backward.argtypes = [vp, vp, i, f, vp, vp, vp, vp, vp]
         L.srn_fit_step.argtypes = [vp, vp, C.POINTER(C.c_int), i, C.c_uint64, i, f, f, f, f, f, vp, vp]
         L.srn_sync_status.argtypes = [vp, vp]
@@ -199,6 +200,12 @@ def srn_density_grad(ctx, pts, rho, grad=None, time=0.0, stream=None):
                                   _stream(stream)))
 
 
+def srn_input_backward(ctx, pts, dout, dpts, time=0.0, stream=None):
+    """dpts [n, 3] = sum_d dout[:, d] * d out_d / d p (overwritten)."""
+    _check(lib().srn_input_backward(ctx, _ptr(pts), pts.shape[0], float(time), _ptr(dout), _ptr(dpts),
+                                    _stream(stream)))
+
+
 def srn_backward(ctx, pts, dout, dgrid, dweights, dbiases, time=0.0, stream=None):
     _check(lib().srn_backward(ctx, _ptr(pts), pts.shape[0], float(time), _ptr(dout), _ptr(dgrid), _ptr(dweights),
                               _ptr(dbiases), _stream(stream)))
@@ -206,8 +213,8 @@ def srn_backward(ctx, pts, dout, dgrid, dweights, dbiases, time=0.0, stream=None
 
 def srn_backward_static(cfg, params, pts, dout, dgrid, dweights, dbiases, time=0.0, stream=None):
     """srn_backward without a context and without any device allocation (a
-    fixed static scratch area inside the library); for callers that may not
-    allocate, e.g. while a stream is being captured into a CUDA graph."""
+    fixed device array inside the library); for callers that may not
+    allocate, e.g. hosts whose device memory belongs to another allocator."""
     _check(lib().srn_backward_static(C.byref(cfg), C.byref(params), _ptr(pts), pts.shape[0], float(time),
                                      _ptr(dout), _ptr(dgrid), _ptr(dweights), _ptr(dbiases), _stream(stream)))
 

@@ -47,11 +47,17 @@ def test_shaded_workload_full_size(srn, shading, precision):
     cams = synth.orbit_cameras(1)
     out = _render(S, net, cams, tf, 1024, 1024, 1 / 1024, 0.99, shading=shading, fd_h=1 / 511)
     pix = synth.sample_pixels(1, 1, 1024, 1024, 96, seed=81)
-    ref, mg, _ = oracle.render(oracle.OracleNet(q), cams, H.oracle_tf(tf), 1024, 1024, 1 / 1024, 0.99,
-                               shading=shading, fd_h=1 / 511, pixels=pix, want_margin=True)
+    on = oracle.OracleNet(q)
+    ref, mg, _ = oracle.render(on, cams, H.oracle_tf(tf), 1024, 1024, 1 / 1024, 0.99, shading=shading, fd_h=1 / 511,
+                               pixels=pix, want_margin=True)
+    _, bound = oracle.render_shade_bound(on, cams, H.oracle_tf(tf), 1024, 1024, 1 / 1024, 0.99, shading,
+                                         oracle.PREC_FP32 if precision == 0 else oracle.PREC_FP16, fd_h=1 / 511,
+                                         pixels=pix)
     got = out.reshape(-1, 4).cpu().numpy()[pix]
-    tol = (5 * H.TOL_FP32_IMG) if precision == 0 else (H.TOL_FP16_IMG if shading == 3 else 5 * H.TOL_FP16_IMG)
-    r = H.compare_images(got, ref, mg, tol, 0.99)
+    img_tol = H.TOL_FP32_IMG if precision == 0 else H.TOL_FP16_IMG
+    r = H.compare_images(got, ref, mg, H.shaded_tol(img_tol, bound), 0.99)
+    print(f"shaded workload {shading}/{precision}: max error {r['max_strict']:.2e}, worst error / bound "
+          f"{r['worst_ratio']:.2f}")
     assert r["ok"], r
 
 
@@ -67,9 +73,13 @@ def test_shaded_dense_dvr_512(srn):
     S.srn_dvr_dense(vol, cams, tf, S.render_desc(1024, 1024, 1 / 1024, 0.99, 2), out)
     torch.cuda.synchronize()
     pix = synth.sample_pixels(1, 1, 1024, 1024, 96, seed=83)
-    ref, mg, _ = oracle.dvr_dense(vol.cpu().numpy(), cams, H.oracle_tf(tf), 1024, 1024, 1 / 1024, 0.99, shading=2,
+    vol_np = vol.cpu().numpy()
+    ref, mg, _ = oracle.dvr_dense(vol_np, cams, H.oracle_tf(tf), 1024, 1024, 1 / 1024, 0.99, shading=2,
                                   pixels=pix, want_margin=True)
-    r = H.compare_images(out.reshape(-1, 4).cpu().numpy()[pix], ref, mg, 5 * H.TOL_FP32_IMG, 0.99)
+    _, bound = oracle.dvr_dense_shade_bound(vol_np, cams, H.oracle_tf(tf), 1024, 1024, 1 / 1024, 0.99,
+                                            H.dense_sample_error(vol_np), pixels=pix)
+    r = H.compare_images(out.reshape(-1, 4).cpu().numpy()[pix], ref, mg, H.shaded_tol(H.TOL_FP32_IMG, bound), 0.99)
+    print(f"shaded dense 512: max error {r['max_strict']:.2e}, worst error / bound {r['worst_ratio']:.2f}")
     assert r["ok"], r
 
 

@@ -49,6 +49,45 @@ def test_autograd_parameter_and_input_gradients(mods):
     assert _rel(pts.grad.cpu().numpy(), g * w_np) <= 1e-4
 
 
+@pytest.mark.parametrize("shape", ["cfg1", "head", "time"])
+def test_input_backward_matches_oracle(mods, shape):
+    """srn_input_backward: dpts = sum_d dout_d d out_d / d p (FP32) against
+    the oracle's backward with respect to the positions, element by element
+    at the FP32 gradient bound (1e-4 of max(|g|, 1) per point); for the
+    four-output head every output's gradient enters.  Through autograd too."""
+    import torch
+    S, A = mods
+    t = 0.0
+    if shape == "cfg1":
+        p = H.cfg1_params(seed=74)
+    elif shape == "head":
+        p = H.cfg2_params(seed=75, R=12, out_dim=4)
+    else:
+        p = synth.random_params(R=6, F=8, m=12, layers=3, width=32, act=synth.ACT_SNAKEALT, seed=76, grid_std=0.5,
+                                n_keyframes=3, key_times=[0.0, 1.0, 4.0])
+        t = 2.5
+    m = A.SRNModule(p, max_batch=4096)
+    net = m.net
+    rng = np.random.default_rng(77)
+    n = 3001
+    pts_np = rng.uniform(0, 1, (n, 3)).astype(np.float32)
+    pts_np[:3] = [[0, 0, 0], [1, 1, 1], [0.5, 1, 0]]
+    dout_np = rng.normal(size=(n, net.out_dim)).astype(np.float32)
+    pts = torch.tensor(pts_np, device="cuda")
+    dpts = torch.full((n, 3), float("nan"), device="cuda")
+    S.srn_input_backward(net.ctx, pts, torch.tensor(dout_np, device="cuda"), dpts, time=t)
+    torch.cuda.synchronize()
+    ref = oracle.net_input_vjp(oracle.OracleNet(p), pts_np, dout_np, t)
+    scale = np.maximum(np.abs(ref).max(axis=1, keepdims=True), 1.0)
+    err = (np.abs(dpts.cpu().numpy() - ref) / scale).max()
+    assert err <= 1e-4, err
+    pg = torch.tensor(pts_np, device="cuda", requires_grad=True)
+    (m(pg, t) * torch.tensor(dout_np, device="cuda")).sum().backward()
+    assert torch.equal(pg.grad, dpts)
+    S.srn_input_backward(net.ctx, torch.zeros((0, 3), device="cuda"), torch.zeros((0, net.out_dim), device="cuda"),
+                         torch.zeros((0, 3), device="cuda"))
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_torch_optimizer_trains_the_module(mods, precision):
     """A torch.optim.Adam loop on the L1 loss of Section 5 through the
