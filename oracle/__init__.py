@@ -142,7 +142,7 @@ class OracleNet:
         Ws = [np.asarray(w) for w in params["weights"]]
         self.W = np.concatenate([_d(w).reshape(-1) for w in Ws])
         self.b = np.concatenate([_d(b).reshape(-1) for b in params["biases"]])
-        self.key_times = _d(params.get("key_times", np.zeros(max(nkey, 1)))).reshape(-1)
+        self.key_times = _d32(params.get("key_times", np.zeros(max(nkey, 1)))).reshape(-1)
         c = Ws[0].shape[0] if len(Ws) > 1 else 0
         D = Ws[-1].shape[0]
         ti = int(params.get("time_input", 0))
@@ -219,7 +219,7 @@ def volume_fd_grad(vol, p):
 def net_forward(net: OracleNet, pts, t: float = 0.0) -> np.ndarray:
     P = _d(pts).reshape(-1, 3)
     out = np.zeros((len(P), net.dims["D"]))
-    lib().orc_net_forward(C.byref(net.s), _p(P), len(P), t, _p(out))
+    lib().orc_net_forward(C.byref(net.s), _p(P), len(P), _f32(t), _p(out))
     return out
 
 
@@ -230,7 +230,7 @@ def net_backward(net: OracleNet, pts, dout, t: float = 0.0):
     dW = np.zeros_like(net.W)
     db = np.zeros_like(net.b)
     dg = np.zeros_like(net.grid)
-    lib().orc_net_backward(C.byref(net.s), _p(P), len(P), t, _p(G), _p(dW), _p(db), _p(dg))
+    lib().orc_net_backward(C.byref(net.s), _p(P), len(P), _f32(t), _p(G), _p(dW), _p(db), _p(dg))
     return net.unpack_W(dW), net.unpack_b(db), dg
 
 
@@ -238,7 +238,7 @@ def net_input_grad(net: OracleNet, pts, t: float = 0.0):
     P = _d(pts).reshape(-1, 3)
     rho = np.zeros(len(P))
     g = np.zeros((len(P), 3))
-    lib().orc_net_input_grad(C.byref(net.s), _p(P), len(P), t, _p(rho), _p(g))
+    lib().orc_net_input_grad(C.byref(net.s), _p(P), len(P), _f32(t), _p(rho), _p(g))
     return rho, g
 
 
@@ -247,15 +247,26 @@ def net_input_vjp(net: OracleNet, pts, dout, t: float = 0.0):
     P = _d(pts).reshape(-1, 3)
     G = _d(dout).reshape(len(P), net.dims["D"])
     g = np.zeros((len(P), 3))
-    lib().orc_net_input_vjp(C.byref(net.s), _p(P), len(P), t, _p(G), _p(g))
+    lib().orc_net_input_vjp(C.byref(net.s), _p(P), len(P), _f32(t), _p(G), _p(g))
     return g
+
+
+def _f32(x):
+    """The FP32 value the C ABI receives for a scalar parameter (camera,
+    transfer function, step, threshold, time): the oracle is given the same
+    value, widened exactly."""
+    return float(np.float32(x))
+
+
+def _d32(a):
+    return np.ascontiguousarray(np.asarray(a, np.float32).astype(np.float64))
 
 
 class OracleTF:
     def __init__(self, pos, rgba, opacity_scale):
-        self.pos = _d(pos).reshape(-1)
-        self.rgba = _d(rgba).reshape(-1)
-        self.s = TF(len(self.pos), _p(self.pos), _p(self.rgba), float(opacity_scale))
+        self.pos = _d32(pos).reshape(-1)
+        self.rgba = _d32(rgba).reshape(-1)
+        self.s = TF(len(self.pos), _p(self.pos), _p(self.rgba), _f32(opacity_scale))
 
 
 def tf_eval(tf: OracleTF, rho: float):
@@ -267,10 +278,10 @@ def tf_eval(tf: OracleTF, rho: float):
 def _cams(cams):
     arr = (Camera * len(cams))()
     for i, c in enumerate(cams):
-        arr[i].eye[:] = list(map(float, c["eye"]))
-        arr[i].target[:] = list(map(float, c["target"]))
-        arr[i].up[:] = list(map(float, c["up"]))
-        arr[i].fovy = float(c["fovy"])
+        arr[i].eye[:] = [_f32(v) for v in c["eye"]]
+        arr[i].target[:] = [_f32(v) for v in c["target"]]
+        arr[i].up[:] = [_f32(v) for v in c["up"]]
+        arr[i].fovy = _f32(c["fovy"])
     return arr
 
 
@@ -297,14 +308,14 @@ def render(net: OracleNet, cams, tf: OracleTF, W, H, step, et, shading=SHADE_NON
            pixels=None, want_margin=False):
     """fV-SRN render.  Returns (rgba [n_pix, 4] or [T, V, H, W, 4], margin, samples)."""
     T = 1 if times is None else len(times)
-    tarr = None if times is None else _d(times)
+    tarr = None if times is None else _d32(times)
     pp, npix, keep = _pix(pixels)
     total = npix if pixels is not None else T * len(cams) * H * W
     out = np.zeros((total, 4))
     mg = np.zeros(total) if want_margin else None
     ns = C.c_longlong()
     lib().orc_render(C.byref(net.s), _cams(cams), len(cams), _p(tarr) if tarr is not None else None, T,
-                     C.byref(tf.s), W, H, step, et, shading, fd_h, pp, npix, _p(out),
+                     C.byref(tf.s), W, H, _f32(step), _f32(et), shading, _f32(fd_h), pp, npix, _p(out),
                      _p(mg) if mg is not None else None, C.byref(ns))
     if pixels is None:
         out = out.reshape(T, len(cams), H, W, 4)
@@ -321,7 +332,7 @@ def dvr_dense(vol, cams, tf: OracleTF, W, H, step, et, shading=SHADE_NONE, pixel
     out = np.zeros((total, 4))
     mg = np.zeros(total) if want_margin else None
     ns = C.c_longlong()
-    lib().orc_dvr_dense(_p(v), nx, ny, nz, _cams(cams), len(cams), C.byref(tf.s), W, H, step, et, shading, pp,
+    lib().orc_dvr_dense(_p(v), nx, ny, nz, _cams(cams), len(cams), C.byref(tf.s), W, H, _f32(step), _f32(et), shading, pp,
                         npix, _p(out), _p(mg) if mg is not None else None, C.byref(ns))
     if pixels is None:
         out = out.reshape(len(cams), H, W, 4)
@@ -346,7 +357,7 @@ def fit_loss_grad(net: OracleNet, vol, n_points, seed, step, t=0.0, gw=0.0, gs=1
     db = np.zeros_like(net.b)
     dg = np.zeros_like(net.grid)
     cp, cres = _cdf_args(cdf)
-    loss = lib().orc_fit_loss_grad(C.byref(net.s), _p(v), nx, ny, nz, n_points, seed, step, t, gw, gs, _p(dW),
+    loss = lib().orc_fit_loss_grad(C.byref(net.s), _p(v), nx, ny, nz, n_points, seed, step, _f32(t), _f32(gw), _f32(gs), _p(dW),
                                    _p(db), _p(dg), cp, cres)
     return loss, net.unpack_W(dW), net.unpack_b(db), dg
 
@@ -359,7 +370,7 @@ def fit_residuals(net: OracleNet, vol, n_points, seed, step, t=0.0, cdf=None):
     r = np.zeros(n_points)
     P = np.zeros((n_points, 3))
     cp, cres = _cdf_args(cdf)
-    lib().orc_fit_residuals(C.byref(net.s), _p(v), nx, ny, nz, n_points, seed, step, t, cp, cres, _p(r), _p(P))
+    lib().orc_fit_residuals(C.byref(net.s), _p(v), nx, ny, nz, n_points, seed, step, _f32(t), cp, cres, _p(r), _p(P))
     return r, P
 
 
@@ -368,7 +379,7 @@ def error_grid(net: OracleNet, vol, res, spv, seed, t=0.0):
     v = _d(vol)
     nz, ny, nx = v.shape
     E = np.zeros(res ** 3)
-    lib().orc_error_grid(C.byref(net.s), _p(v), nx, ny, nz, res, spv, seed, t, _p(E))
+    lib().orc_error_grid(C.byref(net.s), _p(v), nx, ny, nz, res, spv, seed, _f32(t), _p(E))
     return E.reshape(res, res, res)
 
 
@@ -411,8 +422,9 @@ def fit_step(net: OracleNet, adam_m, adam_v, vol, n_points, seed, step, lr_grid,
     grads = np.zeros(net.grid.size + net.W.size + net.b.size)
     st = C.c_int()
     cp, cres = _cdf_args(cdf)
-    loss = lib().orc_fit_step(C.byref(net.s), _p(adam_m), _p(adam_v), _p(v), nx, ny, nz, n_points, seed, step, t,
-                              lr_grid, lr_net, gw, gs, _p(grads), C.byref(st), cp, cres)
+    loss = lib().orc_fit_step(C.byref(net.s), _p(adam_m), _p(adam_v), _p(v), nx, ny, nz, n_points, seed, step,
+                              _f32(t), _f32(lr_grid), _f32(lr_net), _f32(gw), _f32(gs), _p(grads), C.byref(st), cp,
+                              cres)
     return loss, grads, st.value
 
 
@@ -460,7 +472,7 @@ def error_bounds(net: OracleNet, pts, prec, t: float = 0.0, grad=True):
     pr = _d(prec)
     Bo = np.zeros((len(P), net.dims["D"]))
     Bg = np.zeros((len(P), 3)) if grad else None
-    lib().orc_error_bounds(C.byref(net.s), _p(P), len(P), t, _p(pr), _p(Bo), _p(Bg) if grad else None)
+    lib().orc_error_bounds(C.byref(net.s), _p(P), len(P), _f32(t), _p(pr), _p(Bo), _p(Bg) if grad else None)
     return Bo, Bg
 
 
@@ -484,14 +496,15 @@ def render_shade_bound(net: OracleNet, cams, tf: OracleTF, W, H, step, et, shadi
     precision model prec causes (to be added to the unshaded image bound);
     with prec's rho_rel > 0, plus the propagated density error."""
     T = 1 if times is None else len(times)
-    tarr = None if times is None else _d(times)
+    tarr = None if times is None else _d32(times)
     pp, npix, keep = _pix(pixels)
     total = npix if pixels is not None else T * len(cams) * H * W
     out = np.zeros((total, 4))
     bound = np.zeros(total)
     pr = _d(prec)
     lib().orc_render_shade_bound(C.byref(net.s), _cams(cams), len(cams), _p(tarr) if tarr is not None else None, T,
-                                 C.byref(tf.s), W, H, step, et, shading, fd_h, pp, npix, _p(pr), _p(out), _p(bound))
+                                 C.byref(tf.s), W, H, _f32(step), _f32(et), shading, _f32(fd_h), pp, npix, _p(pr),
+                                 _p(out), _p(bound))
     if pixels is None:
         out = out.reshape(T, len(cams), H, W, 4)
         bound = bound.reshape(T, len(cams), H, W)
@@ -508,7 +521,8 @@ def dvr_dense_shade_bound(vol, cams, tf: OracleTF, W, H, step, et, vol_abs, pixe
     out = np.zeros((total, 4))
     bound = np.zeros(total)
     pr = _d((0, 0, 0, 0, 0, 0, 0, 0, vol_abs, 0))
-    lib().orc_dvr_dense_shade_bound(_p(v), nx, ny, nz, _cams(cams), len(cams), C.byref(tf.s), W, H, step, et, pp,
+    lib().orc_dvr_dense_shade_bound(_p(v), nx, ny, nz, _cams(cams), len(cams), C.byref(tf.s), W, H, _f32(step),
+                                    _f32(et), pp,
                                     npix, _p(pr), _p(out), _p(bound))
     if pixels is None:
         out = out.reshape(len(cams), H, W, 4)

@@ -317,7 +317,11 @@ def test_transfer_function_piecewise_linear():
 
 
 def test_camera_center_ray_and_field_of_view():
-    cam = dict(eye=[0.3, -1.2, 2.0], target=[0.1, 0.2, -0.3], up=[0, 1, 0], fovy=math.radians(60))
+    # the C ABI takes FP32 cameras: the closed forms use the same FP32 values
+    r32 = lambda v: [float(np.float32(x)) for x in v]
+    cam = dict(eye=r32([0.3, -1.2, 2.0]), target=r32([0.1, 0.2, -0.3]), up=[0, 1, 0],
+               fovy=float(np.float32(math.radians(60))))
+    half = 0.5 * cam["fovy"]
     W, H = 9, 7
     o, d = oracle.camera_ray(cam, W, H, 4, 3)
     f = np.subtract(cam["target"], cam["eye"])
@@ -326,12 +330,12 @@ def test_camera_center_ray_and_field_of_view():
     # top-centre pixel: angle to the axis is atan((1 - 1/H) tan(fovy/2)), and it tilts up
     _, d0 = oracle.camera_ray(cam, W, H, 4, 0)
     ang = math.acos(np.clip(np.dot(d0, f / np.linalg.norm(f)), -1, 1))
-    assert abs(ang - math.atan((1 - 1 / H) * math.tan(math.radians(30)))) < 1e-12
+    assert abs(ang - math.atan((1 - 1 / H) * math.tan(half))) < 1e-12
     assert d0[1] > d[1]
     # left-middle pixel: horizontal half-angle uses the aspect ratio
     _, d1 = oracle.camera_ray(cam, W, H, 0, 3)
     ang = math.acos(np.clip(np.dot(d1, f / np.linalg.norm(f)), -1, 1))
-    assert abs(ang - math.atan((1 - 1 / W) * math.tan(math.radians(30)) * W / H)) < 1e-12
+    assert abs(ang - math.atan((1 - 1 / W) * math.tan(half) * W / H)) < 1e-12
 
 
 def test_box_intersection():
@@ -361,6 +365,8 @@ def test_constant_slab_transmittance(eye, L, ds):
     """Constant density: prod_k exp(-kappa l_k) = exp(-kappa L) exactly,
     premultiplied colour = c (1 - exp(-kappa L))."""
     rho0, rgb, a, scale = 0.6, [0.2, 0.7, 0.4], 0.5, 3.0
+    ds = float(np.float32(ds))  # the C ABI's FP32 step, as the oracle receives it
+    rgb = [float(np.float32(c)) for c in rgb]
     net = _net(_params_linear(b=[rho0]))
     tf = _const_tf(rgb, a, scale)
     W = H = 5
@@ -375,7 +381,8 @@ def test_constant_slab_transmittance(eye, L, ds):
 def test_early_termination_step_index():
     """Termination after the first sample with A >= et: with full segments
     A_k = 1 - exp(-kappa k ds), so k* = ceil(ln(1/(1-et)) / (kappa ds))."""
-    kappa_a, scale, ds, et = 1.0, 37.0, 1 / 100, 0.99
+    # the C ABI's FP32 step and threshold, as the oracle receives them
+    kappa_a, scale, ds, et = 1.0, 37.0, float(np.float32(1 / 100)), float(np.float32(0.99))
     net = _net(_params_linear(b=[0.5]))
     tf = _const_tf([1, 1, 1], kappa_a, scale)
     out, mg, ns = oracle.render(net, [_axis_cam([0, 0, 2.5])], tf, 3, 3, ds, et, pixels=[4], want_margin=True)
@@ -540,7 +547,8 @@ def test_fit_step_equals_gradient_then_adam():
     for arr, g, lr in [(b.grid, dg, 1e-2), (b.W, np.concatenate([w.ravel() for w in dW]), 5e-3),
                        (b.b, np.concatenate([x.ravel() for x in db]), 5e-3)]:
         tp = torch.tensor(arr.copy(), requires_grad=True)
-        opt = torch.optim.Adam([tp], lr=lr, betas=(0.9, 0.999), eps=1e-8)
+        # the learning rates are FP32 values at the C ABI (and so in the oracle)
+        opt = torch.optim.Adam([tp], lr=float(np.float32(lr)), betas=(0.9, 0.999), eps=1e-8)
         tp.grad = torch.tensor(g)
         opt.step()
         arr[:] = tp.detach().numpy()
@@ -631,7 +639,7 @@ def test_direct_time_input_is_the_last_input():
     net = _net(p)
     for t in [0.0, 0.7, 1.9, 3.0]:
         out = oracle.net_forward(net, [[0.2, 0.4, 0.6]], t)[0, 0]
-        assert out == t + 0.5
+        assert out == float(np.float32(t)) + 0.5  # the time is an FP32 value at the C ABI
     # the time input changes nothing else: same net without it and a zero time weight agree
     p2 = synth.random_params(R=4, F=4, m=6, layers=3, width=8, seed=90, time_input=1)
     p2["weights"][0][:, -1] = 0.0

@@ -69,9 +69,11 @@ def test_dense_fd_shading_uses_the_exact_gradient():
         return 0.8 * (x - 0.5) ** 2 - 0.5 * (y - 0.5) ** 2 + 0.3 * (x - 0.5) * (y - 0.5) + 0.4 + 0 * z
 
     vol = _vertex_volume(q, nx, ny, nz)
-    rgba = np.array([0.9, 0.6, 0.3, 0.1])
+    # FP32 values, as the C ABI passes them (the oracle widens them exactly)
+    rgba = np.array([0.9, 0.6, 0.3, 0.1], np.float32).astype(np.float64)
     tf = oracle.OracleTF([0.0, 1.0], [rgba, rgba], 20.0)
-    cam = dict(eye=[0.0, 0.0, 2.0], target=[0.0, 0.0, 0.0], up=[0.0, 1.0, 0.0], fovy=math.radians(12.0))
+    cam = dict(eye=[0.0, 0.0, 2.0], target=[0.0, 0.0, 0.0], up=[0.0, 1.0, 0.0],
+               fovy=float(np.float32(math.radians(12.0))))
     W, H, ds = 7, 5, 1 / 32
     got, _, _ = oracle.dvr_dense(vol, [cam], tf, W, H, ds, 2.0, shading=oracle.SHADE_FD)
     kappa = rgba[3] * 20.0
@@ -198,8 +200,10 @@ def test_density_image_bound_constant_slab_closed_form():
     p["weights"][-1] = np.zeros_like(p["weights"][-1])
     b = float(np.float32(0.4))  # the network's parameters are float32
     p["biases"][-1] = np.array([b], np.float32)
-    a0, a1, s, e = 0.1, 0.5, 2.0, 1e-3
-    tf = oracle.OracleTF([0.0, 1.0], [[0.3, 0.6, 0.9, a0], [0.3, 0.6, 0.9, a0 + a1]], s)
+    # FP32 TF values, as the C ABI passes them: A(rho) = a0 + (top - a0) rho
+    a0, top, s, e = float(np.float32(0.1)), float(np.float32(0.6)), 2.0, 1e-3
+    a1 = top - a0
+    tf = oracle.OracleTF([0.0, 1.0], [[0.3, 0.6, 0.9, a0], [0.3, 0.6, 0.9, top]], s)
     cam = dict(eye=[0.0, 0.0, 2.0], target=[0.0, 0.0, 0.0], up=[0.0, 1.0, 0.0], fovy=0.5)
     for ds in (1 / 16, 1 / 100):
         img, bound = oracle.density_image_bound(oracle.OracleNet(p), [cam], tf, 1, 1, ds, 2.0, e)
