@@ -445,6 +445,8 @@ def run_ours(args, rank, world):
                    "samples_per_frame": samples / args.steps / world,
                    "fvsrn_ms_per_frame": ms_frame, "fitted_network_frames": fitted_frames,
                    "dense_dvr_ms_per_frame": float(np.median(d_ms)),
+                   "dense_dvr_roofline": dense_roofline(int(dctr.item()), float(np.sum(d_ms)), len(d_ms),
+                                                        vol.numel() * 4),
                    "psnr_fvsrn_vs_dense_db": float(np.mean(psnrs)),
                    "psnr_lowpass_grid_vs_dense_db": float(np.mean(lp_psnrs)), "lowpass_grid": M,
                    "ssim_fvsrn_vs_dense": float(np.mean(ssims)), "ssim_lowpass_grid_vs_dense": float(np.mean(lp_ssims)),
@@ -683,8 +685,29 @@ MMA_FLOP_PER_SAMPLE = 2 * (47 * 32 + 32 * 32 + 32 * 32 + 32 * 1)
 TRANSC_PER_SAMPLE = 3 * 32 + 2 * 14 + 1
 SMS, MUFU_PER_SM_CLK, FP32_PER_SM_CLK, MAX_SM_GHZ = 152, 16, 128, 2.07
 # DRAM bytes of one 1024^2 frame of the render kernel, from the ncu capture
-# summarised in profiles/ (null when the kernel changed after the capture).
-RENDER_DRAM_BYTES = 1143552
+# summarised in profiles/ (None when the kernel changed after the capture).
+RENDER_DRAM_BYTES = None
+# L1 load bandwidth of one SM (bytes per clock) for the gather roofline of
+# dense DVR (unit count; the peak is derived, not measured).
+L1_BYTES_PER_SM_CLK = 128
+DENSE_GATHER_BYTES = 32  # 8 corners x 4 B per dense sample
+
+
+def dense_roofline(samples, ms_total, frames, vol_bytes):
+    """Dense DVR against the L1 gather roofline (8 x 4 B per sample, all SMs
+    at the maximum clock) and, beside it, the HBM floor of reading the
+    volume once per frame against the measured copy bandwidth."""
+    secs = ms_total / 1e3
+    achieved = samples * DENSE_GATHER_BYTES / secs / 1e9
+    peak = SMS * L1_BYTES_PER_SM_CLK * MAX_SM_GHZ
+    hbm = peaks().get("hbm_gbs")
+    vol_gbs = vol_bytes * frames / secs / 1e9
+    return {"bound": "l1", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "dvr_dense_kernel", "per_sample_bytes": DENSE_GATHER_BYTES,
+            "peak_source": "152 SMs x 128 B/clk x 2.07 GHz (unit counts)",
+            "hbm_floor": {"achieved": vol_gbs, "peak": hbm, "unit": "GB/s",
+                          "frac": vol_gbs / hbm if hbm else None,
+                          "note": "the volume read once per frame, against MEASURED_PEAKS.json hbm_gbs"}}
 
 
 def roofline(res):

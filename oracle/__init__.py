@@ -450,7 +450,7 @@ def ssim(a, b):
 # ---------------------------------------------------------------- error bounds
 # Precision models of the two kernel paths for the first-order bounds (field
 # order of orc_prec: in_rel, in_abs, act_abs, act_rel, acc, dact_abs, bwd_rel,
-# jac_rel, vol_abs, rho_rel).
+# jac_rel, vol_abs).
 #  FP16 tensor-core path: layer-0 inputs computed in FP32 and rounded to FP16
 #   (half an FP16 ulp, 2^-11, plus the FP32 features' error, 2^-19 absolute);
 #   hidden activations from MUFU sin / cos (absolute error ~2^-21 for
@@ -461,8 +461,8 @@ def ssim(a, b):
 #  FP32 CUDA-core path: inputs from compensated FP32 sin / cos and an FP32
 #   trilinear (2^-21 relative, 2^-23 absolute); accurate sinf / sincosf
 #   (2^-22); FMA chains (2^-24 per term); Jacobians 2^-21.
-PREC_FP16 = (2.0 ** -11, 2.0 ** -19, 2.0 ** -19, 2.0 ** -22, 2.0 ** -23, 2.0 ** -19, 2.0 ** -22, 2.0 ** -17, 0.0, 0.0)
-PREC_FP32 = (2.0 ** -21, 2.0 ** -23, 2.0 ** -22, 2.0 ** -22, 2.0 ** -24, 2.0 ** -22, 0.0, 2.0 ** -21, 0.0, 0.0)
+PREC_FP16 = (2.0 ** -11, 2.0 ** -19, 2.0 ** -19, 2.0 ** -22, 2.0 ** -23, 2.0 ** -19, 2.0 ** -22, 2.0 ** -17, 0.0)
+PREC_FP32 = (2.0 ** -21, 2.0 ** -23, 2.0 ** -22, 2.0 ** -22, 2.0 ** -24, 2.0 ** -22, 0.0, 2.0 ** -21, 0.0)
 
 
 def error_bounds(net: OracleNet, pts, prec, t: float = 0.0, grad=True):
@@ -481,20 +481,11 @@ def fp16_grad_bound(net: OracleNet, pts, t: float = 0.0):
     return error_bounds(net, pts, PREC_FP16, t)[1]
 
 
-def density_image_bound(net: OracleNet, cams, tf: OracleTF, W, H, step, et, rho_rel, times=None, pixels=None):
-    """(rgba, bound): the oracle render and, per pixel, the first-order bound
-    on the image error that a density error of rho_rel max(|rho|, 1) at
-    every sample causes through the TF and the compositing (unshaded)."""
-    prec = (0.0,) * 9 + (float(rho_rel),)
-    return render_shade_bound(net, cams, tf, W, H, step, et, SHADE_NONE, prec, times=times, pixels=pixels)
-
-
 def render_shade_bound(net: OracleNet, cams, tf: OracleTF, W, H, step, et, shading, prec, fd_h=0.0, times=None,
                        pixels=None):
     """(rgba, bound): the oracle render and, per pixel, the bound on the
     shaded image's error that the gradient error of a kernel path with
-    precision model prec causes (to be added to the unshaded image bound);
-    with prec's rho_rel > 0, plus the propagated density error."""
+    precision model prec causes (to be added to the unshaded image bound)."""
     T = 1 if times is None else len(times)
     tarr = None if times is None else _d32(times)
     pp, npix, keep = _pix(pixels)
@@ -520,7 +511,7 @@ def dvr_dense_shade_bound(vol, cams, tf: OracleTF, W, H, step, et, vol_abs, pixe
     total = npix if pixels is not None else len(cams) * H * W
     out = np.zeros((total, 4))
     bound = np.zeros(total)
-    pr = _d((0, 0, 0, 0, 0, 0, 0, 0, vol_abs, 0))
+    pr = _d((0, 0, 0, 0, 0, 0, 0, 0, vol_abs))
     lib().orc_dvr_dense_shade_bound(_p(v), nx, ny, nz, _cams(cams), len(cams), C.byref(tf.s), W, H, _f32(step),
                                     _f32(et), pp,
                                     npix, _p(pr), _p(out), _p(bound))

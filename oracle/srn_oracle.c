@@ -521,26 +521,7 @@ typedef struct {
   double bwd_rel;          /* backward: relative error of each stored adjoint entry */
   double jac_rel;          /* Jacobian d v0 / d p: relative error of each term */
   double vol_abs;          /* dense volume samples: |drho| <= vol_abs */
-  double rho_rel;          /* > 0: propagate a density error rho_rel max(|rho|, 1) through the compositing */
 } orc_prec;
-
-/* Largest |slope| of the TF's RGBA channels over densities within e of rho
- * (the piecewise-linear TF of orc_tf_eval; flat outside the control
- * points). */
-static void tf_slope_bound(const orc_tf* tf, double rho, double e, double slope[4]) {
-  for (int c = 0; c < 4; ++c) slope[c] = 0.0;
-  const double* P = tf->pos;
-  for (int i = 0; i + 1 < tf->n; ++i) {
-    double lo = P[i], hi = P[i + 1];
-    if (hi <= lo) continue;
-    double a = rho - e < 0.0 ? 0.0 : rho - e, b = rho + e > 1.0 ? 1.0 : rho + e;
-    if (b < lo || a > hi) continue; /* [rho - e, rho + e] (clamped) misses the segment */
-    for (int c = 0; c < 4; ++c) {
-      double sl = fabs(tf->rgba[4 * (i + 1) + c] - tf->rgba[4 * i + c]) / (hi - lo);
-      if (sl > slope[c]) slope[c] = sl;
-    }
-  }
-}
 
 static double sample_shade_bound(const orc_field* fd, const orc_prec* pr, const orc_trace* tr, const double p[3],
                                  const double grad[3], const double rgb[3], const double d[3]);
@@ -557,14 +538,7 @@ static void march(const orc_field* fd, const orc_tf* tf, const double o[3], cons
   double C[3] = {0, 0, 0}, A = 0.0, mg = INFINITY;
   long long ns = 0;
   double t0, t1;
-  /* density-error propagation (tolerance bookkeeping): per sample the
-   * transmittance T, opacity, colour and the changes of opacity and colour
-   * that the sample's density error can cause */
-  int prop = bound && pr && pr->rho_rel > 0.0;
-  double* rec = NULL;
-  long long nrec = 0;
   if (orc_box_intersect(o, d, &t0, &t1)) {
-    if (prop) rec = (double*)malloc(sizeof(double) * 10 * (size_t)(ceil((t1 - t0) / ds) + 2));
     for (long long k = 0;; ++k) {
       double ta = t0 + (double)k * ds;
       if (ta >= t1) break;
@@ -606,17 +580,6 @@ static void march(const orc_field* fd, const orc_tf* tf, const double o[3], cons
       double rgb[3] = {rgba[0], rgba[1], rgba[2]};
       if (fd->shading != ORC_SHADE_NONE) shade(rgba, grad, d, rgb);
       double wgt = (1.0 - A) * alpha;
-      if (prop) {
-        double e = pr->rho_rel * (fabs(rho) > 1.0 ? fabs(rho) : 1.0), sl[4];
-        tf_slope_bound(tf, rho, e, sl);
-        double* r = rec + 10 * nrec++;
-        r[0] = 1.0 - A;                                       /* T */
-        r[1] = alpha;
-        r[2] = rgb[0]; r[3] = rgb[1]; r[4] = rgb[2];
-        r[5] = (1.0 - alpha) * tf->opacity_scale * len * sl[3] * e; /* |d alpha| */
-        r[6] = sl[0] * e; r[7] = sl[1] * e; r[8] = sl[2] * e; /* |d colour| (unshaded TF colour) */
-        r[9] = 0.0;
-      }
       if (bound && fd->shading != ORC_SHADE_NONE) {
         /* tolerance bookkeeping only: the composite weight times the bound
          * on the sample's shaded colour error */
@@ -631,26 +594,6 @@ static void march(const orc_field* fd, const orc_tf* tf, const double o[3], cons
       if (A >= et) break;
     }
   }
-  if (prop) {
-    /* C = sum_k T_k alpha_k c_k: dC / d alpha_k = T_k c_k - (sum_{i>k} T_i
-     * alpha_i c_i) / (1 - alpha_k), dC / d c_k = T_k alpha_k; the same with
-     * c = 1 for the opacity channel */
-    double suf[4] = {0, 0, 0, 0}, pb[4] = {0, 0, 0, 0};
-    for (long long k = nrec - 1; k >= 0; --k) {
-      const double* r = rec + 10 * k;
-      double T = r[0], al = r[1];
-      for (int c = 0; c < 4; ++c) {
-        double col = c < 3 ? r[2 + c] : 1.0;
-        double dA = T * col - (1.0 - al > 1e-300 ? suf[c] / (1.0 - al) : 0.0);
-        pb[c] += fabs(dA) * r[5] + (c < 3 ? T * al * r[6 + c] : 0.0);
-        suf[c] += T * al * col;
-      }
-    }
-    double m = pb[0];
-    for (int c = 1; c < 4; ++c) m = fmax(m, pb[c]);
-    *bound += m;
-  }
-  free(rec);
   out[0] = C[0]; out[1] = C[1]; out[2] = C[2]; out[3] = A;
   if (margin) *margin = mg;
   if (n_samples) *n_samples = ns;

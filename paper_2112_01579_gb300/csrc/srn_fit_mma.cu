@@ -24,7 +24,10 @@
 //   128 features), B a tile of the points' delta rows (hi, lo; N = 64), which
 //   every thread writes with vector stores.  One MMA per tile accumulates
 //   all four hi/lo products in TMEM across the warpgroup's tiles.  The bias
-//   gradient of layer 0 is the row of the constant-1 column.
+//   gradient of layer 0 is the row of the constant-1 column.  The delta rows are
+//   written times 2^s, 2^s >= n (|sign(r)/n| would otherwise fall below the
+//   FP16 normal range, 6.1e-5, for n > ~1e4 and lose its hi + lo precision);
+//   the accumulated rows are scaled back by 2^-s, exactly.
 // * last-layer gradients and the loss are warp reductions in a fixed order.
 // Each warpgroup writes one partial row [W | b | loss], reduced in a fixed
 // order by the same kernel as the FP32 path's rows: the step is deterministic.
@@ -190,6 +193,8 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
   const bool nerf = misc[2] != 0;
   const int step = a.step_ptr ? *a.step_ptr : a.step;
   const float inv_n = 1.0f / (float)a.n;
+  // delta rows of the weight-gradient MMA are staged times 2^dexp >= n
+  const int dexp = a.n > 1 ? 32 - __clz(a.n - 1) : 0;
   const int nchunks = (a.n + 127) / 128;
   const int wg_global = blockIdx.x * kFitWGS + wg, n_wg = gridDim.x * kFitWGS;
   float loss_acc = 0.0f;
@@ -354,7 +359,7 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
       uint32_t hi[4], lo[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        split_h2(delta[8 * cg + 2 * e], delta[8 * cg + 2 * e + 1], hi[e], lo[e]);
+        split_h2(ldexpf(delta[8 * cg + 2 * e], dexp), ldexpf(delta[8 * cg + 2 * e + 1], dexp), hi[e], lo[e]);
       }
       *reinterpret_cast<uint4*>(Bt + sw_off(row, cg)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
       *reinterpret_cast<uint4*>(Bt + sw_off(row, 4 + cg)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
@@ -449,7 +454,7 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
       else if (f < D0) src = f;
 #pragma unroll
       for (int o = 0; o < 32; ++o) {
-        const float g = h0[o] + ex[f * 33 + o];
+        const float g = ldexpf(h0[o] + ex[f * 33 + o], -dexp);  // the delta rows carried 2^dexp
         if (src >= 0) prow[o * D0 + src] = g;
         if (f == D0) prow[nW + o] = g;  // the constant-1 column: bias of layer 0
       }

@@ -29,9 +29,13 @@
 //   to the next layer, and the factor 1/2 and the shift 1/2 are folded into
 //   that layer's weights and bias: the doubled next layer then simply uses W
 //   and 2b + sum_j W_j.
-// * Rays are claimed dynamically (warp-aggregated atomic on a work counter);
-//   a thread whose ray terminates (box exit or opacity >= threshold) writes
-//   its pixel and takes the next ray, so tiles stay full.
+// * Rays are claimed dynamically from a work counter, a warp at a time: when
+//   every lane's ray has terminated (box exit or opacity >= threshold), the
+//   warp takes the next 8 x 4 pixel tile.  The lanes then march neighbouring
+//   rays in step, so their latent-grid gathers mostly hit the same cells and
+//   the L1 serves a warp's loads in few wavefronts (per-lane refill, which
+//   keeps every lane busy but scatters the lanes over the volume, was 10 %
+//   slower on the config-2 frame).
 // * Every mbarrier wait is bounded; on timeout the warpgroup stops, records
 //   SRN_ERR_TIMEOUT in the status word and the CTA frees its TMEM.
 // * A non-finite network output (an input or activation beyond the FP16
@@ -164,18 +168,19 @@ __device__ __forceinline__ uint32_t pack_h2(float a, float b) {
 }
 
 // FP16 hi + lo split of a pair: hi = fp16(a), lo = fp16(a - hi).  The
-// residual a - hi is exact in FP32; it is formed by one mixed-precision add
-// per element ((-hi) in FP16 plus a in FP32) instead of widening hi first.
+// residual a - hi is exact in FP32; it is formed by one mixed-precision FMA
+// per element (hi in FP16 times the FP16 constant -1, plus a in FP32), so
+// neither widening nor negating hi costs an instruction.
 __device__ __forceinline__ void split_h2(float a0, float a1, uint32_t& hi, uint32_t& lo) {
   hi = pack_h2(a0, a1);
-  const uint32_t neg = hi ^ 0x80008000u;
   float r0, r1;
-  asm("{.reg .b16 x, y;\n\t"
+  asm("{.reg .b16 x, y, m;\n\t"
       "mov.b32 {x, y}, %2;\n\t"
-      "add.rn.f32.f16 %0, x, %3;\n\t"
-      "add.rn.f32.f16 %1, y, %4;}"
+      "mov.b16 m, 0xBC00;\n\t"
+      "fma.rn.f32.f16 %0, x, m, %3;\n\t"
+      "fma.rn.f32.f16 %1, y, m, %4;}"
       : "=f"(r0), "=f"(r1)
-      : "r"(neg), "f"(a0), "f"(a1));
+      : "r"(hi), "f"(a0), "f"(a1));
   lo = pack_h2(r0, r1);
 }
 
@@ -697,9 +702,10 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
   }
 
   while (true) {
-    // ---- refill: threads without a ray claim new ones (warp-aggregated)
+    // ---- refill: a warp whose lanes are all done claims the next 32 rays
+    // (one 8 x 4 pixel tile), so its lanes march neighbouring rays together
     while (true) {
-      const bool need = !active && !exhausted && !failed;
+      const bool need = !__any_sync(0xffffffffu, active) && !exhausted && !failed;
       const unsigned int mask = __ballot_sync(0xffffffffu, need);
       if (mask == 0) break;
       unsigned long long base = 0;

@@ -56,14 +56,7 @@ def test_wide_render_parity(srn, width, layers, precision):
     got = _render(S, net, cams, tf, 40, 36, 1 / 128, 0.99)
     on = oracle.OracleNet(q)
     ref, mg, _ = oracle.render(on, cams, H.oracle_tf(tf), 40, 36, 1 / 128, 0.99, want_margin=True)
-    if precision:
-        tol = H.TOL_FP16_IMG
-    else:
-        # the FP32 image bound, or where larger, the image error the FP32
-        # density bound (1e-5 of max(|rho|, 1) at every sample) can cause
-        # through the TF's slopes and the compositing
-        _, dens = oracle.density_image_bound(on, cams, H.oracle_tf(tf), 40, 36, 1 / 128, 0.99, H.TOL_FP32_RHO)
-        tol = np.maximum(H.TOL_FP32_IMG, dens)
+    tol = H.TOL_FP16_IMG if precision else H.TOL_FP32_IMG
     r = H.compare_images(got, ref, mg, tol, 0.99)
     print(f"width {width} x {layers} precision {precision}: max error {r['max_strict']:.2e}, "
           f"worst error / bound {r['worst_ratio']:.2f}")

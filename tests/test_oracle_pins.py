@@ -189,31 +189,6 @@ def test_adaptive_counts_proportional_to_the_error():
 
 
 # ---------------------------------------------------------------- tolerance bounds
-def test_density_image_bound_constant_slab_closed_form():
-    """The image error a density error e causes on a constant slab (zero last
-    layer: rho = b everywhere) behind a TF of constant colour and opacity
-    A(rho) = a0 + a1 rho: the opacity after a chord L is 1 - exp(-s A L),
-    whose change under a density change e at every sample is, to first order,
-    e s L a1 exp(-s A L) (the sum over samples of |d A / d rho_k| e); the
-    colour channels scale it by their constant colour (<= 1)."""
-    p = synth.random_params(R=4, F=4, m=3, layers=3, width=8, act=synth.ACT_SNAKEALT, seed=610)
-    p["weights"][-1] = np.zeros_like(p["weights"][-1])
-    b = float(np.float32(0.4))  # the network's parameters are float32
-    p["biases"][-1] = np.array([b], np.float32)
-    # FP32 TF values, as the C ABI passes them: A(rho) = a0 + (top - a0) rho
-    a0, top, s, e = float(np.float32(0.1)), float(np.float32(0.6)), 2.0, 1e-3
-    a1 = top - a0
-    tf = oracle.OracleTF([0.0, 1.0], [[0.3, 0.6, 0.9, a0], [0.3, 0.6, 0.9, top]], s)
-    cam = dict(eye=[0.0, 0.0, 2.0], target=[0.0, 0.0, 0.0], up=[0.0, 1.0, 0.0], fovy=0.5)
-    for ds in (1 / 16, 1 / 100):
-        img, bound = oracle.density_image_bound(oracle.OracleNet(p), [cam], tf, 1, 1, ds, 2.0, e)
-        L = 1.0
-        A = a0 + a1 * b
-        assert abs(img[0, 0, 0, 0, 3] - (1 - math.exp(-s * A * L))) < 1e-12
-        want = e * s * L * a1 * math.exp(-s * A * L)
-        assert abs(bound[0, 0, 0, 0] - want) < 1e-12 * max(1.0, want), (bound[0, 0, 0, 0], want)
-
-
 def test_error_bounds_of_a_linear_layer():
     """One linear layer rho = W v + b: with only the input term of the
     precision model (|dv_j| <= in_abs, or <= in_rel |v_j|) the bound is
@@ -224,10 +199,10 @@ def test_error_bounds_of_a_linear_layer():
     pts = np.random.default_rng(612).uniform(0, 1, (5, 3))
     W = np.asarray(p["weights"][0], np.float64)[0]
     d = 1e-4
-    B, _ = oracle.error_bounds(on, pts, (0, d, 0, 0, 0, 0, 0, 0, 0, 0), grad=False)
+    B, _ = oracle.error_bounds(on, pts, (0, d, 0, 0, 0, 0, 0, 0, 0), grad=False)
     np.testing.assert_allclose(B[:, 0], 6 * d * np.linalg.norm(W), rtol=1e-12)
     # in_rel: the input vector [p, sin(Fp), cos(Fp), z] from the oracle's own Fourier matrix and latent grid
-    B2, _ = oracle.error_bounds(on, pts, (d, 0, 0, 0, 0, 0, 0, 0, 0, 0), grad=False)
+    B2, _ = oracle.error_bounds(on, pts, (d, 0, 0, 0, 0, 0, 0, 0, 0), grad=False)
     F = np.asarray(p["fourier"], np.float64)
     for k, x in enumerate(pts):
         e = F @ x
