@@ -684,9 +684,11 @@ def _cpu_model():
 MMA_FLOP_PER_SAMPLE = 2 * (47 * 32 + 32 * 32 + 32 * 32 + 32 * 1)
 TRANSC_PER_SAMPLE = 3 * 32 + 2 * 14 + 1
 SMS, MUFU_PER_SM_CLK, FP32_PER_SM_CLK, MAX_SM_GHZ = 152, 16, 128, 2.07
-# DRAM bytes of one 1024^2 frame of the render kernel, from the ncu capture
-# summarised in profiles/ (None when the kernel changed after the capture).
-RENDER_DRAM_BYTES = None
+# DRAM bytes (read + write) of one 1024^2 frame of the render kernel and of
+# the dense DVR, from the ncu captures summarised in profiles/ (None when the
+# kernel changed after the capture).
+RENDER_DRAM_BYTES = 1136384
+DENSE_DRAM_BYTES = 67166208 + 9174016
 # L1 load bandwidth of one SM (bytes per clock) for the gather roofline of
 # dense DVR (unit count; the peak is derived, not measured).
 L1_BYTES_PER_SM_CLK = 128
@@ -703,7 +705,7 @@ def dense_roofline(samples, ms_total, frames, vol_bytes):
     hbm = peaks().get("hbm_gbs")
     vol_gbs = vol_bytes * frames / secs / 1e9
     return {"bound": "l1", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "dvr_dense_kernel", "per_sample_bytes": DENSE_GATHER_BYTES,
+            "traffic": DENSE_DRAM_BYTES, "kernel": "dvr_dense_kernel", "per_sample_bytes": DENSE_GATHER_BYTES,
             "peak_source": "152 SMs x 128 B/clk x 2.07 GHz (unit counts)",
             "hbm_floor": {"achieved": vol_gbs, "peak": hbm, "unit": "GB/s",
                           "frac": vol_gbs / hbm if hbm else None,
@@ -802,7 +804,7 @@ def summarize_launches(path):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fit-steps", type=int, default=FIT_STEPS)

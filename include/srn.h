@@ -215,8 +215,10 @@ srn_status srn_eval(srn_ctx* ctx, const float* pts_dev, int n, float time, float
  * NULL).  Precision follows the context: FP32 CUDA cores, or on FP16 contexts
  * the tensor-core adjoint of the render (FP16 operands, hidden activations
  * and adjoint rows as FP16 hi + lo pairs, FP32 accumulate), which takes
- * width-32 density networks of at most four layers, 12 Fourier rows / 8
- * latent channels or 14 / 16, no time input, FP16 grid (other shapes on FP16
+ * networks of at most four layers, no time input, FP16 grid, of width 32
+ * (12 Fourier rows / 8 latent channels or 14 / 16) or widths 48 / 64 (22 /
+ * 30 Fourier rows, 16 latent channels, SnakeAlt); rho and the gradient are
+ * those of output 0, so 4-output heads are taken too (other shapes on FP16
  * contexts: SRN_ERR_UNSUPPORTED). */
 srn_status srn_density_grad(srn_ctx* ctx, const float* pts_dev, int n, float time, float* rho_dev,
                             float* grad_dev, void* stream);

@@ -450,19 +450,21 @@ def ssim(a, b):
 # ---------------------------------------------------------------- error bounds
 # Precision models of the two kernel paths for the first-order bounds (field
 # order of orc_prec: in_rel, in_abs, act_abs, act_rel, acc, dact_abs, bwd_rel,
-# jac_rel, vol_abs).
+# jac_rel, vol_abs, lat_w).
 #  FP16 tensor-core path: layer-0 inputs computed in FP32 and rounded to FP16
 #   (half an FP16 ulp, 2^-11, plus the FP32 features' error, 2^-19 absolute);
 #   hidden activations from MUFU sin / cos (absolute error ~2^-21 for
 #   |x| <= pi, taken as 2^-20 (1 + |x|)) carried as FP16 hi + lo (2^-22);
 #   tensor-core FP32 accumulation (2^-23 per term, K terms); derivatives from
 #   MUFU as the activations; adjoint rows as hi + lo (2^-22); Fourier and
-#   latent Jacobians recomputed in FP32 with angle doubling (2^-17).
+#   latent Jacobians recomputed in FP32 with angle doubling (2^-17); the
+#   trilinear latent weights rounded to FP16 (2^-11 of sum_k w_k |G_k|).
 #  FP32 CUDA-core path: inputs from compensated FP32 sin / cos and an FP32
 #   trilinear (2^-21 relative, 2^-23 absolute); accurate sinf / sincosf
 #   (2^-22); FMA chains (2^-24 per term); Jacobians 2^-21.
-PREC_FP16 = (2.0 ** -11, 2.0 ** -19, 2.0 ** -19, 2.0 ** -22, 2.0 ** -23, 2.0 ** -19, 2.0 ** -22, 2.0 ** -17, 0.0)
-PREC_FP32 = (2.0 ** -21, 2.0 ** -23, 2.0 ** -22, 2.0 ** -22, 2.0 ** -24, 2.0 ** -22, 0.0, 2.0 ** -21, 0.0)
+PREC_FP16 = (2.0 ** -11, 2.0 ** -19, 2.0 ** -19, 2.0 ** -22, 2.0 ** -23, 2.0 ** -19, 2.0 ** -22, 2.0 ** -17, 0.0,
+             2.0 ** -11)
+PREC_FP32 = (2.0 ** -21, 2.0 ** -23, 2.0 ** -22, 2.0 ** -22, 2.0 ** -24, 2.0 ** -22, 0.0, 2.0 ** -21, 0.0, 0.0)
 
 
 def error_bounds(net: OracleNet, pts, prec, t: float = 0.0, grad=True):
@@ -511,7 +513,7 @@ def dvr_dense_shade_bound(vol, cams, tf: OracleTF, W, H, step, et, vol_abs, pixe
     total = npix if pixels is not None else len(cams) * H * W
     out = np.zeros((total, 4))
     bound = np.zeros(total)
-    pr = _d((0, 0, 0, 0, 0, 0, 0, 0, vol_abs))
+    pr = _d((0, 0, 0, 0, 0, 0, 0, 0, vol_abs, 0))
     lib().orc_dvr_dense_shade_bound(_p(v), nx, ny, nz, _cams(cams), len(cams), C.byref(tf.s), W, H, _f32(step),
                                     _f32(et), pp,
                                     npix, _p(pr), _p(out), _p(bound))

@@ -521,6 +521,7 @@ typedef struct {
   double bwd_rel;          /* backward: relative error of each stored adjoint entry */
   double jac_rel;          /* Jacobian d v0 / d p: relative error of each term */
   double vol_abs;          /* dense volume samples: |drho| <= vol_abs */
+  double lat_w;            /* latent weights rounded: |dz_c| += lat_w sum_k w_k |G_kc| */
 } orc_prec;
 
 static double sample_shade_bound(const orc_field* fd, const orc_prec* pr, const orc_trace* tr, const double p[3],
@@ -986,12 +987,38 @@ static void layer_deltas(const orc_net* n, const orc_trace* tr, int d, double de
   }
 }
 
+/* sum_k w_k |G_kc| over the 8 corners (and the two keyframes, with their
+ * time weights) of the trilinear latent vector at the traced position. */
+static void latent_abs(const orc_net* n, const orc_trace* tr, double t, double* za) {
+  size_t gsz = (size_t)n->R * n->R * n->R * n->F;
+  int k0, ix, iy, iz;
+  double f, fx, fy, fz;
+  time_weights(n, t, &k0, &f);
+  cell_coord(tr->p[0], n->R, &ix, &fx);
+  cell_coord(tr->p[1], n->R, &iy, &fy);
+  cell_coord(tr->p[2], n->R, &iz, &fz);
+  for (int c = 0; c < n->F; ++c) za[c] = 0.0;
+  for (int kk = 0; kk < (n->nkey > 1 ? 2 : 1); ++kk) {
+    double tw = (n->nkey > 1) ? (kk ? f : 1.0 - f) : 1.0;
+    const double* G = n->grid + (size_t)(k0 + kk) * gsz;
+    for (int dz = 0; dz < 2; ++dz)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+          double w = tw * (dx ? fx : 1.0 - fx) * (dy ? fy : 1.0 - fy) * (dz ? fz : 1.0 - fz);
+          size_t v = (((size_t)(iz + dz) * n->R + (iy + dy)) * n->R + (ix + dx)) * (size_t)n->F;
+          for (int c = 0; c < n->F; ++c) za[c] += w * fabs(G[v + c]);
+        }
+  }
+}
+
 /* Scales of the forward sites: sv[i][j] for input j of layer i (its
  * rounding), sr[i][o] for the accumulation of pre-activation h_i[o]. */
-static void forward_sites(const orc_net* n, const orc_trace* tr, const orc_prec* pr, double sv[ORC_MAXL][ORC_MAXW],
-                          double sr[ORC_MAXL][ORC_MAXW]) {
+static void forward_sites(const orc_net* n, const orc_trace* tr, double t, const orc_prec* pr,
+                          double sv[ORC_MAXL][ORC_MAXW], double sr[ORC_MAXL][ORC_MAXW]) {
   const double* W = n->W;
   const double* b = n->b;
+  double za[ORC_MAXW];
+  if (pr->lat_w > 0.0) latent_abs(n, tr, t, za);
   for (int i = 0; i < n->l; ++i) {
     int din = layer_in(n, i), dout_i = layer_out(n, i);
     int K = i == 0 ? din + 2 : 2 * din + 2;
@@ -999,6 +1026,8 @@ static void forward_sites(const orc_net* n, const orc_trace* tr, const orc_prec*
       double v = tr->v[i][j];
       sv[i][j] = i == 0 ? pr->in_rel * fabs(v) + pr->in_abs
                         : pr->act_abs * (1.0 + fabs(tr->h[i - 1][j])) + pr->act_rel * fabs(v);
+      int zc = j - 3 - 2 * n->m;
+      if (i == 0 && pr->lat_w > 0.0 && zc >= 0 && zc < n->F) sv[i][j] += pr->lat_w * za[zc];
     }
     for (int o = 0; o < dout_i; ++o) {
       double mag = fabs(b[o]);
@@ -1011,9 +1040,9 @@ static void forward_sites(const orc_net* n, const orc_trace* tr, const orc_prec*
 }
 
 /* Bound on the error of output d of a traced evaluation. */
-static double output_bound(const orc_net* n, const orc_trace* tr, const orc_prec* pr, int d) {
+static double output_bound(const orc_net* n, const orc_trace* tr, double t, const orc_prec* pr, int d) {
   static __thread double sv[ORC_MAXL][ORC_MAXW], sr[ORC_MAXL][ORC_MAXW], delta[ORC_MAXL][ORC_MAXW];
-  forward_sites(n, tr, pr, sv, sr);
+  forward_sites(n, tr, t, pr, sv, sr);
   layer_deltas(n, tr, d, delta);
   double var = 0.0;
   const double* W = n->W;
@@ -1101,7 +1130,7 @@ static void gradient_bound(const orc_net* n, const orc_trace* tr0, double t, con
   size_t woff[ORC_MAXL + 1];
   woff[0] = 0;
   for (int i = 0; i < L; ++i) woff[i + 1] = woff[i] + (size_t)layer_out(n, i) * layer_in(n, i);
-  forward_sites(n, tr0, pr, sv, sr);
+  forward_sites(n, tr0, t, pr, sv, sr);
   input_jacobian(n, tr0, t, J);
   double g0[3], var[3] = {0.0, 0.0, 0.0};
   traced_gradient(n, tr0, J, g0, delta, dv0);
@@ -1197,7 +1226,7 @@ void orc_error_bounds(const orc_net* n, const double* pts, int n_pts, double t, 
   for (int j = 0; j < n_pts; ++j) {
     orc_trace* tr = (orc_trace*)malloc(sizeof(orc_trace));
     forward(n, pts + 3 * j, t, tr);
-    for (int d = 0; d < n->D; ++d) B_out[(size_t)j * n->D + d] = output_bound(n, tr, &pr, d);
+    for (int d = 0; d < n->D; ++d) B_out[(size_t)j * n->D + d] = output_bound(n, tr, t, &pr, d);
     if (B_grad) gradient_bound(n, tr, t, &pr, B_grad + 3 * (size_t)j);
     free(tr);
   }
@@ -1221,7 +1250,7 @@ static double sample_shade_bound(const orc_field* fd, const orc_prec* pr, const 
     e2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
   } else if (fd->net && fd->shading == ORC_SHADE_HEAD) {
     for (int a = 0; a < 3; ++a) {
-      double b = output_bound(fd->net, tr, pr, 1 + a);
+      double b = output_bound(fd->net, tr, fd->time, pr, 1 + a);
       e2 += b * b;
     }
   } else if (fd->shading == ORC_SHADE_FD) {
@@ -1234,7 +1263,7 @@ static double sample_shade_bound(const orc_field* fd, const orc_prec* pr, const 
         q[a] = clamp01(p[a] + sg * h);
         if (fd->net) {
           forward(fd->net, q, fd->time, tq);
-          s += output_bound(fd->net, tq, pr, 0);
+          s += output_bound(fd->net, tq, fd->time, pr, 0);
         } else {
           s += pr->vol_abs;
         }

@@ -36,10 +36,10 @@ int mma_smem_bytes(const NetDev& n, int shading) {
 
 bool render_mma_supported(const NetDev& n, int shading) {
   if (n.l < 2 || n.l > 8) return false;
-  // adjoint: backward MMAs at width 32, density output, at most four layers
-  // (two stashed derivative blocks in TMEM), no time input, FP16 grid
-  if (shading == SRN_SHADE_ADJOINT && !(n.c == 32 && n.D == 1 && n.l <= mma::kAdjMaxLayers && !n.ti && !n.gq))
-    return false;
+  // adjoint: backward MMAs, at most four layers (two stashed derivative
+  // blocks in TMEM), no time input, FP16 grid; the gradient is that of
+  // output 0, so the 4-output head is taken too
+  if (shading == SRN_SHADE_ADJOINT && !(n.l <= mma::kAdjMaxLayers && !n.ti && !n.gq)) return false;
   if (shading == SRN_SHADE_HEAD && n.D != 4) return false;
   if (n.ti && !(n.c == 32 && n.m == 14 && n.F == 16 && n.act == SRN_ACT_SNAKEALT && shading == SRN_SHADE_NONE))
     return false;
@@ -48,8 +48,9 @@ bool render_mma_supported(const NetDev& n, int shading) {
     return false;
   const bool shape_a = n.c == 32 && n.m == 14 && n.F == 16;
   const bool shape_b = n.c == 32 && n.m == 12 && n.F == 8;
-  const bool shape_c = n.c == 48 && n.m == 22 && n.F == 16 && n.act == SRN_ACT_SNAKEALT && shading == SRN_SHADE_NONE;
-  const bool shape_d = n.c == 64 && n.m == 30 && n.F == 16 && n.act == SRN_ACT_SNAKEALT && shading == SRN_SHADE_NONE;
+  // widths 48 / 64: the sweep's inputs (22 / 30 Fourier rows, 16 latent channels), SnakeAlt, every shading
+  const bool shape_c = n.c == 48 && n.m == 22 && n.F == 16 && n.act == SRN_ACT_SNAKEALT;
+  const bool shape_d = n.c == 64 && n.m == 30 && n.F == 16 && n.act == SRN_ACT_SNAKEALT;
   if (!shape_a && !shape_b && !shape_c && !shape_d) return false;
   const int smem = mma_smem_bytes(n, shading);
   if (smem == 0 || smem > 227 * 1024) return false;
@@ -61,8 +62,8 @@ cudaError_t launch_render_mma(const NetDev& n, const BatchDev& b, unsigned long 
                               cudaStream_t s) {
   if (n.ti) return launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 1, 0>(n, b, PointsDev{}, ctr, status, s);
   if (n.gq) return launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 0, 1>(n, b, PointsDev{}, ctr, status, s);
-  if (n.c == 48) return launch_t<48, 22, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 0, 0>(n, b, PointsDev{}, ctr, status, s);
-  if (n.c == 64) return launch_t<64, 30, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 0, 0>(n, b, PointsDev{}, ctr, status, s);
+  if (n.c == 48) return dispatch_shading<48, 22, 16, SRN_ACT_SNAKEALT>(n, b, ctr, status, s);
+  if (n.c == 64) return dispatch_shading<64, 30, 16, SRN_ACT_SNAKEALT>(n, b, ctr, status, s);
   if (n.m == 14 && n.F == 16) {
     return n.act == SRN_ACT_SNAKEALT ? dispatch_shading<32, 14, 16, SRN_ACT_SNAKEALT>(n, b, ctr, status, s)
                                      : dispatch_shading<32, 14, 16, SRN_ACT_SINE>(n, b, ctr, status, s);
@@ -92,9 +93,7 @@ cudaError_t launch_eval_mma(const NetDev& n, const float* pts, long long count, 
                                    : launch_t<32, 12, 8, SRN_ACT_SINE, kPoints, 0, 0>(n, b, pd, ctr, status, s);
 }
 
-bool density_grad_mma_supported(const NetDev& n) {
-  return render_mma_supported(n, SRN_SHADE_ADJOINT) && n.D == 1;
-}
+bool density_grad_mma_supported(const NetDev& n) { return render_mma_supported(n, SRN_SHADE_ADJOINT); }
 
 // Density and adjoint input gradient at n points (mode kPointsAdj): the
 // forward and backward MMAs of the adjoint-shaded render without the march.
@@ -105,6 +104,8 @@ cudaError_t launch_density_grad_mma(const NetDev& n, const float* pts, long long
   memset(&b, 0, sizeof(b));
   b.tf.n = 2;
   PointsDev pd{pts, rho, count, time, grad};
+  if (n.c == 48) return launch_t<48, 22, 16, SRN_ACT_SNAKEALT, kPointsAdj, 0, 0>(n, b, pd, ctr, status, s);
+  if (n.c == 64) return launch_t<64, 30, 16, SRN_ACT_SNAKEALT, kPointsAdj, 0, 0>(n, b, pd, ctr, status, s);
   if (n.m == 14 && n.F == 16)
     return n.act == SRN_ACT_SNAKEALT
                ? launch_t<32, 14, 16, SRN_ACT_SNAKEALT, kPointsAdj, 0, 0>(n, b, pd, ctr, status, s)

@@ -20,14 +20,21 @@ constexpr bool is_points(int SH) { return SH == kPoints || SH == kPointsAdj; }
 // finite-difference variant, whose extra state needs the 80 registers of 6,
 // and the adjoint variants, whose TMEM stash limits them to 4.
 constexpr int wgs_for(int C, int SH) {
-  return C == 32 ? (SH == SRN_SHADE_FD ? 6 : (is_adjoint(SH) ? 4 : 7)) : (C == 48 ? 4 : 3);
+  return is_adjoint(SH) ? (C == 32 ? 4 : 2)
+                        : (C == 32 ? (SH == SRN_SHADE_FD ? 6 : 7) : (C == 48 ? 4 : 3));
 }
-// TMEM columns a CTA allocates, and the columns of one warpgroup: the
-// adjoint variants keep a 64-column accumulator (the input-gradient MMA has
-// N = 64) plus two 32-column stashes of activation derivatives.
-constexpr int tmem_cols_for(int SH) { return is_adjoint(SH) ? 512 : 256; }
-constexpr int tmem_wg_cols(int C, int SH) { return is_adjoint(SH) ? 128 : C; }
 constexpr int kAdjMaxLayers = 4;  // layers of the networks the tensor-core adjoint takes
+// TMEM columns a CTA allocates, and the columns of one warpgroup.  The
+// adjoint variants keep an accumulator wide enough for the input-gradient
+// MMA (N = K0, the layer-0 input columns) and for the hidden layers (N = C),
+// rounded up to 32 columns, followed by the stashed activation derivatives
+// of the (at most two) hidden layers, C columns each: 64 + 64 (width 32, four
+// warpgroups), 96 + 96 (48, two), 96 + 128 (64, two).
+constexpr int tmem_cols_for(int SH) { return is_adjoint(SH) ? 512 : 256; }
+constexpr int adj_acc_cols(int C, int K0) { return (((K0 > C ? K0 : C) + 31) / 32) * 32; }
+constexpr int tmem_wg_cols(int C, int SH, int K0) {
+  return is_adjoint(SH) ? adj_acc_cols(C, K0) + (kAdjMaxLayers - 2) * C : C;
+}
 constexpr int kTile = 128 * 128;       // one A K-atom: 128 rows x 128 B (64 fp16)
 
 constexpr long long kWaitCycles = 2000000000ll;  // ~1 s at 2 GHz

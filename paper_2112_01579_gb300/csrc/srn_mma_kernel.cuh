@@ -218,7 +218,12 @@ struct RayLat {
 };
 
 // Latent vector (Section 4.2 trilinear latent grid; Section 7 time blend)
-// from the FP16 grid, accumulated in FP32.
+// from the FP16 grid, accumulated in FP32.  Each corner's weight is rounded
+// to FP16 and the products taken by mixed-precision FMAs (FP16 weight times
+// FP16 grid value, exact, plus the FP32 sum): one instruction per channel
+// and corner instead of a widening and an FMA.  The weight rounding (2^-11
+// relative) moves z_c by at most 2^-11 sum_k w_k |G_kc|, about as much as the
+// FP16 rounding of z itself for the A tile.
 template <int F>
 __device__ __forceinline__ void latent_h(const __half* __restrict__ G, int R, const RayLat& rl, float3 p,
                                          float (&z)[F]) {
@@ -240,16 +245,21 @@ __device__ __forceinline__ void latent_h(const __half* __restrict__ G, int R, co
     for (int kk = 0; kk < 2; ++kk) {
       const int g = kk ? rl.g1 : rl.g0;
       if (kk && g < 0) break;
-      const float ww = w * (kk ? rl.w1 : rl.w0);
+      const __half wh = __float2half_rn(w * (kk ? rl.w1 : rl.w0));
+      const uint16_t wb = *reinterpret_cast<const uint16_t*>(&wh);
 #pragma unroll
       for (int c = 0; c < F; c += 8) {
-        uint4 q = __ldg(reinterpret_cast<const uint4*>(G + g + off + c));
-        const __half2* h = reinterpret_cast<const __half2*>(&q);
+        const uint4 q = __ldg(reinterpret_cast<const uint4*>(G + g + off + c));
+        const uint32_t qq[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          float2 v = __half22float2(h[e]);
-          z[c + 2 * e] = fmaf(ww, v.x, z[c + 2 * e]);
-          z[c + 2 * e + 1] = fmaf(ww, v.y, z[c + 2 * e + 1]);
+          asm("{.reg .b16 x, y, w;\n\t"
+              "mov.b32 {x, y}, %2;\n\t"
+              "mov.b16 w, %3;\n\t"
+              "fma.rn.f32.f16 %0, x, w, %0;\n\t"
+              "fma.rn.f32.f16 %1, y, w, %1;}"
+              : "+f"(z[c + 2 * e]), "+f"(z[c + 2 * e + 1])
+              : "r"(qq[e]), "h"(wb));
         }
       }
     }
@@ -420,6 +430,25 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) 
       : "memory");
 }
 
+// Thread's TMEM lane, 16 consecutive FP32 columns written, store waited for.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};\n\t"
+      "tcgen05.wait::st.sync.aligned;"
+      ::"r"(taddr), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]),
+        "f"(v[8]), "f"(v[9]), "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15])
+      : "memory");
+}
+
+// Thread's TMEM lane, C consecutive FP32 columns written (C a multiple of 16).
+template <int C>
+__device__ __forceinline__ void tmem_st_row(uint32_t taddr, const float (&v)[C]) {
+#pragma unroll
+  for (int c = 0; c + 32 <= C; c += 32) tmem_st32(taddr + c, *reinterpret_cast<const float(*)[32]>(v + c));
+  if constexpr (C % 32 != 0) tmem_st16(taddr + (C - 16), v + (C - 16));
+}
+
 // Gradient with respect to p of sum_c gz[c] z_c(p), z the latent vector
 // (trilinear in p inside the cell chosen by cell_coord, time-blended):
 // sum over corners and keyframes of w_time (gz . g_corner) grad w_corner(p),
@@ -482,7 +511,9 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
   constexpr bool SNAKE = ACT == SRN_ACT_SNAKEALT;
   constexpr bool ADJ = is_adjoint(SH);  // input gradient by backward MMAs (Section 5 "adjoint")
   constexpr int TMC = tmem_cols_for(SH);
-  static_assert(!ADJ || (C == 32 && K0 <= 64 && TI == 0 && GQ == 0), "tensor-core adjoint: width 32, K0 <= 64");
+  constexpr int NACC = adj_acc_cols(C, K0);  // adjoint: accumulator columns before the derivative stash
+  static_assert(!ADJ || (TI == 0 && GQ == 0), "tensor-core adjoint: no time input, FP16 grid");
+  static_assert(!ADJ || WGS * tmem_wg_cols(C, SH, K0) <= TMC, "adjoint TMEM layout exceeds the allocation");
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -665,7 +696,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
   __syncthreads();
   const bool nerf = misc[1] != 0;
   const uint32_t tmem = (uint32_t)misc[0];
-  const uint32_t d_tmem = tmem + (uint32_t)(wg * tmem_wg_cols(C, SH));
+  const uint32_t d_tmem = tmem + (uint32_t)(wg * tmem_wg_cols(C, SH, K0));
   const uint32_t t_row = d_tmem + ((uint32_t)((row >> 5) * 32) << 16);  // warp's lane quarter
   uint8_t* A = Aall + wg * NA * kTile;
   const uint32_t a_addr = smem_u32(A), b0_addr = smem_u32(B0), bh_addr = smem_u32(Bh), bb_addr = smem_u32(Bb);
@@ -820,10 +851,10 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
           if constexpr (ADJ) {
             // activation derivative of this hidden layer, kept in TMEM for the
             // backward: SnakeAlt' = 0.5 + sin(2x) (the accumulator holds 2x); sin' = cos
-            float dv[32];
+            float dv[C];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) dv[j] = SNAKE ? 0.5f + __sinf(x[j]) : __cosf(x[j]);
-            tmem_st32(t_row + 64 + 32 * layer, dv);
+            for (int j = 0; j < C; ++j) dv[j] = SNAKE ? 0.5f + __sinf(x[j]) : __cosf(x[j]);
+            tmem_st_row<C>(t_row + NACC + C * layer, dv);
           }
         }
         fence_proxy_async();
@@ -908,15 +939,14 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
         tc_fence_after();
         if (failed) continue;
         if (h >= 1) {
-          float g[32], dv[32];
-          tmem_ld32(t_row, g);
-          tmem_ld32(t_row + 64 + 32 * (h - 1), dv);
+          float g[C], dv[C];
+          tmem_ld_row<C>(t_row, g);
+          tmem_ld_row<C>(t_row + NACC + C * (h - 1), dv);
 #pragma unroll
           for (int j = 0; j < C; ++j) dl[j] = g[j] * dv[j];
         } else {
-          float gv[64];
-          tmem_ld32(t_row, *reinterpret_cast<float(*)[32]>(gv));
-          tmem_ld32(t_row + 32, *reinterpret_cast<float(*)[32]>(gv + 32));
+          float gv[K0];
+          tmem_ld_row<K0>(t_row, gv);
           if (active) {
             // position columns, then the Fourier features (d sin e = cos e F_k,
             // d cos e = -sin e F_k), then the latent vector
@@ -967,12 +997,18 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
 
     if (POINTS) {
       if (active && !failed) {
-        if (ADJ && pd.grad) {
-          pd.grad[3 * pix] = gadj.x;
-          pd.grad[3 * pix + 1] = gadj.y;
-          pd.grad[3 * pix + 2] = gadj.z;
+        if constexpr (ADJ) {
+          // density and gradient mode: out is the density [n] (output 0 of a
+          // 4-output head), grad [n][3]
+          pd.out[pix] = out[0];
+          if (pd.grad) {
+            pd.grad[3 * pix] = gadj.x;
+            pd.grad[3 * pix + 1] = gadj.y;
+            pd.grad[3 * pix + 2] = gadj.z;
+          }
+        } else {
+          for (int dd = 0; dd < D; ++dd) pd.out[pix * D + dd] = out[dd];
         }
-        for (int dd = 0; dd < D; ++dd) pd.out[pix * D + dd] = out[dd];
         overflow |= !(fabsf(out[0]) < INFINITY);
         ++ns;
         active = false;

@@ -151,7 +151,7 @@ def test_mma_adjoint_shapes(srn, shape):
     assert r["ok"], r
 
 
-@pytest.mark.parametrize("shape", ["cfg1", "cfg2", "snake_l3", "init_cfg2", "keyframes"])
+@pytest.mark.parametrize("shape", ["cfg1", "cfg2", "snake_l3", "init_cfg2", "keyframes", "head", "w48", "w64"])
 def test_mma_adjoint_gradient_matches_oracle(srn, shape):
     """srn_density_grad on an FP16 context runs the tensor-core adjoint (the
     render's backward MMAs, Section 5 "adjoint") at given points: the density
@@ -172,9 +172,15 @@ def test_mma_adjoint_gradient_matches_oracle(srn, shape):
                                 grid_std=0.5, bias_std=0.2)
     elif shape == "init_cfg2":
         p = synth.init_params(R=32, F=16, m=14, layers=4, width=32, act=synth.ACT_SNAKEALT, seed=0)
-    else:
+    elif shape == "keyframes":
         p = H.cfg2_params(seed=93, R=12, nkey=3, key_times=[0.0, 1.0, 3.0])
         t = 1.6
+    elif shape == "head":  # the gradient of output 0 of a 4-output network
+        p = H.cfg2_params(seed=95, R=12, out_dim=4)
+    else:  # the sweep's wider networks: widths 48 / 64, 22 / 30 Fourier rows
+        c = 48 if shape == "w48" else 64
+        p = synth.random_params(R=12, F=16, m=synth.fourier_rows_for_width(c), layers=4, width=c,
+                                act=synth.ACT_SNAKEALT, seed=96 + c, grid_std=0.5, bias_std=0.2)
     net, q = _net16(S, p)
     on = oracle.OracleNet(q)
     n = 20000
@@ -187,6 +193,7 @@ def test_mma_adjoint_gradient_matches_oracle(srn, shape):
     assert S.srn_sync_status(net.ctx)[0] == S.SRN_OK
     r2, g2 = oracle.net_input_grad(on, pts, t)
     err_rho = H.rel_density_err(rho.cpu().numpy(), r2).max()
+    print(f"fp16 adjoint {shape}: max rel density error {err_rho:.2e}")
     assert err_rho <= H.TOL_FP16_RHO, err_rho
     B = oracle.error_bounds(on, pts, oracle.PREC_FP16, t)[1]
     diff = np.abs(g.cpu().numpy().astype(np.float64) - g2)
@@ -197,16 +204,22 @@ def test_mma_adjoint_gradient_matches_oracle(srn, shape):
 
 
 def test_mma_adjoint_limits(srn):
-    """Five layers (three stashed derivative blocks) or a 4-output network:
-    the tensor-core adjoint refuses with SRN_ERR_UNSUPPORTED."""
+    """Five layers (three stashed derivative blocks, beyond the TMEM layout)
+    or a direct time input: the tensor-core adjoint refuses with
+    SRN_ERR_UNSUPPORTED, for shading and for srn_density_grad."""
     import torch
     S = srn
     out = torch.zeros((1, 1, 8, 8, 4), device="cuda")
     for p in (synth.random_params(R=8, F=16, m=14, layers=5, width=32, act=synth.ACT_SNAKEALT, seed=29),
-              H.cfg2_params(seed=30, R=8, out_dim=4)):
+              synth.random_params(R=8, F=16, m=14, layers=4, width=32, act=synth.ACT_SNAKEALT, seed=31,
+                                  n_keyframes=2, key_times=[0.0, 1.0], time_input=1)):
         net, _ = _net16(S, p)
         with pytest.raises(S.SrnError) as e:
             S.srn_render(net.ctx, synth.orbit_cameras(1), synth.tf_preset(4), S.render_desc(8, 8, 0.01, 2.0, 1), out)
+        assert e.value.status == S.SRN_ERR_UNSUPPORTED
+        with pytest.raises(S.SrnError) as e:
+            S.srn_density_grad(net.ctx, torch.zeros((4, 3), device="cuda"), torch.zeros(4, device="cuda"),
+                               torch.zeros((4, 3), device="cuda"))
         assert e.value.status == S.SRN_ERR_UNSUPPORTED
 
 

@@ -93,10 +93,38 @@ def test_wide_eval_parity(srn, width, layers):
     assert np.all(np.abs(g - ref_g) <= B), (np.abs(g - ref_g) / B).max()
 
 
+@pytest.mark.parametrize("width", [48, 64])
+@pytest.mark.parametrize("shading", [1, 2, 3])
+def test_wide_shading_parity(srn, width, shading):
+    """Section 5 shading on the wider networks, tensor-core path: adjoint
+    (backward MMAs with the wider accumulator and derivative stash), central
+    differences and the 4-output head, against the oracle within the FP16
+    image bound plus the derived shading allowance."""
+    S = srn
+    p = synth.random_params(R=12, F=16, m=M_FOR[width], layers=4 if shading == 1 else 3, width=width,
+                            out_dim=4 if shading == 3 else 1, act=synth.ACT_SNAKEALT, seed=410 + width + shading,
+                            grid_std=0.5, bias_std=0.2)
+    q = synth.to_half_exact(p)
+    net = S.Network(q, precision=S.SRN_PREC_FP16)
+    tf = synth.tf_preset(8)
+    cams = synth.orbit_cameras(1)
+    import torch
+    out = torch.full((1, 1, 16, 24, 4), -1.0, device="cuda")  # small: the adjoint bound costs ~400 passes a sample
+    S.srn_render(net.ctx, cams, tf, S.render_desc(24, 16, 1 / 48, 2.0, shading, 1 / 64), out)
+    torch.cuda.synchronize()
+    assert S.srn_sync_status(net.ctx)[0] == 0
+    ref, bound = oracle.render_shade_bound(oracle.OracleNet(q), cams, H.oracle_tf(tf), 24, 16, 1 / 48, 2.0, shading,
+                                           oracle.PREC_FP16, fd_h=1 / 64)
+    r = H.compare_images(out.cpu().numpy()[0], ref[0], None, H.shaded_tol(H.TOL_FP16_IMG, bound[0]), 2.0)
+    print(f"width {width} shading {shading}: max error {r['max_strict']:.2e}, worst error / bound "
+          f"{r['worst_ratio']:.2f}")
+    assert r["ok"], r
+
+
 def test_wide_unsupported_shapes_fail_loudly(srn):
-    """The tensor-core variants of width 48 / 64 cover SnakeAlt, no shading,
-    16 latent channels and the widened Fourier count; other shapes and the
-    fused fit (width 32 only) return SRN_ERR_UNSUPPORTED."""
+    """The tensor-core variants of width 48 / 64 cover SnakeAlt, 16 latent
+    channels and the widened Fourier count, every shading mode; other shapes
+    and the fused fit (width 32 only) return SRN_ERR_UNSUPPORTED."""
     import torch
     S = srn
     p = synth.to_half_exact(synth.random_params(R=8, F=16, m=22, layers=3, width=48, act=synth.ACT_SINE, seed=402))
@@ -105,11 +133,10 @@ def test_wide_unsupported_shapes_fail_loudly(srn):
     with pytest.raises(S.SrnError) as e:
         S.srn_render(net.ctx, synth.orbit_cameras(1), synth.tf_preset(4), S.render_desc(8, 8, 0.01), out)
     assert e.value.status == S.SRN_ERR_UNSUPPORTED
-    p = _params(64, 3, 403, R=8)
+    p = _params(64, 5, 403, R=8)  # five layers: beyond the adjoint's TMEM layout
     net = S.Network(synth.to_half_exact(p), precision=S.SRN_PREC_FP16)
     with pytest.raises(S.SrnError) as e:
-        S.srn_render(net.ctx, synth.orbit_cameras(1), synth.tf_preset(4), S.render_desc(8, 8, 0.01, 0.99, 2, 0.01),
-                     out)
+        S.srn_render(net.ctx, synth.orbit_cameras(1), synth.tf_preset(4), S.render_desc(8, 8, 0.01, 0.99, 1), out)
     assert e.value.status == S.SRN_ERR_UNSUPPORTED
     fit = S.Network(p, max_fit_points=1024, adam=True)
     vol = torch.zeros((16, 16, 16), device="cuda")

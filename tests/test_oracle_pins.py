@@ -191,24 +191,30 @@ def test_adaptive_counts_proportional_to_the_error():
 # ---------------------------------------------------------------- tolerance bounds
 def test_error_bounds_of_a_linear_layer():
     """One linear layer rho = W v + b: with only the input term of the
-    precision model (|dv_j| <= in_abs, or <= in_rel |v_j|) the bound is
-    lambda sqrt(sum_j (W_j dv_j)^2), lambda = 6 (Hoeffding at 3e-8); the
-    bounds are linear in the precision model."""
+    precision model (|dv_j| <= in_abs, <= in_rel |v_j|, or for the latent
+    inputs <= lat_w sum_k w_k |G_k|) the bound is lambda sqrt(sum_j (W_j
+    dv_j)^2), lambda = 6 (Hoeffding at 3e-8); the bounds are linear in the
+    precision model."""
     p = synth.random_params(R=4, F=4, m=3, layers=1, width=8, act=synth.ACT_SINE, seed=611)
     on = oracle.OracleNet(p)
     pts = np.random.default_rng(612).uniform(0, 1, (5, 3))
     W = np.asarray(p["weights"][0], np.float64)[0]
     d = 1e-4
-    B, _ = oracle.error_bounds(on, pts, (0, d, 0, 0, 0, 0, 0, 0, 0), grad=False)
+    B, _ = oracle.error_bounds(on, pts, (0, d, 0, 0, 0, 0, 0, 0, 0, 0), grad=False)
     np.testing.assert_allclose(B[:, 0], 6 * d * np.linalg.norm(W), rtol=1e-12)
     # in_rel: the input vector [p, sin(Fp), cos(Fp), z] from the oracle's own Fourier matrix and latent grid
-    B2, _ = oracle.error_bounds(on, pts, (d, 0, 0, 0, 0, 0, 0, 0, 0), grad=False)
+    B2, _ = oracle.error_bounds(on, pts, (d, 0, 0, 0, 0, 0, 0, 0, 0, 0), grad=False)
     F = np.asarray(p["fourier"], np.float64)
     for k, x in enumerate(pts):
         e = F @ x
         z = oracle.trilinear(np.asarray(p["grid"], np.float64)[0], x)
         v = np.concatenate([x, np.sin(e), np.cos(e), z])
         assert abs(B2[k, 0] - 6 * d * np.linalg.norm(W * v)) < 1e-12
+    # lat_w: the FP16-rounded trilinear weights, 2^-11 of sum_k w_k |G_kc| per latent input
+    B3, _ = oracle.error_bounds(on, pts, (0, 0, 0, 0, 0, 0, 0, 0, 0, d), grad=False)
+    for k, x in enumerate(pts):
+        za = oracle.trilinear(np.abs(np.asarray(p["grid"], np.float64)[0]), x)
+        assert abs(B3[k, 0] - 6 * d * np.linalg.norm(W[3 + 2 * 3:] * za)) < 1e-12
     q = synth.random_params(R=4, F=4, m=3, layers=3, width=8, act=synth.ACT_SNAKEALT, seed=613)
     oq = oracle.OracleNet(q)
     prec = np.array(oracle.PREC_FP16)
