@@ -238,6 +238,16 @@ def fit_cfg3(vol, pts, steps=FIT_STEPS, seed=0):
            "steps_per_s_single_calls": single_sps, "graph_equals_single_calls": same,
            "final_loss": float(loss.item()), "density_psnr_db": density_psnr_network(net, vol, pts),
            "lowpass_grid": M, "lowpass_density_psnr_db": lp_psnr, "status": st}
+    pk = peaks()
+    tf_ach = sps * FIT_POINTS * FIT_FLOP_PER_POINT / 1e12
+    gb_ach = sps * FIT_POINTS * FIT_GATHER_BYTES_PER_POINT / 1e9
+    res["roofline"] = {"bound": "latency", "tensor": {"achieved": tf_ach, "peak": pk.get("bf16_tflops"),
+                                                      "unit": "TFLOP/s", "flop_per_point": FIT_FLOP_PER_POINT,
+                                                      "frac": tf_ach / pk["bf16_tflops"] if pk.get("bf16_tflops") else None},
+                       "gather": {"achieved": gb_ach, "unit": "GB/s", "bytes_per_point": FIT_GATHER_BYTES_PER_POINT,
+                                  "hbm_frac": gb_ach / pk["hbm_gbs"] if pk.get("hbm_gbs") else None},
+                       "note": "eight short dependent kernels per step (2-15 us each): launch and tail latency, "
+                               "not a unit's throughput, set the rate"}
     net.close()
     return res
 
@@ -688,6 +698,16 @@ SMS, MUFU_PER_SM_CLK, FP32_PER_SM_CLK, MAX_SM_GHZ = 152, 16, 128, 2.07
 # the dense DVR, from the ncu captures summarised in profiles/ (None when the
 # kernel changed after the capture).
 RENDER_DRAM_BYTES = 1136384
+# Warp instructions per network sample of the render kernel from the same
+# capture (smsp__inst_executed.sum 1.0246e10 over 2.088e8 samples).
+WARP_INST_PER_SAMPLE = 1.0246e10 / 2.08797e8
+# Algorithmic work of one plain-workload fit step per point: forward 2 (35 x 32
+# + 32) FLOP, weight gradients the same again, the backward through the
+# output layer (2 x 32), the latent-input gradient (2 x 32 x 8) and its
+# trilinear scatter (8 corners x 8 channels x 2); gathers: the volume's eight
+# 4-byte corners.
+FIT_FLOP_PER_POINT = 2 * (35 * 32 + 32) * 2 + 2 * 32 + 2 * 32 * 8 + 8 * 8 * 2
+FIT_GATHER_BYTES_PER_POINT = 32
 DENSE_DRAM_BYTES = 67166208 + 9174016
 # L1 load bandwidth of one SM (bytes per clock) for the gather roofline of
 # dense DVR (unit count; the peak is derived, not measured).
@@ -730,6 +750,10 @@ def roofline(res):
                                                                     "mma_flop": MMA_FLOP_PER_SAMPLE},
             "tensor": {"achieved": achieved_tc, "peak": peak_tc, "unit": "TFLOP/s", "frac": achieved_tc / peak_tc,
                        "peak_source": "MEASURED_PEAKS.json bf16_tflops (fp16 dense rate equal)"},
+            "issue": {"achieved": sps * WARP_INST_PER_SAMPLE / 1e12, "peak": SMS * 4 * MAX_SM_GHZ * 1e9 / 1e12,
+                      "unit": "T warp instructions/s", "frac": sps * WARP_INST_PER_SAMPLE / (SMS * 4 * MAX_SM_GHZ * 1e9),
+                      "per_sample": WARP_INST_PER_SAMPLE,
+                      "note": "warp instructions per sample from the ncu capture; 4 issue slots per SM per clock"},
             "peak_source": "unit counts x max SM clock; probe measured 15.1 sin/clk/SM"}
 
 
