@@ -709,6 +709,7 @@ WARP_INST_PER_SAMPLE = 1.0246e10 / 2.08797e8
 FIT_FLOP_PER_POINT = 2 * (35 * 32 + 32) * 2 + 2 * 32 + 2 * 32 * 8 + 8 * 8 * 2
 FIT_GATHER_BYTES_PER_POINT = 32
 DENSE_DRAM_BYTES = 67166208 + 9174016
+DENSE_L1_WAVEFRONT_PCT = 88.3  # l1tex__data_pipe_lsu_wavefronts, % of peak, same capture
 # L1 load bandwidth of one SM (bytes per clock) for the gather roofline of
 # dense DVR (unit count; the peak is derived, not measured).
 L1_BYTES_PER_SM_CLK = 128
@@ -727,6 +728,9 @@ def dense_roofline(samples, ms_total, frames, vol_bytes):
     return {"bound": "l1", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": DENSE_DRAM_BYTES, "kernel": "dvr_dense_kernel", "per_sample_bytes": DENSE_GATHER_BYTES,
             "peak_source": "152 SMs x 128 B/clk x 2.07 GHz (unit counts)",
+            "l1_data_wavefronts_pct": DENSE_L1_WAVEFRONT_PCT,
+            "l1_note": "ncu: the L1 data pipe is 88 % busy with the wavefronts of the scattered 4-byte corner "
+                       "gathers (several cache lines per warp load), which is what bounds the kernel",
             "hbm_floor": {"achieved": vol_gbs, "peak": hbm, "unit": "GB/s",
                           "frac": vol_gbs / hbm if hbm else None,
                           "note": "the volume read once per frame, against MEASURED_PEAKS.json hbm_gbs"}}

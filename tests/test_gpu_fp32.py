@@ -139,6 +139,30 @@ def test_dvr_dense_parity(srn, shading):
     assert abs(int(ns.item()) - ns_ref) <= 0.001 * ns_ref
 
 
+@pytest.mark.parametrize("dims", [(40, 29, 23), (37, 29, 23)])
+@pytest.mark.parametrize("shading", [0, 2])
+def test_dvr_dense_anisotropic(srn, dims, shading):
+    """Anisotropic volumes: nx a multiple of 4 (rows read by aligned 16-byte
+    loads) and nx = 37 (rows read by 4-byte loads); per-axis FD steps."""
+    import torch
+    S = srn
+    nx, ny, nz = dims
+    vol = np.ascontiguousarray(synth.blobs_volume(40, 6, seed=9).numpy()[:nz, :ny, :nx])
+    tf = synth.tf_preset(4)
+    cams = synth.orbit_cameras(3)
+    out = torch.zeros((3, 36, 44, 4), device="cuda")
+    S.srn_dvr_dense(torch.tensor(vol, device="cuda"), cams, tf, S.render_desc(44, 36, 1 / 96, 0.99, shading), out)
+    torch.cuda.synchronize()
+    ref, mg, _ = oracle.dvr_dense(vol, cams, H.oracle_tf(tf), 44, 36, 1 / 96, 0.99, shading=shading, want_margin=True)
+    tol = H.TOL_FP32_IMG
+    if shading:
+        _, bound = oracle.dvr_dense_shade_bound(vol, cams, H.oracle_tf(tf), 44, 36, 1 / 96, 0.99,
+                                                H.dense_sample_error(vol))
+        tol = H.shaded_tol(H.TOL_FP32_IMG, bound)
+    r = H.compare_images(out.cpu().numpy(), ref, mg, tol, 0.99)
+    assert r["ok"], r
+
+
 def test_dvr_dense_full_size_sampled(srn):
     """Config 2 dense volume size (256^3) at 1024 x 1024: sampled pixels."""
     import torch
