@@ -436,6 +436,22 @@ def run_ours(args, rank, world):
           "psnr_vs_dense_db": _psnr_imgs(srn, out[0], dense), "density_psnr_db": density_psnr_network(n8, vol, pts),
           "grid_bytes": n8.grid_q.numel()}
     n8.close()
+    # the FP32 CUDA-core path on the same fitted network and frame, and how far
+    # the FP16 tensor-core image is from it
+    n32 = srn.Network(net.unpack(), precision=srn.SRN_PREC_FP32)
+    c32 = torch.zeros(1, dtype=torch.int64, device=dev)
+    ms32 = _time_frames(lambda: srn.srn_render(n32.ctx, cams[:1], tf, desc, out, samples=c32), n=3)
+    c32.zero_()
+    srn.srn_render(n32.ctx, cams[:1], tf, desc, out, samples=c32)
+    img32 = out.clone()
+    srn.srn_render(net.ctx, cams[:1], tf, desc, out)
+    torch.cuda.synchronize()
+    fp32_path = {"ms_per_frame": ms32, "samples_per_s": int(c32.item()) / (ms32 / 1e3),
+                 "psnr_vs_dense_db": _psnr_imgs(srn, img32[0], dense),
+                 "fp16_vs_fp32_max_abs": float((out - img32).abs().max().item()),
+                 "fp32_over_fp16_time": ms32 / fitted_frames["ms_per_frame"]}
+    del img32
+    n32.close()
     cfg3 = fit_cfg3(vol, pts, steps=args.fit_steps) if fit_info.get("steps") else None
     del pts
 
@@ -461,7 +477,7 @@ def run_ours(args, rank, world):
                    "psnr_lowpass_grid_vs_dense_db": float(np.mean(lp_psnrs)), "lowpass_grid": M,
                    "ssim_fvsrn_vs_dense": float(np.mean(ssims)), "ssim_lowpass_grid_vs_dense": float(np.mean(lp_ssims)),
                    "density_psnr_fvsrn_db": fvsrn_dpsnr, "density_psnr_lowpass_db": lp_dpsnr, "u8_grid": u8,
-                   "fit_render_network": fit_info,
+                   "fp32_path": fp32_path, "fit_render_network": fit_info,
                    "fit_steps_per_s": cfg3["steps_per_s"] if cfg3 else None, "fit_cfg3": cfg3,
                    "parallelism": f"replicas x{world} (views split across ranks)"},
         "e2e": e2e, "gpu_launches": args.steps,

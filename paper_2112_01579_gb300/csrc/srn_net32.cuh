@@ -67,15 +67,20 @@ __device__ void load_net(float* sm, const Layout& L, const NetDev& n) {
   __syncthreads();
 }
 
+// h += a * row, two outputs per packed FP32x2 FMA (each lane a correctly
+// rounded FMA, so the same bits as scalar fmaf).
 template <int C>
 __device__ __forceinline__ void axpy(float (&h)[C], const float* __restrict__ row, float a) {
+  const float2 aa = make_float2(a, a);
 #pragma unroll
   for (int o = 0; o < C; o += 4) {
-    float4 w = *reinterpret_cast<const float4*>(row + o);
-    h[o] = fmaf(w.x, a, h[o]);
-    h[o + 1] = fmaf(w.y, a, h[o + 1]);
-    h[o + 2] = fmaf(w.z, a, h[o + 2]);
-    h[o + 3] = fmaf(w.w, a, h[o + 3]);
+    const float4 w = *reinterpret_cast<const float4*>(row + o);
+    const float2 r0 = __ffma2_rn(make_float2(w.x, w.y), aa, make_float2(h[o], h[o + 1]));
+    const float2 r1 = __ffma2_rn(make_float2(w.z, w.w), aa, make_float2(h[o + 2], h[o + 3]));
+    h[o] = r0.x;
+    h[o + 1] = r0.y;
+    h[o + 2] = r1.x;
+    h[o + 3] = r1.y;
   }
 }
 
