@@ -195,6 +195,7 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
   const float inv_n = 1.0f / (float)a.n;
   // delta rows of the weight-gradient MMA are staged times 2^dexp >= n
   const int dexp = a.n > 1 ? 32 - __clz(a.n - 1) : 0;
+  const float dscale = __int_as_float((127 + dexp) << 23), dunscale = __int_as_float((127 - dexp) << 23);
   const int nchunks = (a.n + 127) / 128;
   const int wg_global = blockIdx.x * kFitWGS + wg, n_wg = gridDim.x * kFitWGS;
   float loss_acc = 0.0f;
@@ -359,7 +360,7 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
       uint32_t hi[4], lo[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        split_h2(ldexpf(delta[8 * cg + 2 * e], dexp), ldexpf(delta[8 * cg + 2 * e + 1], dexp), hi[e], lo[e]);
+        split_h2(delta[8 * cg + 2 * e] * dscale, delta[8 * cg + 2 * e + 1] * dscale, hi[e], lo[e]);
       }
       *reinterpret_cast<uint4*>(Bt + sw_off(row, cg)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
       *reinterpret_cast<uint4*>(Bt + sw_off(row, 4 + cg)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
@@ -454,7 +455,7 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
       else if (f < D0) src = f;
 #pragma unroll
       for (int o = 0; o < 32; ++o) {
-        const float g = ldexpf(h0[o] + ex[f * 33 + o], -dexp);  // the delta rows carried 2^dexp
+        const float g = (h0[o] + ex[f * 33 + o]) * dunscale;  // the delta rows carried 2^dexp
         if (src >= 0) prow[o * D0 + src] = g;
         if (f == D0) prow[nW + o] = g;  // the constant-1 column: bias of layer 0
       }
