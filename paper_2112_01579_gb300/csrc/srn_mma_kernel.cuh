@@ -538,6 +538,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
   // the FP16 latent grid holds G 2^-gexp: the latent columns' layer-0 weights
   // are staged times 2^gexp (exact), the 8-bit grid's lo / step times 2^-gexp
   const int gexp = net.grid_exp ? *net.grid_exp : 0;
+  const float gscale = __int_as_float((127 + gexp) << 23);  // 2^gexp, gexp <= 113
 
   // ---- stage parameters as FP16 B tiles (row o = output neuron, K-major,
   // 128B-swizzled K-atoms).  Layer 0: columns in the tile's input order, FP32
@@ -987,7 +988,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
               }
             }
             float3 gl = latent_grad_h<F>(net.grid_h, net.R, rl, qs, gv + 2 * M + 3);
-            gl = make_float3(ldexpf(gl.x, gexp), ldexpf(gl.y, gexp), ldexpf(gl.z, gexp));  // grid_h = G 2^-gexp
+            gl = make_float3(gl.x * gscale, gl.y * gscale, gl.z * gscale);  // grid_h = G 2^-gexp
             gadj = make_float3(gp.x + gl.x, gp.y + gl.y, gp.z + gl.z);
           }
         }
