@@ -5,6 +5,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -306,6 +307,11 @@ srn_status srn_render(srn_ctx* ctx, const srn_camera* cams, int n_views, const f
   BatchDev b;
   srn_status st = fill_batch(b, cams, n_views, times, n_times, tf, desc, rgba_dev, samples_dev, true);
   if (st) return st;
+  // test hook of the timeout path (host-side injection): with SRN_TEST_STALL=1
+  // in the environment the tensor-core render issues no MMA, so its bounded
+  // mbarrier waits run out (~1 s) and the call reports SRN_ERR_TIMEOUT
+  const char* stall = getenv("SRN_TEST_STALL");
+  b.stall_test = stall && stall[0] == '1' && stall[1] == 0;
   if (desc->shading == SRN_SHADE_HEAD && ctx->cfg.out_dim != 4)
     return fail(SRN_ERR_INVALID_ARG, "head shading needs out_dim 4");
   st = use_device(ctx);

@@ -63,6 +63,7 @@ struct BatchDev {
   TFDev tf;
   float* out;                     // [n_times][n_views][H][W][4]
   unsigned long long* samples;    // nullable
+  int stall_test;                 // test of the timeout path: the tensor-core render issues no MMA
 };
 
 // Dense volume source for the plain DVR.

@@ -810,7 +810,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
     tc_fence_before();
     const bool any = bar_red_or(bar_id, 128, active && !failed);
     if (!any || misc[4 + wg]) break;
-    if (row == 0) {
+    if (row == 0 && !b.stall_test) {  // stall_test: no MMA, no commit, nothing in flight
       tc_fence_after();
 #pragma unroll
       for (int kk = 0; kk < K0 / 16; ++kk) {

@@ -374,3 +374,32 @@ def test_mma_eval_trained_network(srn):
     err = H.rel_density_err(got, ref)
     print(f"fp16 eval trained: max rel density error {err.max():.2e}, mean {err.mean():.2e}")
     assert err.max() <= H.TOL_FP16_RHO
+
+
+@pytest.mark.parametrize("which", ["cfg1", "cfg2"])
+def test_mma_bounded_wait_reports_timeout(srn, monkeypatch, which):
+    """The timeout path without a fault: with SRN_TEST_STALL=1 the render
+    issues no MMA (nothing in flight), every warpgroup's bounded mbarrier
+    wait runs out after about a second, the kernel frees its TMEM and returns,
+    and the status reads SRN_ERR_TIMEOUT; the context then renders normally."""
+    import time
+    import torch
+    S = srn
+    net, q = _net16(S, H.cfg1_params(seed=23) if which == "cfg1" else H.cfg2_params(seed=24, R=16))
+    tf = synth.tf_preset(4)
+    cams = synth.orbit_cameras(1)
+    out = torch.full((1, 1, 16, 16, 4), -1.0, device="cuda")
+    torch.cuda.synchronize()
+    monkeypatch.setenv("SRN_TEST_STALL", "1")
+    t0 = time.time()
+    S.srn_render(net.ctx, cams, tf, S.render_desc(16, 16, 1 / 64, 0.99), out)
+    torch.cuda.synchronize()
+    dt = time.time() - t0
+    monkeypatch.delenv("SRN_TEST_STALL")
+    st, msg = S.srn_sync_status(net.ctx)
+    assert st == S.SRN_ERR_TIMEOUT, (st, msg)
+    assert 0.2 < dt < 60, dt
+    got, _ = _render(S, net, cams, tf, 16, 16, 1 / 64, 2.0)
+    ref, _, _ = oracle.render(oracle.OracleNet(q), cams, H.oracle_tf(tf), 16, 16, 1 / 64, 2.0)
+    assert np.abs(got - ref).max() <= H.TOL_FP16_IMG
+    net.close()
