@@ -392,9 +392,11 @@ srn_status srn_load(srn_ctx* ctx, const char* path, int* step_out);
  * SRN_OK, SRN_ERR_NONFINITE, SRN_ERR_TIMEOUT or SRN_ERR_INTERNAL.
  * SRN_ERR_TIMEOUT: a bounded wait of the tensor-core kernels (about one
  * second of clock) ran out; the kernel left its loop, freed its tensor
- * memory and returned, and the context stays usable.  For testing that path,
- * srn_render reads the environment variable SRN_TEST_STALL at each call: when
- * it is "1" the tensor-core render issues no MMA, so every wait runs out. */
+ * memory and returned, and the context stays usable (a fit step that timed
+ * out leaves parameters and Adam moments as they were).  For testing that
+ * path, srn_render and srn_fit_step(s) read the environment variable
+ * SRN_TEST_STALL at each call: when it is "1" the tensor-core render and the
+ * tensor-core fit point kernel issue no MMA, so every wait runs out. */
 srn_status srn_sync_status(srn_ctx* ctx, void* stream);
 
 /* Mean squared error over the RGB channels of n RGBA float32 pixels, the

@@ -58,6 +58,15 @@ srn_status cuda_fail(cudaError_t e, const char* what) {
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
+// Host-side switch for testing the timeout path: with SRN_TEST_STALL=1 in the
+// environment, srn_render and the fit's tensor-core point kernel issue no MMA,
+// so their bounded mbarrier waits run out (~1 s of clock) and report
+// SRN_ERR_TIMEOUT; a fit step then leaves the parameters as they are.
+bool test_stall() {
+  const char* v = getenv("SRN_TEST_STALL");
+  return v && v[0] == '1' && v[1] == 0;
+}
+
 // (2n + 1) * Q < 2^64 for every adaptive distribution over res^3 voxels
 // (Q <= 65535 res^3), so the stratum midpoints stay exact in 64 bits.
 bool adaptive_fits(long long n, int res) {
@@ -307,11 +316,7 @@ srn_status srn_render(srn_ctx* ctx, const srn_camera* cams, int n_views, const f
   BatchDev b;
   srn_status st = fill_batch(b, cams, n_views, times, n_times, tf, desc, rgba_dev, samples_dev, true);
   if (st) return st;
-  // test hook of the timeout path (host-side injection): with SRN_TEST_STALL=1
-  // in the environment the tensor-core render issues no MMA, so its bounded
-  // mbarrier waits run out (~1 s) and the call reports SRN_ERR_TIMEOUT
-  const char* stall = getenv("SRN_TEST_STALL");
-  b.stall_test = stall && stall[0] == '1' && stall[1] == 0;
+  b.stall_test = test_stall();
   if (desc->shading == SRN_SHADE_HEAD && ctx->cfg.out_dim != 4)
     return fail(SRN_ERR_INVALID_ARG, "head shading needs out_dim 4");
   st = use_device(ctx);
@@ -452,6 +457,7 @@ srn_status make_fit_args(srn_ctx* ctx, const float* volume_dev, const int dims[3
   a.cdf = ctx->cdf_active ? ctx->cdf : nullptr;
   a.cdf_res = ctx->cdf_res;
   a.step_ptr = nullptr;
+  a.stall_test = test_stall();
   *out = a;
   return SRN_OK;
 }
@@ -474,7 +480,7 @@ bool same_graph_args(const FitArgs& x, const FitArgs& y) {
          memcmp(&x.grad_weight, &y.grad_weight, sizeof(float)) == 0 &&
          memcmp(&x.grad_scale, &y.grad_scale, sizeof(float)) == 0 && x.loss == y.loss && x.grid_h == y.grid_h &&
          x.weights_h == y.weights_h && x.adam_m == y.adam_m && x.adam_v == y.adam_v && x.grid == y.grid &&
-         x.weights == y.weights && x.biases == y.biases && x.cdf == y.cdf && x.cdf_res == y.cdf_res;
+         x.weights == y.weights && x.biases == y.biases && x.cdf == y.cdf && x.cdf_res == y.cdf_res && x.stall_test == y.stall_test;
 }
 
 // Captures one step (fit step, whose Adam kernel advances the step index,

@@ -63,6 +63,7 @@ struct PointArgs {
   float* part;
   int n_entries;
   int dstride;  // stride of the staged input rows
+  int stall_test;  // timeout-path test (tensor-core point kernel only)
 };
 
 // Adds the contribution of the CTA's points to the gradient entries of one
@@ -766,7 +767,9 @@ __device__ __forceinline__ void adam_update(float* __restrict__ grid, float* __r
 
 // Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias correction at step + 1) over
 // [grid | weights | biases]; refreshes the FP16 copies.  Skipped entirely
-// when the step produced a non-finite loss or gradient.  With the step index
+// when the step produced a non-finite loss or gradient (flag bit 0,
+// SRN_ERR_NONFINITE) or a bounded wait of the point kernel gave up (bit 1,
+// SRN_ERR_TIMEOUT).  With the step index
 // in device memory (step_ptr), the last block to finish advances it by one
 // for the next step (flag[1] counts finished blocks and is reset by that block).
 __global__ void adam_kernel(float* __restrict__ grid, float* __restrict__ W, float* __restrict__ b,
@@ -776,8 +779,10 @@ __global__ void adam_kernel(float* __restrict__ grid, float* __restrict__ W, flo
                             __half* __restrict__ grid_h, __half* __restrict__ W_h,
                             const int* __restrict__ grid_exp) {
   const int step = step_ptr ? *step_ptr : step_arg;
-  if (*flag) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(status, (unsigned int)SRN_ERR_NONFINITE);
+  const unsigned int f = *flag;
+  if (f) {
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+      atomicExch(status, (unsigned int)((f & 2u) ? SRN_ERR_TIMEOUT : SRN_ERR_NONFINITE));
   } else {
     adam_update(grid, W, b, g, m, v, ng, nW, nb, lr_grid, lr_net, step, grid_h, W_h, grid_exp);
   }
@@ -831,8 +836,8 @@ cudaError_t run_backward(FitScratch& s, const NetDev& net, PointArgs pa, float* 
     // tensor-core point kernel: one partial row per warpgroup
     const int rows = fit_mma_rows_per_cta();
     const int grid = std::max(1, std::min({sm_count(), s.max_cta / rows, (n + 128 * rows - 1) / (128 * rows)}));
-    PointArgsMma ma{n,      pa.seed, pa.step, pa.time, pa.vol, pa.cdf,   pa.cdf_res,
-                    pa.step_ptr, s.pts,  s.dz,    s.key,  s.idx,  s.part};
+    PointArgsMma ma{n,           pa.seed, pa.step, pa.time, pa.vol, pa.cdf, pa.cdf_res, pa.step_ptr,
+                    s.pts,       s.dz,    s.key,   s.idx,  s.part, s.flag, pa.stall_test};
     e = launch_fit_mma(net, ma, grid, mma_status, st);
     if (e != cudaSuccess) return e;
     n_cta = grid * rows;
@@ -987,6 +992,11 @@ cudaError_t fit_scratch_alloc(FitScratch& s, const NetDev& net, int max_points) 
   alloc((void**)&s.grads, sizeof(float) * (s.n_grid + s.n_entries));
   alloc((void**)&s.flag, sizeof(unsigned int) * 4);
   if (e == cudaSuccess) e = cudaMemset(s.flag, 0, sizeof(unsigned int) * 4);  // flag[1]: Adam's block counter
+  // cell keys and point indices start valid (cell 0, point 0) and are only ever
+  // overwritten with valid ones, so a step whose point kernel gave up (bounded
+  // wait, SRN_ERR_TIMEOUT) still sorts and gathers inside the buffers
+  for (unsigned int* q : {s.key, s.key_alt, s.idx, s.idx_alt})
+    if (e == cudaSuccess) e = cudaMemset(q, 0, sizeof(unsigned int) * n);
   if ((size_t)max_points >= 32 * s.n_cells) alloc((void**)&s.cell_part, sizeof(float) * s.n_cells * 8 * net.F);
   return e;
 }
@@ -1032,6 +1042,7 @@ cudaError_t launch_fit_step(FitScratch& s, const NetDev& net, const FitArgs& a, 
   pa.cdf = a.cdf;
   pa.cdf_res = a.cdf_res;
   pa.step_ptr = a.step_ptr;
+  pa.stall_test = a.stall_test;
   const size_t ng = s.n_grid, nW = net_weight_count(net), nb = net_bias_count(net);
   cudaError_t e = run_backward(s, net, pa, s.grads, s.grads + ng, s.grads + ng + nW, a.loss, st, a.status);
   if (e != cudaSuccess) return e;

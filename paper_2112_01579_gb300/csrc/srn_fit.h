@@ -49,6 +49,7 @@ struct FitArgs {
   int cdf_res;
   int* step_ptr;  // when not null, the step index is read from here (CUDA-graph replay), not `step`, and
                   // the step's last kernel (Adam) advances it by one
+  int stall_test;  // test of the timeout path: the tensor-core point kernel issues no MMA
 };
 
 bool fit_supported(const NetDev& net);
@@ -80,6 +81,8 @@ struct PointArgsMma {
   unsigned int* key;
   unsigned int* idx;
   float* part;
+  unsigned int* flag;  // bit 1: a bounded wait gave up (the step's Adam then skips the update)
+  int stall_test;      // test of the timeout path: issue no MMA, so every wait runs out
 };
 bool fit_mma_supported(const NetDev& n);
 int fit_mma_rows_per_cta();

@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
     tc_fence_before();
     bar_sync(bar_id, 128);
     if (misc[4 + wg]) break;
-    if (row == 0) {
+    if (row == 0 && !a.stall_test) {  // stall_test: no MMA, no commit, nothing in flight
       tc_fence_after();
       // K blocks [v hi | v lo | v hi] x [W hi | W hi | W lo]: the third A block is the first
 #pragma unroll
@@ -478,7 +478,10 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
     }
   }
   if (failed || misc[4 + wg]) {
-    if (row == 0) atomicExch(status, (unsigned int)SRN_ERR_TIMEOUT);
+    if (row == 0) {
+      atomicExch(status, (unsigned int)SRN_ERR_TIMEOUT);
+      atomicOr(a.flag, 2u);  // the step's Adam leaves the parameters as they are
+    }
   }
   tc_fence_before();
   __syncthreads();

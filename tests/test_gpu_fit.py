@@ -328,3 +328,39 @@ def test_fit_nonfinite_leaves_parameters(srn):
     assert torch.equal(before[0], net.grid) and torch.equal(before[1], net.weights)
     assert torch.equal(before[2], net.biases)
     assert S.srn_sync_status(net.ctx)[0] == 0  # the status word is cleared once read
+
+
+def test_fit_bounded_wait_reports_timeout(srn, monkeypatch):
+    """The fit's timeout path without a fault: with SRN_TEST_STALL=1 the
+    tensor-core point kernel issues no MMA, its bounded waits run out, the
+    step reports SRN_ERR_TIMEOUT and Adam leaves parameters and moments as
+    they were; the next step on the same context equals that step on a fresh
+    context bit for bit."""
+    import torch
+    S = srn
+    vol = torch.tensor(synth.blobs_volume(32, 4, seed=46).numpy(), device="cuda")
+    p = synth.init_params(R=8, F=8, m=12, layers=2, width=32, act=synth.ACT_SINE, seed=47)
+    assert _mma_fit(p)
+    n = 1 << 14
+    net = S.Network(p, max_fit_points=n, adam=True)
+    fresh = S.Network(p, max_fit_points=n, adam=True)
+    state = lambda m: [t.clone() for t in (m.grid, m.weights, m.biases, m.adam_m, m.adam_v)]
+    before = state(net)
+    loss = torch.zeros(1, device="cuda")
+    torch.cuda.synchronize()
+    monkeypatch.setenv("SRN_TEST_STALL", "1")
+    S.srn_fit_step(net.ctx, vol, n, 5, 0, loss)
+    torch.cuda.synchronize()
+    monkeypatch.delenv("SRN_TEST_STALL")
+    st, msg = S.srn_sync_status(net.ctx)
+    assert st == S.SRN_ERR_TIMEOUT, (st, msg)
+    assert all(torch.equal(a, b) for a, b in zip(before, state(net)))
+    loss2 = torch.zeros(1, device="cuda")
+    S.srn_fit_step(net.ctx, vol, n, 5, 0, loss)
+    S.srn_fit_step(fresh.ctx, vol, n, 5, 0, loss2)
+    torch.cuda.synchronize()
+    assert S.srn_sync_status(net.ctx)[0] == 0 and S.srn_sync_status(fresh.ctx)[0] == 0
+    assert torch.equal(loss, loss2) and bool(torch.isfinite(loss).all())
+    assert all(torch.equal(a, b) for a, b in zip(state(net), state(fresh)))
+    net.close()
+    fresh.close()
