@@ -54,7 +54,14 @@ typedef enum srn_status {
 } srn_status;
 
 enum { SRN_ACT_SINE = 0, SRN_ACT_SNAKEALT = 1 };   /* sin(x); Eq. 3: 0.5x + sin^2 x */
-enum { SRN_PREC_FP32 = 0, SRN_PREC_FP16 = 1 };     /* network arithmetic of render / eval */
+/* Network arithmetic of render / eval.  SRN_PREC_BF16 is named for
+ * completeness and not implemented (srn_create returns SRN_ERR_UNSUPPORTED):
+ * BF16 and FP16 run at the same tensor-core rate, BF16's 8-bit mantissa would
+ * need the layer-0 inputs split into hi + lo as well (twice the operand tile
+ * per warpgroup), and its wider range buys nothing the FP16 path lacks (the
+ * latent grid is power-of-two scaled, hidden values beyond 65504 are outside
+ * every FP32-accumulating kernel's tolerance). */
+enum { SRN_PREC_FP32 = 0, SRN_PREC_FP16 = 1, SRN_PREC_BF16 = 2 };
 enum { SRN_SHADE_NONE = 0, SRN_SHADE_ADJOINT = 1, SRN_SHADE_FD = 2, SRN_SHADE_HEAD = 3 };
 
 #define SRN_MAX_KEYFRAMES 32

@@ -84,6 +84,8 @@ srn_status check_config(const srn_config* c) {
   if (c->out_dim != 1 && c->out_dim != 4) return fail(SRN_ERR_INVALID_ARG, "out_dim must be 1 or 4");
   if (c->activation != SRN_ACT_SINE && c->activation != SRN_ACT_SNAKEALT)
     return fail(SRN_ERR_INVALID_ARG, "unknown activation");
+  if (c->precision == SRN_PREC_BF16)
+    return fail(SRN_ERR_UNSUPPORTED, "BF16 network arithmetic is not implemented (FP16 tensor cores or FP32)");
   if (c->precision != SRN_PREC_FP32 && c->precision != SRN_PREC_FP16)
     return fail(SRN_ERR_INVALID_ARG, "unknown precision");
   if (c->n_keyframes < 1 || c->n_keyframes > SRN_MAX_KEYFRAMES)

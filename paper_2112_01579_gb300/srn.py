@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libsrn.so")
 SRN_OK, SRN_ERR_INVALID_ARG, SRN_ERR_UNSUPPORTED, SRN_ERR_CUDA, SRN_ERR_NONFINITE, SRN_ERR_TIMEOUT, \
     SRN_ERR_INTERNAL = range(7)
 SRN_ACT_SINE, SRN_ACT_SNAKEALT = 0, 1
-SRN_PREC_FP32, SRN_PREC_FP16 = 0, 1
+SRN_PREC_FP32, SRN_PREC_FP16, SRN_PREC_BF16 = 0, 1, 2
 SRN_SHADE_NONE, SRN_SHADE_ADJOINT, SRN_SHADE_FD, SRN_SHADE_HEAD = 0, 1, 2, 3
 SRN_MAX_KEYFRAMES, SRN_MAX_TF_POINTS, SRN_MAX_VIEWS, SRN_MAX_TIMES = 32, 32, 64, 64
 

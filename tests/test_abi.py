@@ -50,7 +50,8 @@ def test_create_rejects_bad_configs_without_a_device(lib):
     bad = [("grid_res", 1, lib.SRN_ERR_INVALID_ARG), ("feat", 6, lib.SRN_ERR_INVALID_ARG),
            ("layers", 1, lib.SRN_ERR_INVALID_ARG), ("out_dim", 2, lib.SRN_ERR_INVALID_ARG),
            ("activation", 7, lib.SRN_ERR_INVALID_ARG), ("width", 40, lib.SRN_ERR_UNSUPPORTED),
-           ("n_keyframes", 0, lib.SRN_ERR_INVALID_ARG), ("layers", 12, lib.SRN_ERR_UNSUPPORTED)]
+           ("n_keyframes", 0, lib.SRN_ERR_INVALID_ARG), ("layers", 12, lib.SRN_ERR_UNSUPPORTED),
+           ("precision", lib.SRN_PREC_BF16, lib.SRN_ERR_UNSUPPORTED), ("precision", 3, lib.SRN_ERR_INVALID_ARG)]
     for field, val, st in bad:
         c2 = lib.srn_config.from_buffer_copy(cfg)
         setattr(c2, field, val)
