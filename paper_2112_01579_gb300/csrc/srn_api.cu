@@ -22,7 +22,8 @@ struct srn_ctx {
   srn_params prm;
   int device;
   // device words: [0] status (SRN_OK / SRN_ERR_NONFINITE / ...), [1] graph step
-  // index, [2..3] render work counter, [4] FP16 latent-grid scale exponent
+  // index, [2..3] render work counter, [4] FP16 latent-grid scale exponent,
+  // [5] scratch of its computation (bits of max |grid|)
   unsigned int* status;
   unsigned long long* ray_counter;  // persistent-render work counter (8-byte aligned)
   FitScratch fit;             // scratch of srn_fit_step / srn_backward

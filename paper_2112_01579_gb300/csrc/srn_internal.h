@@ -96,9 +96,10 @@ cudaError_t launch_density_grad_mma(const NetDev& net, const float* pts, long lo
 
 // Conversions and small utilities.
 cudaError_t launch_to_half(const float* src, __half* dst, size_t n, cudaStream_t s);
-// FP16 latent grid with power-of-two scaling: *exp_out = max(0, e - 15) for
-// max |grid| <= 2^e, then dst = fp16(grid 2^-k) (one block reduces, then a
-// grid-stride conversion reads the exponent from device memory).
+// FP16 latent grid with power-of-two scaling: exp_out[0] = k = max(0, e - 15)
+// for max |grid| <= 2^e, then dst = fp16(grid 2^-k).  exp_out[1] is scratch
+// (the bits of max |grid|, reduced by all blocks with one atomicMax each); the
+// conversion kernel computes k from it and writes exp_out[0].
 cudaError_t launch_grid_to_half_scaled(const float* grid, __half* dst, size_t n, int* exp_out, cudaStream_t s);
 cudaError_t launch_quantize_grid(const float* grid, size_t n_vert, int F, uint8_t* q, float* qp, cudaStream_t s);
 cudaError_t launch_image_mse(const float* a, const float* b, long long n, double* out, cudaStream_t s);

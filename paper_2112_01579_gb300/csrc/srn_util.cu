@@ -298,13 +298,15 @@ cudaError_t launch_to_half(const float* src, __half* dst, size_t n, cudaStream_t
 }
 
 namespace {
-// Exponent of the FP16 latent-grid scale: the smallest k >= 0 with
-// max |grid| 2^-k <= 2^15 (max |grid| = 0 or non-finite: k = 0; a non-finite
-// grid is reported by the kernels that read it).
-__global__ void grid_exp_kernel(const float* __restrict__ g, size_t n, int* __restrict__ exp_out) {
+// max |grid| over all blocks: each block reduces its grid-stride share, then
+// one atomicMax on the bits (non-negative floats order like their bits; NaN
+// entries are skipped by fmaxf, as non-finite grids are reported by the
+// kernels that read them).
+__global__ void grid_absmax_kernel(const float* __restrict__ g, size_t n, unsigned int* __restrict__ max_bits) {
   __shared__ float red[32];
   float m = 0.0f;
-  for (size_t i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, fabsf(g[i]));
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(g[i]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
@@ -313,17 +315,23 @@ __global__ void grid_exp_kernel(const float* __restrict__ g, size_t n, int* __re
     m = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (threadIdx.x == 0) {
-      int e = 0;
-      if (m > 0.0f && m <= 3.4e38f) frexpf(m, &e);  // m = f 2^e, f in [0.5, 1): m <= 2^e
-      *exp_out = e > 15 ? e - 15 : 0;
-    }
+    if (threadIdx.x == 0) atomicMax(max_bits, __float_as_uint(m));
   }
 }
 
+// Exponent of the FP16 latent-grid scale: the smallest k >= 0 with
+// max |grid| 2^-k <= 2^15 (max |grid| = 0 or non-finite: k = 0).
+__device__ __forceinline__ int grid_scale_exp(unsigned int max_bits) {
+  const float m = __uint_as_float(max_bits);
+  int e = 0;
+  if (m > 0.0f && m <= 3.4e38f) frexpf(m, &e);  // m = f 2^e, f in [0.5, 1): m <= 2^e
+  return e > 15 ? e - 15 : 0;
+}
+
 __global__ void to_half_scaled_kernel(const float* __restrict__ src, __half* __restrict__ dst, size_t n,
-                                      const int* __restrict__ exp_in) {
-  const int k = *exp_in;
+                                      int* __restrict__ exp_out, const unsigned int* __restrict__ max_bits) {
+  const int k = grid_scale_exp(*max_bits);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *exp_out = k;
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (; i < n; i += stride) dst[i] = __float2half_rn(ldexpf(src[i], -k));
@@ -331,12 +339,18 @@ __global__ void to_half_scaled_kernel(const float* __restrict__ src, __half* __r
 }  // namespace
 
 cudaError_t launch_grid_to_half_scaled(const float* grid, __half* dst, size_t n, int* exp_out, cudaStream_t s) {
-  grid_exp_kernel<<<1, 1024, 0, s>>>(grid, n, exp_out);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || n == 0) return e;
+  unsigned int* max_bits = reinterpret_cast<unsigned int*>(exp_out + 1);
+  cudaError_t e = cudaMemsetAsync(max_bits, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
   size_t blocks = (n + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  to_half_scaled_kernel<<<(unsigned)blocks, 256, 0, s>>>(grid, dst, n, exp_out);
+  if (blocks == 0) blocks = 1;
+  if (n > 0) {
+    grid_absmax_kernel<<<(unsigned)blocks, 256, 0, s>>>(grid, n, max_bits);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  // with n = 0 this still writes k = 0
+  to_half_scaled_kernel<<<(unsigned)blocks, 256, 0, s>>>(grid, dst, n, exp_out, max_bits);
   return cudaGetLastError();
 }
 
