@@ -713,7 +713,7 @@ SMS, MUFU_PER_SM_CLK, FP32_PER_SM_CLK, MAX_SM_GHZ = 152, 16, 128, 2.07
 # DRAM bytes (read + write) of one 1024^2 frame of the render kernel and of
 # the dense DVR, from the ncu captures summarised in profiles/ (None when the
 # kernel changed after the capture).
-RENDER_DRAM_BYTES = 1136896
+RENDER_DRAM_BYTES = None  # kernel changed after the last capture
 # Warp instructions per network sample of the render kernel from the same
 # capture (smsp__inst_executed.sum 1.02518e10 over 2.08797e8 samples).
 WARP_INST_PER_SAMPLE = 1.02518e10 / 2.08797e8

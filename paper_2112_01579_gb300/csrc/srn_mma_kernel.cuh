@@ -343,7 +343,9 @@ __device__ __forceinline__ void write_input_row(uint8_t* tile, int row, float3 p
   if (nerf) {
     // NeRF rows are 2^j w along axis k mod 3 (octave j = k div 3, w the
     // stored FP32 value of 2 pi): one sin/cos per axis, then angle doubling
-    // sin 2t = 2 s c, cos 2t = (c - s)(c + s).  Doubling doubles the error of
+    // sin 2t = 2 s c, cos 2t = 1 - 2 s^2 (three instructions; the FMA form's
+    // absolute error, about 2^-23, is far below the FP16 rounding of the
+    // features for the A tile, 2^-12).  Doubling doubles the error of
     // the base angle, so with more than five octaves the base is recomputed
     // every fourth octave from the reduced argument: with x = 2^j p_a and
     // r = round(x) (both exact in FP32), 2^j w p_a = w (x - r) + (w - 2 pi) r
@@ -361,9 +363,9 @@ __device__ __forceinline__ void write_input_row(uint8_t* tile, int row, float3 p
         const float r = rintf(x);
         __sincosf(fmaf(kW, x - r, kWErr * r), &s[a], &c[a]);
       } else {
-        const float ss = s[a], cc = c[a];
-        s[a] = 2.0f * ss * cc;
-        c[a] = (cc - ss) * (cc + ss);
+        const float ss = s[a], cc = c[a], t2 = ss + ss;
+        s[a] = t2 * cc;
+        c[a] = fmaf(-t2, ss, 1.0f);
       }
       emit(s[a], c[a]);
     }
