@@ -268,9 +268,13 @@ __device__ __forceinline__ void latent_h(const __half* __restrict__ G, int R, co
 
 // Latent vector from the 8-bit grid (Section 4.2: per-channel codes, value
 // lo + step * code).  F = 16 codes of a vertex are one 16-byte load; each
-// byte is spliced into the FP16 value 1024 + code (exact), widened and
-// accumulated in FP32 as sum_c w_c (1024 + code_c); the offset 1024 * sum w
-// is removed and lo, step applied once per channel.
+// byte is spliced into the FP16 value 1024 + code and 1152 subtracted in
+// FP16, both exact, giving the centred code c - 128.  As in latent_h the
+// corner weight is rounded to FP16 and sum_k w_k (c_k - 128) accumulated by
+// mixed-precision FMAs; since the weights sum to 1,
+// z = (lo + 128 step) + step * sum_k w_k (c_k - 128), with lo + 128 step
+// staged per channel in qp[2 f].  The weight rounding moves z by at most
+// 2^-11 step sum_k w_k |c_k - 128| (half the channel's range, at most).
 template <int F>
 __device__ __forceinline__ void latent_q(const uint8_t* __restrict__ Q, const float* qp, int R, const RayLat& rl,
                                          float3 p, float (&z)[F]) {
@@ -282,9 +286,9 @@ __device__ __forceinline__ void latent_q(const uint8_t* __restrict__ Q, const fl
   cell_coord(p.z, R, iz, fz);
   const int sx = F, sy = R * F, sz = R * R * F;
   const int base = iz * sz + iy * sy + ix * sx;
+  const __half2 k1152 = __float2half2_rn(1152.0f);
 #pragma unroll
   for (int f = 0; f < F; ++f) z[f] = 0.0f;
-  float wsum = 0.0f;
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
@@ -294,26 +298,32 @@ __device__ __forceinline__ void latent_q(const uint8_t* __restrict__ Q, const fl
     for (int kk = 0; kk < 2; ++kk) {
       const int g = kk ? rl.g1 : rl.g0;
       if (kk && g < 0) break;
-      const float ww = w * (kk ? rl.w1 : rl.w0);
-      wsum += ww;
+      const __half wh = __float2half_rn(w * (kk ? rl.w1 : rl.w0));
+      const uint16_t wb = *reinterpret_cast<const uint16_t*>(&wh);
       const uint4 q = __ldg(reinterpret_cast<const uint4*>(Q + g + off));
       const uint32_t words[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         uint32_t lo2 = __byte_perm(words[e], 0x64646464u, 0x4140u);
         uint32_t hi2 = __byte_perm(words[e], 0x64646464u, 0x4342u);
-        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&lo2));
-        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hi2));
-        z[4 * e] = fmaf(ww, a.x, z[4 * e]);
-        z[4 * e + 1] = fmaf(ww, a.y, z[4 * e + 1]);
-        z[4 * e + 2] = fmaf(ww, b.x, z[4 * e + 2]);
-        z[4 * e + 3] = fmaf(ww, b.y, z[4 * e + 3]);
+        const __half2 a2 = __hsub2(*reinterpret_cast<const __half2*>(&lo2), k1152);
+        const __half2 b2 = __hsub2(*reinterpret_cast<const __half2*>(&hi2), k1152);
+        const uint32_t au = *reinterpret_cast<const uint32_t*>(&a2), bu = *reinterpret_cast<const uint32_t*>(&b2);
+        asm("{.reg .b16 x, y, w;\n\t"
+            "mov.b32 {x, y}, %4;\n\t"
+            "mov.b16 w, %6;\n\t"
+            "fma.rn.f32.f16 %0, x, w, %0;\n\t"
+            "fma.rn.f32.f16 %1, y, w, %1;\n\t"
+            "mov.b32 {x, y}, %5;\n\t"
+            "fma.rn.f32.f16 %2, x, w, %2;\n\t"
+            "fma.rn.f32.f16 %3, y, w, %3;}"
+            : "+f"(z[4 * e]), "+f"(z[4 * e + 1]), "+f"(z[4 * e + 2]), "+f"(z[4 * e + 3])
+            : "r"(au), "r"(bu), "h"(wb));
       }
     }
   }
-  const float off1024 = 1024.0f * wsum;
 #pragma unroll
-  for (int f = 0; f < F; ++f) z[f] = fmaf(qp[2 * f + 1], z[f] - off1024, qp[2 * f]);
+  for (int f = 0; f < F; ++f) z[f] = fmaf(qp[2 * f + 1], z[f], qp[2 * f]);
 }
 
 // Layer-0 input row (Eq. 1-2 features, Section 4.2 latent vector, Section 7
@@ -655,7 +665,8 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
     }
     for (int i = tid; i < 3 * M; i += THREADS) fm[i] = net.fourier[i];
     if (GQ)
-      for (int i = tid; i < 2 * F; i += THREADS) qp[i] = ldexpf(net.grid_qp[i], -gexp);
+      for (int i = tid; i < 2 * F; i += THREADS)  // [lo + 128 step, step] per channel (latent_q)
+        qp[i] = ldexpf((i & 1) ? net.grid_qp[i] : fmaf(128.0f, net.grid_qp[i + 1], net.grid_qp[i]), -gexp);
   }
   load_tf(tf, b.tf);
   // the thread's A row starts at zero; the constant tile has ones in columns
