@@ -281,8 +281,8 @@ __global__ void __launch_bounds__(128 * kFitWGS, 1)
       for (int e = 0; e < 4; ++e) {
         split_h2(v[8 * cg + 2 * e], v[8 * cg + 2 * e + 1], hi[e], lo[e]);
       }
-      *reinterpret_cast<uint4*>(Af + a_off(row, cg)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-      *reinterpret_cast<uint4*>(Af + a_off(row, 8 + cg)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      *reinterpret_cast<uint4*>(Af + sw_tile_off(row, cg)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<uint4*>(Af + sw_tile_off(row, 8 + cg)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
     fence_proxy_async();
     tc_fence_before();

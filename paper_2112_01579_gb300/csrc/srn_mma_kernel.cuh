@@ -11,7 +11,8 @@
 //   compositing, early termination) stays one thread per ray as in the paper,
 //   while the layers run as M=128 x N=C tensor-core MMAs.
 // * Every sample: the thread writes its FP16 layer-0 input row into a
-//   128B-swizzled shared-memory tile; one elected thread issues tcgen05.mma
+//   K-major shared-memory tile (no swizzle, see a_off); one elected thread
+//   issues tcgen05.mma
 //   (kind::f16, FP32 accumulate in TMEM); the thread reads its row back with
 //   tcgen05.ld, applies the activation in FP32 and writes it into the same
 //   tile as the next layer's A row as an FP16 hi + lo pair (a = hi + lo to
@@ -192,9 +193,35 @@ __device__ __forceinline__ float act_fold(float acc) {
   return ACT == SRN_ACT_SNAKEALT ? fmaf(0.5f, acc, -__cosf(acc)) : __sinf(acc);
 }
 
-// Byte offset of global 16-byte chunk cg (= column / 8) of row r in an A tile
-// made of 128-row K-atoms.
-__device__ __forceinline__ uint32_t a_off(int r, int cg) { return (uint32_t)((cg >> 3) * kTile) + sw_off(r, cg & 7); }
+// Byte offset of 16-byte chunk cg (= column / 8) of row r in a tile of
+// 128B-swizzled 128-row K-atoms (the fit kernel's operand tiles).
+__device__ __forceinline__ uint32_t sw_tile_off(int r, int cg) {
+  return (uint32_t)((cg >> 3) * kTile) + sw_off(r, cg & 7);
+}
+
+// A tiles (the per-ray operand rows: layer inputs, activations, adjoint rows)
+// are K-major without swizzle: core matrices of 8 rows x 16 bytes, chunk cg
+// (= column / 8) of row r at (r / 8) SBO + 128 cg + 16 (r % 8) with
+// SBO = NA 1024 for NA 64-column blocks of K.  A thread's chunk offsets are
+// then immediates from its row base (no per-store swizzle arithmetic), and a
+// quarter-warp's 16-byte stores of one chunk fill 128 contiguous bytes, free
+// of bank conflicts.  The tile is NA kTile bytes, as the swizzled one was.
+template <int NA>
+__device__ __forceinline__ uint32_t a_off(int r, int cg) {
+  return (uint32_t)((r >> 3) * (NA * 1024) + cg * 128 + (r & 7) * 16);
+}
+// Descriptor of such a tile at saddr: leading byte offset 128 (the next core
+// matrix along K), stride byte offset NA 1024 (the next 8-row group), no
+// swizzle, sm100 descriptor version 1.  K = 16 per MMA advances saddr by 256.
+template <int NA>
+__device__ __forceinline__ uint64_t a_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)(128u >> 4) << 16;
+  d |= (uint64_t)((NA * 1024u) >> 4) << 32;
+  d |= (uint64_t)1u << 46;
+  return d;
+}
 
 // Transfer function with precomputed reciprocal segment widths (same
 // segments and lerp as the shared tf_eval).
@@ -331,7 +358,7 @@ __device__ __forceinline__ void latent_q(const uint8_t* __restrict__ Q, const fl
 // sin_{m-1}, cos_{m-1}, p, z, (t), 1, 1, 0...] over the K0 columns layer 0
 // reads.  Values are packed to FP16 pairs
 // and stored 16 bytes at a time as they are produced.
-template <int M, int F, int K0, int TI, int GQ>
+template <int M, int F, int K0, int TI, int GQ, int NA>
 __device__ __forceinline__ void write_input_row(uint8_t* tile, int row, float3 p, bool nerf, const float* fm,
                                                 const __half* G, const uint8_t* Q, const float* qp, int R,
                                                 const RayLat& rl) {
@@ -345,7 +372,7 @@ __device__ __forceinline__ void write_input_row(uint8_t* tile, int row, float3 p
   auto emit = [&](float a, float b) {
     w[nw++] = pack_h2(a, b);
     if (nw == 4) {
-      *reinterpret_cast<uint4*>(tile + a_off(row, chunk)) = make_uint4(w[0], w[1], w[2], w[3]);
+      *reinterpret_cast<uint4*>(tile + a_off<NA>(row, chunk)) = make_uint4(w[0], w[1], w[2], w[3]);
       ++chunk;
       nw = 0;
     }
@@ -546,7 +573,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
   const int tid = threadIdx.x;
   const int wg = tid >> 7, row = tid & 127, lane = tid & 31;
   const int L = net.l, D = net.D;
-  const int NA = NA0 > NAH ? NA0 : NAH;
+  constexpr int NA = NA0 > NAH ? NA0 : NAH;
   // the FP16 latent grid holds G 2^-gexp: the latent columns' layer-0 weights
   // are staged times 2^gexp (exact), the 8-bit grid's lo / step times 2^-gexp
   const int gexp = net.grid_exp ? *net.grid_exp : 0;
@@ -674,7 +701,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
   {
     uint8_t* A = Aall + wg * NA * kTile;
     uint8_t* One = sm + plan.oOne;
-    for (int cg = 0; cg < NA * 8; ++cg) *reinterpret_cast<uint4*>(A + a_off(row, cg)) = make_uint4(0, 0, 0, 0);
+    for (int cg = 0; cg < NA * 8; ++cg) *reinterpret_cast<uint4*>(A + a_off<NA>(row, cg)) = make_uint4(0, 0, 0, 0);
     if (wg == 0) {
 #pragma unroll
       for (int j = 0; j < 8; ++j)
@@ -800,7 +827,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
     float len = 0.f;
     float3 qs = make_float3(0.f, 0.f, 0.f);  // sample position of this pass
     if (POINTS && active && !failed) {
-      write_input_row<M, F, K0, TI, GQ>(A, row, ppos, nerf, fm, net.grid_h, net.grid_q, qp, net.R, rl);
+      write_input_row<M, F, K0, TI, GQ, NA>(A, row, ppos, nerf, fm, net.grid_h, net.grid_q, qp, net.R, rl);
       qs = ppos;
     } else if (active && !failed) {
       const float ta = fmaf((float)k, b.step, t0);
@@ -816,7 +843,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
         if (ax == 1) q.y = clamp01f(q.y + h);
         if (ax == 2) q.z = clamp01f(q.z + h);
       }
-      write_input_row<M, F, K0, TI, GQ>(A, row, q, nerf, fm, net.grid_h, net.grid_q, qp, net.R, rl);
+      write_input_row<M, F, K0, TI, GQ, NA>(A, row, q, nerf, fm, net.grid_h, net.grid_q, qp, net.R, rl);
       qs = q;
     }
     fence_proxy_async();
@@ -828,7 +855,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
 #pragma unroll
       for (int kk = 0; kk < K0 / 16; ++kk) {
         const uint32_t ka = ((16 * kk) >> 6), kb = ((16 * kk) & 63) * 2;
-        mma_f16(d_tmem, sw128_desc(a_addr + ka * kTile + kb), sw128_desc(b0_addr + ka * BT + kb), IDESC, kk > 0);
+        mma_f16(d_tmem, a_desc<NA>(a_addr + kk * 256), sw128_desc(b0_addr + ka * BT + kb), IDESC, kk > 0);
       }
       mma_commit(mb);
     }
@@ -859,8 +886,8 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
             for (int e = 0; e < 4; ++e) {
               split_h2(act_fold<ACT>(x[8 * j + 2 * e]), act_fold<ACT>(x[8 * j + 2 * e + 1]), hi[e], lo[e]);
             }
-            *reinterpret_cast<uint4*>(A + a_off(row, j)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-            *reinterpret_cast<uint4*>(A + a_off(row, C / 8 + j)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+            *reinterpret_cast<uint4*>(A + a_off<NA>(row, j)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4*>(A + a_off<NA>(row, C / 8 + j)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
           }
           if constexpr (ADJ) {
             // activation derivative of this hidden layer, kept in TMEM for the
@@ -884,7 +911,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
 #pragma unroll
           for (int kk = 0; kk < 2 * C / 16; ++kk) {
             const uint32_t ka = ((16 * kk) >> 6), kb = ((16 * kk) & 63) * 2;
-            mma_f16(d_tmem, sw128_desc(a_addr + ka * kTile + kb), sw128_desc(bw + ka * BT + kb), IDESC, 1u);
+            mma_f16(d_tmem, a_desc<NA>(a_addr + kk * 256), sw128_desc(bw + ka * BT + kb), IDESC, 1u);
           }
           mma_commit(mb);
         }
@@ -924,8 +951,8 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
             for (int e = 0; e < 4; ++e) {
               split_h2(dl[8 * j + 2 * e], dl[8 * j + 2 * e + 1], hi[e], lo[e]);
             }
-            *reinterpret_cast<uint4*>(A + a_off(row, j)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-            *reinterpret_cast<uint4*>(A + a_off(row, C / 8 + j)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+            *reinterpret_cast<uint4*>(A + a_off<NA>(row, j)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4*>(A + a_off<NA>(row, C / 8 + j)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
           }
         }
         fence_proxy_async();
@@ -937,7 +964,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
 #pragma unroll
           for (int kk = 0; kk < 2 * C / 16; ++kk) {
             const uint32_t ka = ((16 * kk) >> 6), kb = ((16 * kk) & 63) * 2;
-            const uint64_t ad = sw128_desc(a_addr + ka * kTile + kb);
+            const uint64_t ad = a_desc<NA>(a_addr + kk * 256);
             if (h >= 1)
               mma_f16(d_tmem, ad, sw128_desc(bht_addr + (h - 1) * NAH * BT + ka * BT + kb), IDESC, kk > 0);
             else
