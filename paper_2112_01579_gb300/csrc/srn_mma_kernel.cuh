@@ -534,7 +534,7 @@ __device__ __forceinline__ float3 latent_grad_h(const __half* __restrict__ G, in
   return make_float3(s * g.x, s * g.y, s * g.z);
 }
 
-template <int C, int M, int F, int ACT, int SH, int TI, int GQ>
+template <int C, int M, int F, int ACT, int SH, int TI, int GQ, int LF>
 __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
     render_mma_kernel(const NetDev net, const BatchDev b, const PointsDev pd, const SmemPlan plan,
                       unsigned long long* __restrict__ ray_counter, unsigned int* __restrict__ status) {
@@ -572,7 +572,9 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
 
   const int tid = threadIdx.x;
   const int wg = tid >> 7, row = tid & 127, lane = tid & 31;
-  const int L = net.l, D = net.D;
+  // LF > 0: the layer count fixed at compile time (the layer loop unrolls);
+  // the dispatch picks such an instantiation only when net.l == LF
+  const int L = LF > 0 ? LF : net.l, D = net.D;
   constexpr int NA = NA0 > NAH ? NA0 : NAH;
   // the FP16 latent grid holds G 2^-gexp: the latent columns' layer-0 weights
   // are staged times 2^gexp (exact), the 8-bit grid's lo / step times 2^-gexp
@@ -864,6 +866,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
     float out[4] = {0.f, 0.f, 0.f, 0.f};
     float dl[C];  // adjoint variant: d out / d (pre-activation) of the current layer
     bool stop = false;
+#pragma unroll(LF > 0 ? LF - 1 : 1)
     for (int layer = 0; layer < L - 1; ++layer) {
       // the failure decision is warp-uniform so tcgen05.ld stays convergent;
       // a failed thread keeps arriving at the warpgroup barriers, which all
@@ -1110,11 +1113,12 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
   if (tid < 32) tmem_dealloc(tmem, TMC);
 }
 
-template <int C, int M, int F, int ACT, int SH, int TI, int GQ>
+template <int C, int M, int F, int ACT, int SH, int TI, int GQ, int LF>
 cudaError_t launch_t(const NetDev& net, const BatchDev& b, const PointsDev& pd, unsigned long long* ctr,
                      unsigned int* status, cudaStream_t s) {
+  if (LF > 0 && net.l != LF) return cudaErrorInvalidValue;
   SmemPlan plan = make_plan(net, C, wgs_for(C, SH), is_adjoint(SH));
-  auto k = render_mma_kernel<C, M, F, ACT, SH, TI, GQ>;
+  auto k = render_mma_kernel<C, M, F, ACT, SH, TI, GQ, LF>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
@@ -1127,10 +1131,12 @@ cudaError_t launch_t(const NetDev& net, const BatchDev& b, const PointsDev& pd, 
   return cudaGetLastError();
 }
 
-// Explicit instantiation of one variant (used by the srn_mma_k*.cu units).
-#define SRN_MMA_INSTANTIATE(C, M, F, ACT, SH, TI, GQ)                                                      \
-  template cudaError_t launch_t<C, M, F, ACT, SH, TI, GQ>(const NetDev&, const BatchDev&, const PointsDev&, \
-                                                          unsigned long long*, unsigned int*, cudaStream_t);
+// Explicit instantiation of one variant (used by the srn_mma_w*.cu units);
+// SRN_MMA_INSTANTIATE_L fixes the layer count.
+#define SRN_MMA_INSTANTIATE_L(C, M, F, ACT, SH, TI, GQ, LF)                                                    \
+  template cudaError_t launch_t<C, M, F, ACT, SH, TI, GQ, LF>(const NetDev&, const BatchDev&, const PointsDev&, \
+                                                              unsigned long long*, unsigned int*, cudaStream_t);
+#define SRN_MMA_INSTANTIATE(C, M, F, ACT, SH, TI, GQ) SRN_MMA_INSTANTIATE_L(C, M, F, ACT, SH, TI, GQ, 0)
 
 }  // namespace mma
 }  // namespace srn

@@ -1,0 +1,13 @@
+// Tensor-core render and point evaluation of the four-layer width-32
+// SnakeAlt network (14 Fourier rows, 16 latent channels) with the layer count
+// fixed at compile time, so the layer loop unrolls.
+#include "srn_mma_kernel.cuh"
+
+namespace srn {
+namespace mma {
+
+SRN_MMA_INSTANTIATE_L(32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 0, 0, 4)
+SRN_MMA_INSTANTIATE_L(32, 14, 16, SRN_ACT_SNAKEALT, kPoints, 0, 0, 4)
+
+}  // namespace mma
+}  // namespace srn
