@@ -66,7 +66,7 @@ cudaError_t launch_render_mma(const NetDev& n, const BatchDev& b, unsigned long 
   if (n.c == 64) return dispatch_shading<64, 30, 16, SRN_ACT_SNAKEALT>(n, b, ctr, status, s);
   if (n.m == 14 && n.F == 16) {
     // the four-layer SnakeAlt network of the inference workload: layer loop unrolled
-    if (n.act == SRN_ACT_SNAKEALT && n.l == 4 && b.shading == SRN_SHADE_NONE)
+    if (n.act == SRN_ACT_SNAKEALT && n.l == 4 && n.D == 1 && b.shading == SRN_SHADE_NONE)
       return launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 0, 0, 4>(n, b, PointsDev{}, ctr, status, s);
     return n.act == SRN_ACT_SNAKEALT ? dispatch_shading<32, 14, 16, SRN_ACT_SNAKEALT>(n, b, ctr, status, s)
                                      : dispatch_shading<32, 14, 16, SRN_ACT_SINE>(n, b, ctr, status, s);
@@ -90,7 +90,7 @@ cudaError_t launch_eval_mma(const NetDev& n, const float* pts, long long count, 
   if (n.c == 48) return launch_t<48, 22, 16, SRN_ACT_SNAKEALT, kPoints, 0, 0>(n, b, pd, ctr, status, s);
   if (n.c == 64) return launch_t<64, 30, 16, SRN_ACT_SNAKEALT, kPoints, 0, 0>(n, b, pd, ctr, status, s);
   if (n.m == 14 && n.F == 16) {
-    if (n.act == SRN_ACT_SNAKEALT && n.l == 4)
+    if (n.act == SRN_ACT_SNAKEALT && n.l == 4 && n.D == 1)
       return launch_t<32, 14, 16, SRN_ACT_SNAKEALT, kPoints, 0, 0, 4>(n, b, pd, ctr, status, s);
     return n.act == SRN_ACT_SNAKEALT ? launch_t<32, 14, 16, SRN_ACT_SNAKEALT, kPoints, 0, 0>(n, b, pd, ctr, status, s)
                                      : launch_t<32, 14, 16, SRN_ACT_SINE, kPoints, 0, 0>(n, b, pd, ctr, status, s);

@@ -1,6 +1,7 @@
 // Tensor-core render and point evaluation of the four-layer width-32
-// SnakeAlt network (14 Fourier rows, 16 latent channels) with the layer count
-// fixed at compile time, so the layer loop unrolls.
+// SnakeAlt density network (14 Fourier rows, 16 latent channels, one output)
+// with layer count and output fixed at compile time, so the layer loop
+// unrolls.
 #include "srn_mma_kernel.cuh"
 
 namespace srn {
