@@ -65,9 +65,18 @@ cudaError_t launch_render_mma(const NetDev& n, const BatchDev& b, unsigned long 
   if (n.c == 48) return dispatch_shading<48, 22, 16, SRN_ACT_SNAKEALT>(n, b, ctr, status, s);
   if (n.c == 64) return dispatch_shading<64, 30, 16, SRN_ACT_SNAKEALT>(n, b, ctr, status, s);
   if (n.m == 14 && n.F == 16) {
-    // the four-layer SnakeAlt network of the inference workload: layer loop unrolled
-    if (n.act == SRN_ACT_SNAKEALT && n.l == 4 && n.D == 1 && b.shading == SRN_SHADE_NONE)
-      return launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 0, 0, 4>(n, b, PointsDev{}, ctr, status, s);
+    // the four-layer SnakeAlt networks of the inference and shading workloads:
+    // layer loop unrolled, output count fixed (the adjoint keeps the generic
+    // kernel, whose register allocation spills less there)
+    if (n.act == SRN_ACT_SNAKEALT && n.l == 4) {
+      const PointsDev pd{};
+      if (n.D == 1 && b.shading == SRN_SHADE_NONE)
+        return launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 0, 0, 4>(n, b, pd, ctr, status, s);
+      if (n.D == 1 && b.shading == SRN_SHADE_FD)
+        return launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_FD, 0, 0, 4>(n, b, pd, ctr, status, s);
+      if (n.D == 4 && b.shading == SRN_SHADE_HEAD)
+        return launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_HEAD, 0, 0, 4>(n, b, pd, ctr, status, s);
+    }
     return n.act == SRN_ACT_SNAKEALT ? dispatch_shading<32, 14, 16, SRN_ACT_SNAKEALT>(n, b, ctr, status, s)
                                      : dispatch_shading<32, 14, 16, SRN_ACT_SINE>(n, b, ctr, status, s);
   }

@@ -87,8 +87,8 @@ inline SmemPlan make_plan(const NetDev& n, int C, int WGS, bool adjoint = false)
 
 // One kernel variant: hidden width C, M Fourier rows, F latent channels,
 // activation ACT, shading SH (or kPoints), direct time input TI, 8-bit grid
-// GQ; LF > 0: a density network (D = 1) of LF layers, both fixed at compile
-// time (0: layer count and outputs read from the network).
+// GQ; LF > 0: a network of LF layers and D = 1 output (4 with head
+// shading), both fixed at compile time (0: read from the network).
 // Defined in srn_mma_kernel.cuh, instantiated in srn_mma_w*.cu.
 template <int C, int M, int F, int ACT, int SH, int TI, int GQ, int LF = 0>
 cudaError_t launch_t(const NetDev& net, const BatchDev& b, const PointsDev& pd, unsigned long long* ctr,

@@ -572,11 +572,13 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
 
   const int tid = threadIdx.x;
   const int wg = tid >> 7, row = tid & 127, lane = tid & 31;
-  // LF > 0: a density network (D = 1) of LF layers, both fixed at compile
-  // time (the layer loop unrolls, the output loop has one term); the
-  // dispatch picks such an instantiation only for such a network
+  // LF > 0: a network of LF layers and D = 1 output (4 for the gradient
+  // head), both fixed at compile time (the layer loop unrolls, the output
+  // loop has its exact trip count); the dispatch picks such an instantiation
+  // only for such a network
+  constexpr int DF = SH == SRN_SHADE_HEAD ? 4 : 1;
   const int L = LF > 0 ? LF : net.l;
-  const int D = LF > 0 ? 1 : net.D;
+  const int D = LF > 0 ? DF : net.D;
   constexpr int NA = NA0 > NAH ? NA0 : NAH;
   // the FP16 latent grid holds G 2^-gexp: the latent columns' layer-0 weights
   // are staged times 2^gexp (exact), the 8-bit grid's lo / step times 2^-gexp
@@ -1118,7 +1120,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
 template <int C, int M, int F, int ACT, int SH, int TI, int GQ, int LF>
 cudaError_t launch_t(const NetDev& net, const BatchDev& b, const PointsDev& pd, unsigned long long* ctr,
                      unsigned int* status, cudaStream_t s) {
-  if (LF > 0 && (net.l != LF || net.D != 1)) return cudaErrorInvalidValue;
+  if (LF > 0 && (net.l != LF || net.D != (SH == SRN_SHADE_HEAD ? 4 : 1))) return cudaErrorInvalidValue;
   SmemPlan plan = make_plan(net, C, wgs_for(C, SH), is_adjoint(SH));
   auto k = render_mma_kernel<C, M, F, ACT, SH, TI, GQ, LF>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total);
