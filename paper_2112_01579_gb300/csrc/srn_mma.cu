@@ -60,8 +60,13 @@ bool render_mma_supported(const NetDev& n, int shading) {
 
 cudaError_t launch_render_mma(const NetDev& n, const BatchDev& b, unsigned long long* ctr, unsigned int* status,
                               cudaStream_t s) {
-  if (n.ti) return launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 1, 0>(n, b, PointsDev{}, ctr, status, s);
-  if (n.gq) return launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 0, 1>(n, b, PointsDev{}, ctr, status, s);
+  const bool l4 = n.l == 4 && n.D == 1;  // the workloads' four-layer density network
+  if (n.ti)
+    return l4 ? launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 1, 0, 4>(n, b, PointsDev{}, ctr, status, s)
+              : launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 1, 0>(n, b, PointsDev{}, ctr, status, s);
+  if (n.gq)
+    return l4 ? launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 0, 1, 4>(n, b, PointsDev{}, ctr, status, s)
+              : launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 0, 1>(n, b, PointsDev{}, ctr, status, s);
   if (n.c == 48) return dispatch_shading<48, 22, 16, SRN_ACT_SNAKEALT>(n, b, ctr, status, s);
   if (n.c == 64) return dispatch_shading<64, 30, 16, SRN_ACT_SNAKEALT>(n, b, ctr, status, s);
   if (n.m == 14 && n.F == 16) {
