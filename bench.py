@@ -713,10 +713,10 @@ SMS, MUFU_PER_SM_CLK, FP32_PER_SM_CLK, MAX_SM_GHZ = 152, 16, 128, 2.07
 # DRAM bytes (read + write) of one 1024^2 frame of the render kernel and of
 # the dense DVR, from the ncu captures summarised in profiles/ (None when the
 # kernel changed after the capture).
-RENDER_DRAM_BYTES = 1685248 + 110080
+RENDER_DRAM_BYTES = 1174272 + 10240
 # Warp instructions per network sample of the render kernel from the same
-# capture (smsp__inst_executed.sum 9.36694e9 over 2.08797e8 samples).
-WARP_INST_PER_SAMPLE = 9.36694e9 / 2.08797e8
+# capture (smsp__inst_executed.sum 8.19375e9 over 2.08797e8 samples).
+WARP_INST_PER_SAMPLE = 8.19375e9 / 2.08797e8
 # Algorithmic work of one plain-workload fit step per point: forward 2 (35 x 32
 # + 32) FLOP, weight gradients the same again, the backward through the
 # output layer (2 x 32), the latent-input gradient (2 x 32 x 8) and its

@@ -60,27 +60,31 @@ bool render_mma_supported(const NetDev& n, int shading) {
 
 cudaError_t launch_render_mma(const NetDev& n, const BatchDev& b, unsigned long long* ctr, unsigned int* status,
                               cudaStream_t s) {
-  const bool l4 = n.l == 4 && n.D == 1;  // the workloads' four-layer density network
+  // the workloads' four-layer density network with a single latent grid
+  const bool l4s = n.l == 4 && n.D == 1 && n.nkey == 1;
   if (n.ti)
-    return l4 ? launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 1, 0, 4>(n, b, PointsDev{}, ctr, status, s)
-              : launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 1, 0>(n, b, PointsDev{}, ctr, status, s);
+    return l4s ? launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 1, 0, 4, 1>(n, b, PointsDev{}, ctr, status, s)
+               : launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 1, 0>(n, b, PointsDev{}, ctr, status, s);
   if (n.gq)
-    return l4 ? launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 0, 1, 4>(n, b, PointsDev{}, ctr, status, s)
-              : launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 0, 1>(n, b, PointsDev{}, ctr, status, s);
+    return l4s ? launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 0, 1, 4, 1>(n, b, PointsDev{}, ctr, status, s)
+               : launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 0, 1>(n, b, PointsDev{}, ctr, status, s);
   if (n.c == 48) return dispatch_shading<48, 22, 16, SRN_ACT_SNAKEALT>(n, b, ctr, status, s);
   if (n.c == 64) return dispatch_shading<64, 30, 16, SRN_ACT_SNAKEALT>(n, b, ctr, status, s);
   if (n.m == 14 && n.F == 16) {
     // the four-layer SnakeAlt networks of the inference and shading workloads:
     // layer loop unrolled, output count fixed (the adjoint keeps the generic
     // kernel, whose register allocation spills less there)
+    // (single latent grid: no time blend in the gather)
     if (n.act == SRN_ACT_SNAKEALT && n.l == 4) {
       const PointsDev pd{};
+      const bool st = n.nkey == 1;
       if (n.D == 1 && b.shading == SRN_SHADE_NONE)
-        return launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 0, 0, 4>(n, b, pd, ctr, status, s);
-      if (n.D == 1 && b.shading == SRN_SHADE_FD)
-        return launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_FD, 0, 0, 4>(n, b, pd, ctr, status, s);
-      if (n.D == 4 && b.shading == SRN_SHADE_HEAD)
-        return launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_HEAD, 0, 0, 4>(n, b, pd, ctr, status, s);
+        return st ? launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 0, 0, 4, 1>(n, b, pd, ctr, status, s)
+                  : launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 0, 0, 4, 0>(n, b, pd, ctr, status, s);
+      if (st && n.D == 1 && b.shading == SRN_SHADE_FD)
+        return launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_FD, 0, 0, 4, 1>(n, b, pd, ctr, status, s);
+      if (st && n.D == 4 && b.shading == SRN_SHADE_HEAD)
+        return launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_HEAD, 0, 0, 4, 1>(n, b, pd, ctr, status, s);
     }
     return n.act == SRN_ACT_SNAKEALT ? dispatch_shading<32, 14, 16, SRN_ACT_SNAKEALT>(n, b, ctr, status, s)
                                      : dispatch_shading<32, 14, 16, SRN_ACT_SINE>(n, b, ctr, status, s);
@@ -105,7 +109,8 @@ cudaError_t launch_eval_mma(const NetDev& n, const float* pts, long long count, 
   if (n.c == 64) return launch_t<64, 30, 16, SRN_ACT_SNAKEALT, kPoints, 0, 0>(n, b, pd, ctr, status, s);
   if (n.m == 14 && n.F == 16) {
     if (n.act == SRN_ACT_SNAKEALT && n.l == 4 && n.D == 1)
-      return launch_t<32, 14, 16, SRN_ACT_SNAKEALT, kPoints, 0, 0, 4>(n, b, pd, ctr, status, s);
+      return n.nkey == 1 ? launch_t<32, 14, 16, SRN_ACT_SNAKEALT, kPoints, 0, 0, 4, 1>(n, b, pd, ctr, status, s)
+                         : launch_t<32, 14, 16, SRN_ACT_SNAKEALT, kPoints, 0, 0, 4, 0>(n, b, pd, ctr, status, s);
     return n.act == SRN_ACT_SNAKEALT ? launch_t<32, 14, 16, SRN_ACT_SNAKEALT, kPoints, 0, 0>(n, b, pd, ctr, status, s)
                                      : launch_t<32, 14, 16, SRN_ACT_SINE, kPoints, 0, 0>(n, b, pd, ctr, status, s);
   }

@@ -88,9 +88,10 @@ inline SmemPlan make_plan(const NetDev& n, int C, int WGS, bool adjoint = false)
 // One kernel variant: hidden width C, M Fourier rows, F latent channels,
 // activation ACT, shading SH (or kPoints), direct time input TI, 8-bit grid
 // GQ; LF > 0: a network of LF layers and D = 1 output (4 with head
-// shading), both fixed at compile time (0: read from the network).
+// shading), both fixed at compile time (0: read from the network); ST = 1:
+// a single latent grid (no keyframes), so the gather has no time blend.
 // Defined in srn_mma_kernel.cuh, instantiated in srn_mma_w*.cu.
-template <int C, int M, int F, int ACT, int SH, int TI, int GQ, int LF = 0>
+template <int C, int M, int F, int ACT, int SH, int TI, int GQ, int LF = 0, int ST = 0>
 cudaError_t launch_t(const NetDev& net, const BatchDev& b, const PointsDev& pd, unsigned long long* ctr,
                      unsigned int* status, cudaStream_t s);
 

@@ -251,7 +251,8 @@ struct RayLat {
 // and corner instead of a widening and an FMA.  The weight rounding (2^-11
 // relative) moves z_c by at most 2^-11 sum_k w_k |G_kc|, about as much as the
 // FP16 rounding of z itself for the A tile.
-template <int F>
+// ST: one latent grid (no keyframes), known at compile time: no time blend.
+template <int F, int ST>
 __device__ __forceinline__ void latent_h(const __half* __restrict__ G, int R, const RayLat& rl, float3 p,
                                          float (&z)[F]) {
   int ix, iy, iz;
@@ -269,10 +270,10 @@ __device__ __forceinline__ void latent_h(const __half* __restrict__ G, int R, co
     const float w = (dx ? fx : 1.0f - fx) * (dy ? fy : 1.0f - fy) * (dz ? fz : 1.0f - fz);
     const int off = base + dx * sx + dy * sy + dz * sz;
 #pragma unroll
-    for (int kk = 0; kk < 2; ++kk) {
-      const int g = kk ? rl.g1 : rl.g0;
-      if (kk && g < 0) break;
-      const __half wh = __float2half_rn(w * (kk ? rl.w1 : rl.w0));
+    for (int kk = 0; kk < (ST ? 1 : 2); ++kk) {
+      const int g = ST ? 0 : (kk ? rl.g1 : rl.g0);
+      if (!ST && kk && g < 0) break;
+      const __half wh = __float2half_rn(ST ? w : w * (kk ? rl.w1 : rl.w0));
       const uint16_t wb = *reinterpret_cast<const uint16_t*>(&wh);
 #pragma unroll
       for (int c = 0; c < F; c += 8) {
@@ -302,7 +303,7 @@ __device__ __forceinline__ void latent_h(const __half* __restrict__ G, int R, co
 // z = (lo + 128 step) + step * sum_k w_k (c_k - 128), with lo + 128 step
 // staged per channel in qp[2 f].  The weight rounding moves z by at most
 // 2^-11 step sum_k w_k |c_k - 128| (half the channel's range, at most).
-template <int F>
+template <int F, int ST>
 __device__ __forceinline__ void latent_q(const uint8_t* __restrict__ Q, const float* qp, int R, const RayLat& rl,
                                          float3 p, float (&z)[F]) {
   static_assert(F == 16, "one 16-byte load per vertex");
@@ -322,10 +323,10 @@ __device__ __forceinline__ void latent_q(const uint8_t* __restrict__ Q, const fl
     const float w = (dx ? fx : 1.0f - fx) * (dy ? fy : 1.0f - fy) * (dz ? fz : 1.0f - fz);
     const int off = base + dx * sx + dy * sy + dz * sz;
 #pragma unroll
-    for (int kk = 0; kk < 2; ++kk) {
-      const int g = kk ? rl.g1 : rl.g0;
-      if (kk && g < 0) break;
-      const __half wh = __float2half_rn(w * (kk ? rl.w1 : rl.w0));
+    for (int kk = 0; kk < (ST ? 1 : 2); ++kk) {
+      const int g = ST ? 0 : (kk ? rl.g1 : rl.g0);
+      if (!ST && kk && g < 0) break;
+      const __half wh = __float2half_rn(ST ? w : w * (kk ? rl.w1 : rl.w0));
       const uint16_t wb = *reinterpret_cast<const uint16_t*>(&wh);
       const uint4 q = __ldg(reinterpret_cast<const uint4*>(Q + g + off));
       const uint32_t words[4] = {q.x, q.y, q.z, q.w};
@@ -358,15 +359,15 @@ __device__ __forceinline__ void latent_q(const uint8_t* __restrict__ Q, const fl
 // sin_{m-1}, cos_{m-1}, p, z, (t), 1, 1, 0...] over the K0 columns layer 0
 // reads.  Values are packed to FP16 pairs
 // and stored 16 bytes at a time as they are produced.
-template <int M, int F, int K0, int TI, int GQ, int NA>
+template <int M, int F, int K0, int TI, int GQ, int NA, int ST>
 __device__ __forceinline__ void write_input_row(uint8_t* tile, int row, float3 p, bool nerf, const float* fm,
                                                 const __half* G, const uint8_t* Q, const float* qp, int R,
                                                 const RayLat& rl) {
   constexpr int D0 = 3 + 2 * M + F + TI;
   static_assert(M >= 3, "the NeRF recurrence needs the three base rows");
   float z[F];
-  if constexpr (GQ != 0) latent_q<F>(Q, qp, R, rl, p, z);
-  else latent_h<F>(G, R, rl, p, z);
+  if constexpr (GQ != 0) latent_q<F, ST>(Q, qp, R, rl, p, z);
+  else latent_h<F, ST>(G, R, rl, p, z);
   uint32_t w[4];
   int nw = 0, chunk = 0;
   auto emit = [&](float a, float b) {
@@ -534,7 +535,7 @@ __device__ __forceinline__ float3 latent_grad_h(const __half* __restrict__ G, in
   return make_float3(s * g.x, s * g.y, s * g.z);
 }
 
-template <int C, int M, int F, int ACT, int SH, int TI, int GQ, int LF>
+template <int C, int M, int F, int ACT, int SH, int TI, int GQ, int LF, int ST>
 __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
     render_mma_kernel(const NetDev net, const BatchDev b, const PointsDev pd, const SmemPlan plan,
                       unsigned long long* __restrict__ ray_counter, unsigned int* __restrict__ status) {
@@ -833,7 +834,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
     float len = 0.f;
     float3 qs = make_float3(0.f, 0.f, 0.f);  // sample position of this pass
     if (POINTS && active && !failed) {
-      write_input_row<M, F, K0, TI, GQ, NA>(A, row, ppos, nerf, fm, net.grid_h, net.grid_q, qp, net.R, rl);
+      write_input_row<M, F, K0, TI, GQ, NA, ST>(A, row, ppos, nerf, fm, net.grid_h, net.grid_q, qp, net.R, rl);
       qs = ppos;
     } else if (active && !failed) {
       const float ta = fmaf((float)k, b.step, t0);
@@ -849,7 +850,7 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
         if (ax == 1) q.y = clamp01f(q.y + h);
         if (ax == 2) q.z = clamp01f(q.z + h);
       }
-      write_input_row<M, F, K0, TI, GQ, NA>(A, row, q, nerf, fm, net.grid_h, net.grid_q, qp, net.R, rl);
+      write_input_row<M, F, K0, TI, GQ, NA, ST>(A, row, q, nerf, fm, net.grid_h, net.grid_q, qp, net.R, rl);
       qs = q;
     }
     fence_proxy_async();
@@ -1117,12 +1118,13 @@ __global__ void __launch_bounds__(128 * wgs_for(C, SH), 1)
   if (tid < 32) tmem_dealloc(tmem, TMC);
 }
 
-template <int C, int M, int F, int ACT, int SH, int TI, int GQ, int LF>
+template <int C, int M, int F, int ACT, int SH, int TI, int GQ, int LF, int ST>
 cudaError_t launch_t(const NetDev& net, const BatchDev& b, const PointsDev& pd, unsigned long long* ctr,
                      unsigned int* status, cudaStream_t s) {
   if (LF > 0 && (net.l != LF || net.D != (SH == SRN_SHADE_HEAD ? 4 : 1))) return cudaErrorInvalidValue;
+  if (ST && net.nkey != 1) return cudaErrorInvalidValue;
   SmemPlan plan = make_plan(net, C, wgs_for(C, SH), is_adjoint(SH));
-  auto k = render_mma_kernel<C, M, F, ACT, SH, TI, GQ, LF>;
+  auto k = render_mma_kernel<C, M, F, ACT, SH, TI, GQ, LF, ST>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, plan.total);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
@@ -1136,11 +1138,13 @@ cudaError_t launch_t(const NetDev& net, const BatchDev& b, const PointsDev& pd, 
 }
 
 // Explicit instantiation of one variant (used by the srn_mma_w*.cu units);
-// SRN_MMA_INSTANTIATE_L fixes the layer count.
-#define SRN_MMA_INSTANTIATE_L(C, M, F, ACT, SH, TI, GQ, LF)                                                    \
-  template cudaError_t launch_t<C, M, F, ACT, SH, TI, GQ, LF>(const NetDev&, const BatchDev&, const PointsDev&, \
-                                                              unsigned long long*, unsigned int*, cudaStream_t);
-#define SRN_MMA_INSTANTIATE(C, M, F, ACT, SH, TI, GQ) SRN_MMA_INSTANTIATE_L(C, M, F, ACT, SH, TI, GQ, 0)
+// SRN_MMA_INSTANTIATE_L fixes the layer count (LF) and whether the network
+// has a single latent grid (ST).
+#define SRN_MMA_INSTANTIATE_L(C, M, F, ACT, SH, TI, GQ, LF, ST)                                                  \
+  template cudaError_t launch_t<C, M, F, ACT, SH, TI, GQ, LF, ST>(const NetDev&, const BatchDev&,               \
+                                                                  const PointsDev&, unsigned long long*,        \
+                                                                  unsigned int*, cudaStream_t);
+#define SRN_MMA_INSTANTIATE(C, M, F, ACT, SH, TI, GQ) SRN_MMA_INSTANTIATE_L(C, M, F, ACT, SH, TI, GQ, 0, 0)
 
 }  // namespace mma
 }  // namespace srn
