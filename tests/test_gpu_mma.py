@@ -403,3 +403,29 @@ def test_mma_bounded_wait_reports_timeout(srn, monkeypatch, which):
     ref, _, _ = oracle.render(oracle.OracleNet(q), cams, H.oracle_tf(tf), 16, 16, 1 / 64, 2.0)
     assert np.abs(got - ref).max() <= H.TOL_FP16_IMG
     net.close()
+
+
+def test_mma_single_grid_kernel_equals_keyframe_kernel(srn):
+    """The render instantiation for one latent grid (no time blend) against
+    the keyframe instantiation on the same grid stored as two identical
+    keyframes, rendered at the first keyframe time: the blend weights are
+    exactly 1 and 0, so the two images agree bit for bit; both against the
+    oracle at the FP16 bound."""
+    import torch
+    S = srn
+    p1 = H.cfg2_params(seed=97, R=16)
+    p2 = dict(p1)
+    p2["grid"] = np.concatenate([p1["grid"], p1["grid"]], axis=0)  # [keyframe][z][y][x][F]
+    p2["key_times"] = np.asarray([0.0, 1.0], np.float32)
+    n1, q1 = _net16(S, p1)
+    n2, _ = _net16(S, p2)
+    tf = synth.tf_preset(8)
+    cams = synth.orbit_cameras(2)
+    a, _ = _render(S, n1, cams, tf, 48, 40, 1 / 128, 0.99)
+    b, _ = _render(S, n2, cams, tf, 48, 40, 1 / 128, 0.99, times=[0.0])
+    assert np.array_equal(a, b)
+    ref, mg, _ = oracle.render(oracle.OracleNet(q1), cams, H.oracle_tf(tf), 48, 40, 1 / 128, 0.99, want_margin=True)
+    r = H.compare_images(a[0], ref[0], mg[0], H.TOL_FP16_IMG, 0.99)
+    assert r["ok"], r
+    n1.close()
+    n2.close()
