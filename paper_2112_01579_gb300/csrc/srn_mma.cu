@@ -60,7 +60,8 @@ bool render_mma_supported(const NetDev& n, int shading) {
 
 cudaError_t launch_render_mma(const NetDev& n, const BatchDev& b, unsigned long long* ctr, unsigned int* status,
                               cudaStream_t s) {
-  // the workloads' four-layer density network with a single latent grid
+  // direct time input / 8-bit grid: the four-layer density network with a
+  // single latent grid runs the specialised instantiation (see below)
   const bool l4s = n.l == 4 && n.D == 1 && n.nkey == 1;
   if (n.ti)
     return l4s ? launch_t<32, 14, 16, SRN_ACT_SNAKEALT, SRN_SHADE_NONE, 1, 0, 4, 1>(n, b, PointsDev{}, ctr, status, s)
@@ -72,9 +73,9 @@ cudaError_t launch_render_mma(const NetDev& n, const BatchDev& b, unsigned long 
   if (n.c == 64) return dispatch_shading<64, 30, 16, SRN_ACT_SNAKEALT>(n, b, ctr, status, s);
   if (n.m == 14 && n.F == 16) {
     // the four-layer SnakeAlt networks of the inference and shading workloads:
-    // layer loop unrolled, output count fixed (the adjoint keeps the generic
-    // kernel, whose register allocation spills less there)
-    // (single latent grid: no time blend in the gather)
+    // layer loop unrolled, output count fixed and, for a single latent grid,
+    // no time blend in the gather (the adjoint keeps the generic kernel, whose
+    // register allocation spills less there)
     if (n.act == SRN_ACT_SNAKEALT && n.l == 4) {
       const PointsDev pd{};
       const bool st = n.nkey == 1;
