@@ -35,7 +35,7 @@ constexpr int adj_acc_cols(int C, int K0) { return (((K0 > C ? K0 : C) + 31) / 3
 constexpr int tmem_wg_cols(int C, int SH, int K0) {
   return is_adjoint(SH) ? adj_acc_cols(C, K0) + (kAdjMaxLayers - 2) * C : C;
 }
-constexpr int kTile = 128 * 128;       // one A K-atom: 128 rows x 128 B (64 fp16)
+constexpr int kTile = 128 * 128;       // 128 rows x 128 B (64 FP16 columns): an A-tile block, the constant tile
 
 constexpr long long kWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
 
@@ -54,8 +54,9 @@ struct SmemPlan {
 };
 
 // Shared memory for hidden width C and WGS warpgroups.  An operand row spans
-// ceil(K / 64) K-atoms of 64 FP16 columns; atoms of an A tile are kTile
-// bytes apart, atoms of a B tile C * 128 bytes apart.
+// ceil(K / 64) blocks of 64 FP16 columns: a warpgroup's A tile (128 rows,
+// unswizzled core-matrix layout, see a_off) takes kTile bytes per block; B
+// tiles are 128B-swizzled K-atoms C * 128 bytes apart.
 inline SmemPlan make_plan(const NetDev& n, int C, int WGS, bool adjoint = false) {
   const int D0 = net_d0(n);
   const int K0 = ((D0 + 2 + 15) / 16) * 16;
